@@ -1,0 +1,191 @@
+/*
+ * cteno.h -- C ABI of the GB300 (sm_103a) CTENO / CTENOZ finite-volume library.
+ *
+ * The library advances the compressible Euler equations (paper eq. 1) on triangle (2D) and
+ * tetrahedron (3D) meshes with the semi-discretisation of eq. 2: a per-cell high-order
+ * reconstruction (Sec. 2.1-2.6: reference-space least squares, eqs. 5-12; smoothness indicators,
+ * eq. 15; CWENO optimal-polynomial split, eqs. 16-18; CTENO selection, Alg. 1, or CTENOZ
+ * selection, Alg. 2), the HLLC flux at face Gauss points (Sec. 2.7, eqs. 24-29), and the
+ * explicit third-order Runge-Kutta update (Sec. 2, after eq. 2). Several independent meshes can
+ * share one context; each RK stage advances all of them in the same kernel launches.
+ *
+ * Conventions, for every entry point:
+ *   - Return 0 on success or a negative CTENO_ERR_* code. The message of the last failure is
+ *     cteno_last_error(ctx). A context whose device state reported a fault (non-finite state,
+ *     bounds violation) returns CTENO_ERR_DEVICE from every later synchronising call.
+ *   - Input arrays are copied; the library never keeps a caller's pointer. Output arrays are
+ *     allocated by the caller.
+ *   - Host pointers are plain host memory; "device" pointers are CUDA device (or managed)
+ *     memory of the context's device.
+ *   - Work is enqueued on the stream passed to cteno_create (borrowed, never destroyed) and the
+ *     call returns without synchronising, except the cteno_get_* calls that write host memory,
+ *     cteno_sync and cteno_lsq_build, which synchronise that stream.
+ *   - State layout at the boundary: conserved cell means U[v][c], variable-major, v = 0..d+1
+ *     (rho, rho u, rho v[, rho w], E), c in the caller's original cell numbering of that mesh.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef CTENO_H
+#define CTENO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  CTENO_OK = 0,
+  CTENO_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, bad parameter) */
+  CTENO_ERR_STATE = -2,    /* call out of order (e.g. rk_stage before lsq_build) */
+  CTENO_ERR_MESH = -3,     /* degenerate cell, non-manifold face, or bad connectivity */
+  CTENO_ERR_STENCIL = -4,  /* a cell cannot gather M = 2K stencil cells */
+  CTENO_ERR_RANK = -5,     /* a central least-squares matrix is rank deficient */
+  CTENO_ERR_CUDA = -6,     /* a CUDA runtime call failed (message has the CUDA error) */
+  CTENO_ERR_DEVICE = -7,   /* a kernel reported a fault in its error word */
+  CTENO_ERR_NOMEM = -8     /* host or device allocation failed */
+};
+
+enum { CTENO_SCHEME_CTENO = 0, CTENO_SCHEME_CTENOZ = 1 };
+enum { CTENO_FP64 = 0, CTENO_MIXED = 1 };
+enum { CTENO_BOUNDARY_TRANSMISSIVE = 0 };
+
+/* Scheme parameters (paper notation). */
+typedef struct {
+  int dim;              /* d = 2 (triangles) or 3 (tetrahedra) */
+  int degree;           /* r = 2 or 3: central polynomial degree, order r+1 (Sec. 2.1) */
+  int scheme;           /* CTENO_SCHEME_CTENO (Alg. 1) or CTENO_SCHEME_CTENOZ (Alg. 2) */
+  int precision;        /* CTENO_FP64: all arithmetic in FP64. CTENO_MIXED: reconstruction and
+                           flux in FP32; geometry, least-squares build, residual accumulation and
+                           the RK update in FP64 */
+  int lam_gamma;        /* 1: scale-separation measure gamma_s carries the linear coefficient
+                           lambda_s of eq. 18 (default, reproduces Tables 1-3); 0: as printed in
+                           eq. 19 / Alg. 1-2 */
+  int positivity_guard; /* 1: a cell whose face state has rho <= 0 or p <= 0 uses its cell mean
+                           at all its face points for that stage (not in the paper) */
+  double C_T;           /* cut-off of eq. 23 (paper: 1e-6) */
+  double lambda1p;      /* lambda_1' of eq. 18 (paper: 1e4 or 1e15) */
+  double eps;           /* epsilon of eqs. 19 and CTENOZ (not given by the paper; default 1e-40) */
+  double cfl;           /* Courant number of the time step rule (cteno_run) */
+  double gamma;         /* ratio of specific heats (1.4) */
+} cteno_params;
+
+typedef struct cteno_ctx cteno_ctx;
+
+/* Fill *p with the defaults: d = 2, r = 2, CTENO, FP64, lam_gamma 1, guard 1, C_T = 1e-6,
+ * lambda_1' = 1e15, eps = 1e-40, CFL 0.5, gamma 1.4. */
+void cteno_default_params(cteno_params *p);
+
+/* Create a context on the current CUDA device. `cuda_stream` is a cudaStream_t (may be NULL for
+ * the legacy default stream); it is borrowed for the life of the context. */
+int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream);
+
+/* Append one mesh to the context (Sec. 2: the physical domain as triangles / tetrahedra).
+ *   nverts, xyz        : host, xyz[nverts][dim] vertex coordinates (copied).
+ *   ncells, cell_verts : host, cell_verts[ncells][dim+1] vertex ids (any orientation; copied).
+ *   period             : host, period[dim]; period[j] > 0 makes direction j periodic with that
+ *                        length (vertices are stored once and cells unwrap across the box);
+ *                        NULL or 0 = bounded. Bounded boundary faces are transmissive.
+ *   mesh_id_out        : receives the index of the mesh in the batch.
+ * Errors: CTENO_ERR_MESH for degenerate cells or faces shared by more than two cells. Meshes can
+ * only be added before cteno_stencil_build. */
+int cteno_mesh_build(cteno_ctx *ctx, int64_t nverts, const double *xyz, int64_t ncells,
+                     const int32_t *cell_verts, const double *period, int boundary_kind,
+                     int32_t *mesh_id_out);
+
+/* Build, on the host, the central stencil of M = 2K cells of every cell (Sec. 2.1, eq. 6; the
+ * "SBC" compact stencil) and its directional stencils (Sec. 2.3, Fig. 1), then renumber the cells
+ * of each mesh along a Morton curve of their centroids. CTENO_ERR_STENCIL when a cell cannot
+ * gather M cells (mesh too small) or a periodic stencil spans too much of the box. */
+int cteno_stencil_build(cteno_ctx *ctx);
+
+/* Upload the meshes and build on the GPU, in FP64, the geometry, the basis moments of every
+ * stencil in the target cell's reference space (eqs. 5, 7, 10) and their least-squares
+ * pseudo-inverses by Householder QR (eq. 12). The mixed path stores them in FP32.
+ * CTENO_ERR_RANK when a central matrix is rank deficient. Synchronises. */
+int cteno_lsq_build(cteno_ctx *ctx);
+
+/* Set the conserved cell means of one mesh: U[v][c] (layout above), host or device pointer
+ * (is_device = 0 / 1). Also computes the CFL time step of the new state for cteno_run. */
+int cteno_set_state(cteno_ctx *ctx, int32_t mesh_id, const double *U, int is_device);
+
+/* One stage (stage = 0, 1, 2) of the SSP-RK3 step, for every mesh, with the time step dt[mesh]
+ * (host array of length nmeshes). Stage 0 stores U^n. */
+int cteno_rk_stage(cteno_ctx *ctx, int stage, const double *dt);
+
+/* nsteps full SSP-RK3 steps, each with dt = CFL * min_i |V_i| / sum_f |A_f| (|u_i.n_f| + c_i)
+ * taken per mesh from the state at the start of the step. The 3 stages of a step are captured
+ * once into a CUDA graph and replayed. */
+int cteno_run(cteno_ctx *ctx, int nsteps);
+
+/* Read the conserved cell means of one mesh into U_out[v][c] (host or device). */
+int cteno_get_state(cteno_ctx *ctx, int32_t mesh_id, double *U_out, int is_device);
+
+/* Time step used by the last step of cteno_run for each mesh: host dt_out[nmeshes]. */
+int cteno_get_dt(cteno_ctx *ctx, double *dt_out);
+
+/* Enable (1) or disable (0, default) recording of the stencil-selection flags. */
+int cteno_record_flags(cteno_ctx *ctx, int enable);
+
+/* Selection flags of the last reconstruction of one mesh, host out[c][v] (original numbering):
+ * bit 0 = central stencil kept (delta_1 = 1); bit 1+f = directional stencil of local face f
+ * selected (eq. 23 and Alg. 1 / 2). Local faces follow the positively oriented vertex order. */
+int cteno_get_flags(cteno_ctx *ctx, int32_t mesh_id, uint8_t *out);
+
+/* Reconstructed face Gauss-point states of the last reconstruction (debug), host
+ * out[c][f][q][v], f local face, q canonical point order of the face. FP64 values (the mixed
+ * path's FP32 values converted). */
+int cteno_get_face_states(cteno_ctx *ctx, int32_t mesh_id, double *out);
+
+/* Host-side stencil of one cell (after cteno_stencil_build, before or after lsq_build):
+ * central[M] original cell ids in nearest-first order, dir[(d+1)][2d] positions in `central` of
+ * the members of each directional stencil (-1 padded). Admissibility is known only after
+ * cteno_lsq_build; dok may be NULL before it. */
+int cteno_get_stencil(cteno_ctx *ctx, int32_t mesh_id, int64_t cell, int32_t *central,
+                      int32_t *dir, int32_t *dok);
+
+/* Sizes: out[0] = nmeshes, out[1] = total cells, out[2] = M, out[3] = K-1, out[4] = nv,
+ * out[5] = faces per cell, out[6] = Gauss points per face, out[7] = cells of mesh `mesh_id`
+ * (or 0 if mesh_id < 0). */
+int cteno_info(cteno_ctx *ctx, int32_t mesh_id, int64_t *out);
+
+/* Number of cells that fell back to their mean under the positivity guard since the last call,
+ * and whether any kernel reported a fault. Synchronises. */
+int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
+
+/* Launch configuration: block sizes of the reconstruction and flux kernels (0 = keep). */
+int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block);
+
+/* Time the candidate launch configurations on the current state and keep the fastest; the state
+ * is restored afterwards. best_out[2] (may be NULL) receives the chosen block sizes. */
+int cteno_autotune(cteno_ctx *ctx, int32_t *best_out);
+
+/* Kernel statistics for roofline accounting: out[0] = algorithmic DRAM bytes of one
+ * reconstruction launch, out[1] = of one flux/update launch, out[2] = FLOPs of one
+ * reconstruction launch, out[3] = of one flux/update launch (all cells of all meshes). */
+int cteno_kernel_stats(cteno_ctx *ctx, double *out);
+
+/* Time each kernel of one step with CUDA events on the context stream (FLOP/byte accounting):
+ * ms_out[0] = reconstruction (3 launches), ms_out[1] = flux/update (3 launches) of one step,
+ * averaged over nsteps steps of cteno_run's graph-free path. Advances the state. */
+int cteno_profile_step(cteno_ctx *ctx, int nsteps, double *ms_out);
+
+/* Enable (1) or disable (0, default) timing of the kernels inside cteno_run's step graph: event
+ * record nodes around every launch, read back by cteno_last_kernel_ms. Rebuilds the graph. */
+int cteno_set_timing(cteno_ctx *ctx, int enable);
+
+/* Device time of the last step replayed by cteno_run (timing enabled): ms_out[0] = the three
+ * reconstruction launches, ms_out[1] = the three flux/update launches. Synchronises. */
+int cteno_last_kernel_ms(cteno_ctx *ctx, double *ms_out);
+
+/* Measure the FP64 and FP32 FMA throughput of the current device (TFLOP/s, 2 FLOP per FMA) with
+ * independent FMA chains on every SM; about 0.5 s. Used as the ALU roofline denominator. */
+int cteno_measure_alu_peak(double *fp64_tflops, double *fp32_tflops);
+
+const char *cteno_last_error(cteno_ctx *ctx);
+void cteno_destroy(cteno_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTENO_H */

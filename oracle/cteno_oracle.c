@@ -252,7 +252,9 @@ static double dmonomial(const int *e, const int *al, const double *xi, int d) {
 /* ------------------------------------------------------------------------------------------ */
 /* Mesh and geometry (Sec. 2, eq. 2)                                                           */
 /* ------------------------------------------------------------------------------------------ */
-static double wrap1(double dx, double L) { return (L > 0.0) ? dx - L * round(dx / L) : dx; }
+/* Translation by a whole number of periods bringing a point at offset dx next to the origin
+ * (0 in a bounded direction). */
+static double image_shift(double dx, double L) { return (L > 0.0) ? -L * round(dx / L) : 0.0; }
 
 static int build_geometry(orc *o, const double *xyz, const int *cells) {
   const int d = o->p.dim, nvc = d + 1, n = o->ncells;
@@ -266,11 +268,11 @@ static int build_geometry(orc *o, const double *xyz, const int *cells) {
     int v[4];
     double X[4][3];
     for (int a = 0; a < nvc; ++a) v[a] = cells[i * nvc + a];
-    /* unwrap periodic images next to local vertex 0 */
+    /* unwrap periodic images next to local vertex 0: x - L round((x - x0) / L) */
     for (int a = 0; a < nvc; ++a)
       for (int j = 0; j < d; ++j) {
         double x0 = xyz[v[0] * d + j], x = xyz[v[a] * d + j];
-        X[a][j] = x0 + wrap1(x - x0, o->period[j]);
+        X[a][j] = x + image_shift(x - x0, o->period[j]);
       }
     double J[9];
     for (int r = 0; r < d; ++r)
@@ -536,9 +538,8 @@ static int central_stencil(orc *o, int i, orc_cell *c) {
     q->id = m;
     q->dist2 = 0.0;
     for (int j = 0; j < d; ++j) {
-      double dx = o->cen[m * d + j] - o->cen[i * d + j];
-      double w = wrap1(dx, o->period[j]);
-      q->sh[j] = w - dx;
+      q->sh[j] = image_shift(o->cen[m * d + j] - o->cen[i * d + j], o->period[j]);
+      double w = (o->cen[m * d + j] + q->sh[j]) - o->cen[i * d + j];
       q->dist2 += w * w;
     }
   }

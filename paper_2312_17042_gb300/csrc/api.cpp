@@ -1,0 +1,765 @@
+// api.cpp -- the C ABI of include/cteno.h: context, device memory, set-up and the time loop.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device.h"
+#include "internal.h"
+
+using namespace cteno;
+
+struct cteno_ctx {
+  cteno_params p{};
+  cudaStream_t stream = nullptr;     // borrowed
+  cudaStream_t capture = nullptr;    // owned, for graph capture
+  int d = 0, nv = 0, nf = 0, nq = 0, nk = 0, M = 0, nd = 0;
+  bool fp32 = false;
+  std::vector<Mesh> meshes;
+  bool stencils = false, built = false;
+  int64_t N = 0;
+  std::string err;
+  Tables tab{};
+  std::vector<uint32_t> h_cinfo;     // device-order cinfo after set-up (admissibility)
+  // device memory
+  DevTables *d_tab = nullptr;
+  int64_t *d_mesh_off = nullptr;
+  double *U = nullptr, *Un = nullptr;
+  float *U32 = nullptr;
+  int32_t *st = nullptr, *nbr = nullptr;
+  uint32_t *cinfo = nullptr, *fmeta = nullptr;
+  void *Pc = nullptr, *Pd = nullptr, *Uf = nullptr;
+  uint8_t *flags = nullptr;
+  double *fn = nullptr, *fa = nullptr, *vol = nullptr, *dt = nullptr;
+  float *fn32 = nullptr, *fa32 = nullptr;
+  int *derr = nullptr;
+  unsigned long long *guard = nullptr;
+  std::vector<int32_t *> d_rank;
+  double *stage_buf = nullptr;       // staging for host <-> device state copies
+  size_t stage_cap = 0;
+  double *backup = nullptr;          // autotune state backup
+  int recon_block = 128, flux_block = 128;
+  bool record_flags = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<void *> allocations;
+  int64_t member_sum = 0;            // admissible directional members over all cells
+  bool timing = false;
+  cudaEvent_t tev[7] = {};           // event record nodes of the step graph
+};
+
+namespace {
+
+int fail(cteno_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(ctx, CTENO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(cteno_ctx *ctx, P **ptr, size_t bytes) {
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  if (e == cudaSuccess) {
+    ctx->allocations.push_back(p);
+    *ptr = (P *)p;
+  }
+  return e;
+}
+
+KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
+  KArgs a{};
+  a.N = ctx->N;
+  a.nmesh = (int)ctx->meshes.size();
+  a.mesh_off = ctx->d_mesh_off;
+  a.U = ctx->U;
+  a.Un = ctx->Un;
+  a.U32 = ctx->U32;
+  a.st = ctx->st;
+  a.cinfo = ctx->cinfo;
+  a.Pc = ctx->Pc;
+  a.Pd = ctx->Pd;
+  a.Uf = ctx->Uf;
+  a.flags = ctx->record_flags ? ctx->flags : nullptr;
+  a.nbr = ctx->nbr;
+  a.fmeta = ctx->fmeta;
+  a.fn = ctx->fn;
+  a.fa = ctx->fa;
+  a.fn32 = ctx->fn32;
+  a.fa32 = ctx->fa32;
+  a.vol = ctx->vol;
+  a.dt = ctx->dt;
+  a.tab = ctx->d_tab;
+  a.err = ctx->derr;
+  a.guard = ctx->guard;
+  a.C_T = ctx->p.C_T;
+  a.lambda1p = ctx->p.lambda1p;
+  a.eps = ctx->p.eps;
+  a.gamma = ctx->p.gamma;
+  a.cfl = ctx->p.cfl;
+  a.lam_gamma = ctx->p.lam_gamma;
+  a.guard_on = ctx->p.positivity_guard;
+  a.stage = stage;
+  a.dt_swap = dt_swap;
+  return a;
+}
+
+void enqueue_stage(cteno_ctx *ctx, int stage, int dt_swap, cudaStream_t s) {
+  const KArgs a = make_args(ctx, stage, dt_swap);
+  launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, ctx->p.scheme, a, ctx->recon_block, s);
+  launch_flux(ctx->d, ctx->fp32 ? 1 : 0, a, ctx->flux_block, s);
+}
+
+int check_built(cteno_ctx *ctx) {
+  if (!ctx) return CTENO_ERR_ARG;
+  if (!ctx->built) return fail(ctx, CTENO_ERR_STATE, "cteno_lsq_build has not run");
+  return CTENO_OK;
+}
+
+int check_mesh(cteno_ctx *ctx, int32_t mesh_id) {
+  if (mesh_id < 0 || mesh_id >= (int32_t)ctx->meshes.size())
+    return fail(ctx, CTENO_ERR_ARG, "mesh_id out of range");
+  return CTENO_OK;
+}
+
+int ensure_stage_buf(cteno_ctx *ctx, size_t count) {
+  if (count <= ctx->stage_cap) return CTENO_OK;
+  if (ctx->stage_buf) cudaFree(ctx->stage_buf);
+  ctx->stage_buf = nullptr;
+  ctx->stage_cap = 0;
+  CK(cudaMalloc(&ctx->stage_buf, count * sizeof(double)));
+  ctx->stage_cap = count;
+  return CTENO_OK;
+}
+
+int device_status(cteno_ctx *ctx) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (e & kErrNonFinite) return fail(ctx, CTENO_ERR_DEVICE, "a cell state became non-finite");
+  if (e & kErrRank) return fail(ctx, CTENO_ERR_RANK, "a central least-squares matrix is rank deficient");
+  return CTENO_OK;
+}
+
+void drop_graph(cteno_ctx *ctx) {
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->graph_exec = nullptr;
+  ctx->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cteno_default_params(cteno_params *p) {
+  if (!p) return;
+  p->dim = 2;
+  p->degree = 2;
+  p->scheme = CTENO_SCHEME_CTENO;
+  p->precision = CTENO_FP64;
+  p->lam_gamma = 1;
+  p->positivity_guard = 1;
+  p->C_T = 1e-6;
+  p->lambda1p = 1e15;
+  p->eps = 1e-40;
+  p->cfl = 0.5;
+  p->gamma = 1.4;
+}
+
+int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream) {
+  if (!out || !p) return CTENO_ERR_ARG;
+  *out = nullptr;
+  if ((p->dim != 2 && p->dim != 3) || (p->degree != 2 && p->degree != 3) ||
+      (p->scheme != 0 && p->scheme != 1) || (p->precision != 0 && p->precision != 1) ||
+      !(p->lambda1p > 1.0) || !(p->C_T >= 0.0 && p->C_T < 1.0) || !(p->eps >= 0.0) ||
+      !(p->cfl > 0.0) || !(p->gamma > 1.0))
+    return CTENO_ERR_ARG;
+  cteno_ctx *ctx = new (std::nothrow) cteno_ctx();
+  if (!ctx) return CTENO_ERR_NOMEM;
+  ctx->p = *p;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->d = p->dim;
+  ctx->nv = p->dim + 2;
+  ctx->nf = p->dim + 1;
+  ctx->nq = (p->dim == 2) ? 2 : 4;
+  ctx->nk = coeff_count(p->degree, p->dim) - 1;
+  ctx->M = 2 * coeff_count(p->degree, p->dim);
+  ctx->nd = 2 * p->dim;
+  ctx->fp32 = (p->precision == CTENO_MIXED);
+  build_tables(p->dim, p->degree, &ctx->tab);
+  *out = ctx;
+  return CTENO_OK;
+}
+
+int cteno_mesh_build(cteno_ctx *ctx, int64_t nverts, const double *xyz, int64_t ncells,
+                     const int32_t *cell_verts, const double *period, int boundary_kind,
+                     int32_t *mesh_id_out) {
+  if (!ctx) return CTENO_ERR_ARG;
+  if (ctx->stencils) return fail(ctx, CTENO_ERR_STATE, "meshes must be added before cteno_stencil_build");
+  if (!xyz || !cell_verts || nverts <= 0 || ncells <= 0 || ncells > INT32_MAX / 2 ||
+      boundary_kind != CTENO_BOUNDARY_TRANSMISSIVE)
+    return fail(ctx, CTENO_ERR_ARG, "invalid mesh arguments");
+  Mesh m;
+  int rc = ingest_mesh(ctx->d, nverts, xyz, ncells, cell_verts, period, &m, &ctx->err);
+  if (rc) return rc;
+  if (!ctx->meshes.empty())
+    for (int j = 0; j < 3; ++j)
+      if (ctx->meshes[0].period[j] != m.period[j])
+        return fail(ctx, CTENO_ERR_ARG, "all meshes of one context must have the same period");
+  ctx->meshes.push_back(std::move(m));
+  if (mesh_id_out) *mesh_id_out = (int32_t)ctx->meshes.size() - 1;
+  return CTENO_OK;
+}
+
+int cteno_stencil_build(cteno_ctx *ctx) {
+  if (!ctx) return CTENO_ERR_ARG;
+  if (ctx->meshes.empty()) return fail(ctx, CTENO_ERR_STATE, "no mesh");
+  if (ctx->stencils) return CTENO_OK;
+  int64_t off = 0;
+  for (auto &m : ctx->meshes) {
+    int rc = build_stencils(&m, ctx->p.degree, &ctx->err);
+    if (rc) return rc;
+    morton_order(&m);
+    m.offset = off;
+    off += m.ncells;
+  }
+  if (off > INT32_MAX) return fail(ctx, CTENO_ERR_ARG, "more than 2^31 cells in one context");
+  ctx->N = off;
+  ctx->stencils = true;
+  return CTENO_OK;
+}
+
+int cteno_lsq_build(cteno_ctx *ctx) {
+  if (!ctx) return CTENO_ERR_ARG;
+  if (!ctx->stencils) return fail(ctx, CTENO_ERR_STATE, "cteno_stencil_build has not run");
+  if (ctx->built) return CTENO_OK;
+  const int d = ctx->d, nvc = d + 1, nf = ctx->nf, M = ctx->M, nd = ctx->nd;
+  const int64_t N = ctx->N;
+  const int nmesh = (int)ctx->meshes.size();
+  const Tables &tab = ctx->tab;
+  // host arrays in device order
+  std::vector<double> hX((size_t)N * nvc * d);
+  std::vector<int32_t> hst((size_t)M * N), hnbr((size_t)nf * N);
+  std::vector<uint32_t> hinfo(N), hmeta(N);
+  std::vector<int64_t> hoff(nmesh + 1);
+  for (int k = 0; k < nmesh; ++k) {
+    const Mesh &m = ctx->meshes[k];
+    hoff[k] = m.offset;
+    hoff[k + 1] = m.offset + m.ncells;
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < m.ncells; ++r) {
+      const int64_t c = m.order[r], g = m.offset + r;
+      for (int t = 0; t < nvc * d; ++t) hX[g * nvc * d + t] = m.X[c * nvc * d + t];
+      // stencil: directional members face after face, then the remaining cells nearest first
+      bool used[kMaxM] = {};
+      int pos = 0;
+      uint32_t info = 0;
+      for (int f = 0; f < nf; ++f) {
+        int cnt = 0;
+        for (int j = 0; j < nd; ++j) {
+          const int8_t p = m.dirpos[(c * nf + f) * nd + j];
+          if (p < 0) continue;
+          hst[(size_t)pos++ * N + g] = (int32_t)(m.offset + m.rank[m.central[c * M + p]]);
+          used[p] = true;
+          ++cnt;
+        }
+        info |= (uint32_t)cnt << (4 * f);
+      }
+      for (int p = 0; p < M; ++p)
+        if (!used[p]) hst[(size_t)pos++ * N + g] = (int32_t)(m.offset + m.rank[m.central[c * M + p]]);
+      // canonical Gauss-point order of each face: permutation to sorted global vertex ids
+      for (int f = 0; f < nf; ++f) {
+        int slots[3], ns = 0;
+        for (int a = 0; a < nvc; ++a)
+          if (a != f) slots[ns++] = a;
+        int srt[3] = {0, 1, 2};  // face-vertex slots ordered by global vertex id
+        for (int x = 1; x < d; ++x)
+          for (int y = x; y > 0 && m.cv[c * nvc + slots[srt[y - 1]]] > m.cv[c * nvc + slots[srt[y]]]; --y)
+            std::swap(srt[y - 1], srt[y]);
+        int pidx = 0;
+        for (int pp = 0; pp < tab.nperm; ++pp) {
+          bool same = true;
+          for (int j = 0; j < d; ++j) same = same && (tab.perm_list[pp][j] == srt[j]);
+          if (same) pidx = pp;
+        }
+        info |= (uint32_t)pidx << (kInfoPermShift + 3 * f);
+      }
+      hinfo[g] = info;
+      uint32_t meta = 0;
+      for (int f = 0; f < nf; ++f) {
+        const int32_t nb = m.nbr[c * nf + f];
+        if (nb < 0) {
+          hnbr[(size_t)f * N + g] = -1;
+          meta |= 1u << (kMetaOwnerShift + f);
+        } else {
+          const int64_t gn = m.offset + m.rank[nb];
+          hnbr[(size_t)f * N + g] = (int32_t)gn;
+          meta |= (uint32_t)m.nbrf[c * nf + f] << (2 * f);
+          if (g < gn) meta |= 1u << (kMetaOwnerShift + f);
+        }
+      }
+      hmeta[g] = meta;
+    }
+  }
+  // device allocations
+  const size_t sT = ctx->fp32 ? sizeof(float) : sizeof(double);
+  double *dX = nullptr;
+  CK(cudaMalloc(&dX, hX.size() * sizeof(double)));
+  CK(dalloc(ctx, &ctx->d_tab, sizeof(DevTables)));
+  CK(dalloc(ctx, &ctx->d_mesh_off, sizeof(int64_t) * (nmesh + 1)));
+  CK(dalloc(ctx, &ctx->U, sizeof(double) * ctx->nv * N));
+  CK(dalloc(ctx, &ctx->Un, sizeof(double) * ctx->nv * N));
+  if (ctx->fp32) CK(dalloc(ctx, &ctx->U32, sizeof(float) * ctx->nv * N));
+  CK(dalloc(ctx, &ctx->st, sizeof(int32_t) * M * N));
+  CK(dalloc(ctx, &ctx->nbr, sizeof(int32_t) * nf * N));
+  CK(dalloc(ctx, &ctx->cinfo, sizeof(uint32_t) * N));
+  CK(dalloc(ctx, &ctx->fmeta, sizeof(uint32_t) * N));
+  CK(dalloc(ctx, &ctx->Pc, sT * ctx->nk * M * N));
+  CK(dalloc(ctx, &ctx->Pd, sT * nf * d * nd * N));
+  CK(dalloc(ctx, &ctx->Uf, sT * nf * ctx->nq * ctx->nv * N));
+  CK(dalloc(ctx, &ctx->fn, sizeof(double) * nf * d * N));
+  CK(dalloc(ctx, &ctx->fa, sizeof(double) * nf * N));
+  if (ctx->fp32) {
+    CK(dalloc(ctx, &ctx->fn32, sizeof(float) * nf * d * N));
+    CK(dalloc(ctx, &ctx->fa32, sizeof(float) * nf * N));
+  }
+  CK(dalloc(ctx, &ctx->vol, sizeof(double) * N));
+  CK(dalloc(ctx, &ctx->dt, sizeof(double) * 2 * nmesh));
+  CK(dalloc(ctx, &ctx->derr, sizeof(int)));
+  CK(dalloc(ctx, &ctx->guard, sizeof(unsigned long long)));
+  ctx->d_rank.resize(nmesh);
+  for (int k = 0; k < nmesh; ++k) {
+    CK(dalloc(ctx, &ctx->d_rank[k], sizeof(int32_t) * ctx->meshes[k].ncells));
+    CK(cudaMemcpyAsync(ctx->d_rank[k], ctx->meshes[k].rank.data(),
+                       sizeof(int32_t) * ctx->meshes[k].ncells, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  DevTables dt{};
+  dt.nk = tab.nk;
+  dt.nq = tab.nq;
+  dt.nperm = tab.nperm;
+  dt.nvq = tab.nvq;
+  std::memcpy(dt.ex, tab.ex, sizeof(dt.ex));
+  std::memcpy(dt.psibar, tab.psibar, sizeof(dt.psibar));
+  std::memcpy(dt.O, tab.O, sizeof(dt.O));
+  std::memcpy(dt.Phi, tab.Phi, sizeof(dt.Phi));
+  std::memcpy(dt.fw, tab.fw, sizeof(dt.fw));
+  std::memcpy(dt.vq, tab.vq, sizeof(dt.vq));
+  std::memcpy(dt.vw, tab.vw, sizeof(dt.vw));
+  CK(cudaMemcpyAsync(ctx->d_tab, &dt, sizeof(DevTables), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_mesh_off, hoff.data(), sizeof(int64_t) * (nmesh + 1), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(dX, hX.data(), hX.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->st, hst.data(), hst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->nbr, hnbr.data(), hnbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->cinfo, hinfo.data(), hinfo.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->fmeta, hmeta.data(), hmeta.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->guard, 0, sizeof(unsigned long long), ctx->stream));
+  CK(cudaMemsetAsync(ctx->U, 0, sizeof(double) * ctx->nv * N, ctx->stream));
+  SetupArgs s{};
+  s.N = N;
+  s.X = dX;
+  s.st = ctx->st;
+  s.cinfo = ctx->cinfo;
+  s.nbr = ctx->nbr;
+  s.fmeta = ctx->fmeta;
+  for (int j = 0; j < 3; ++j) s.period[j] = 0.0;
+  s.Pc = ctx->Pc;
+  s.Pd = ctx->Pd;
+  s.store_fp32 = ctx->fp32 ? 1 : 0;
+  s.fn = ctx->fn;
+  s.fa = ctx->fa;
+  s.vol = ctx->vol;
+  s.fn32 = ctx->fn32;
+  s.fa32 = ctx->fa32;
+  s.tab = ctx->d_tab;
+  s.err = ctx->derr;
+  for (int j = 0; j < 3; ++j) s.period[j] = ctx->meshes[0].period[j];  // shared by all meshes
+  launch_setup(d, ctx->p.degree, s, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  cudaFree(dX);
+  int rc = device_status(ctx);
+  if (rc) return rc;
+  ctx->h_cinfo.resize(N);
+  CK(cudaMemcpy(ctx->h_cinfo.data(), ctx->cinfo, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost));
+  int64_t ms = 0;
+  for (int64_t g = 0; g < N; ++g) {
+    const uint32_t info = ctx->h_cinfo[g];
+    for (int f = 0; f < nf; ++f)
+      if ((info >> (kInfoAdmShift + f)) & 1u) ms += (info >> (4 * f)) & 15u;
+  }
+  ctx->member_sum = ms;
+  CK(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+  ctx->built = true;
+  return CTENO_OK;
+}
+
+int cteno_set_state(cteno_ctx *ctx, int32_t mesh_id, const double *U, int is_device) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if ((rc = check_mesh(ctx, mesh_id))) return rc;
+  if (!U) return fail(ctx, CTENO_ERR_ARG, "null state");
+  const Mesh &m = ctx->meshes[mesh_id];
+  const size_t cnt = (size_t)ctx->nv * m.ncells;
+  const double *src = U;
+  if (!is_device) {
+    if ((rc = ensure_stage_buf(ctx, cnt))) return rc;
+    CK(cudaMemcpyAsync(ctx->stage_buf, U, cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    src = ctx->stage_buf;
+  }
+  launch_permute_in(ctx->nv, m.ncells, ctx->N, m.offset, ctx->d_rank[mesh_id], src, ctx->U, ctx->U32,
+                    ctx->stream);
+  KArgs a = make_args(ctx, 0, 0);
+  launch_dt(ctx->d, a, ctx->stream);
+  CK(cudaGetLastError());
+  return CTENO_OK;
+}
+
+int cteno_rk_stage(cteno_ctx *ctx, int stage, const double *dt) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (stage < 0 || stage > 2 || !dt) return fail(ctx, CTENO_ERR_ARG, "bad stage or dt");
+  CK(cudaMemcpyAsync(ctx->dt, dt, sizeof(double) * ctx->meshes.size(), cudaMemcpyHostToDevice, ctx->stream));
+  if (stage == 0) launch_dt_reset(make_args(ctx, 0, 0), ctx->stream);
+  enqueue_stage(ctx, stage, 0, ctx->stream);
+  CK(cudaGetLastError());
+  return CTENO_OK;
+}
+
+int cteno_run(cteno_ctx *ctx, int nsteps) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (nsteps < 0) return fail(ctx, CTENO_ERR_ARG, "nsteps < 0");
+  if (!ctx->graph_exec) {
+    CK(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+    if (ctx->timing) CK(cudaEventRecordWithFlags(ctx->tev[0], ctx->capture, cudaEventRecordExternal));
+    for (int s = 0; s < 3; ++s) {
+      const KArgs a = make_args(ctx, s, s == 0 ? 1 : 0);
+      launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, ctx->p.scheme, a, ctx->recon_block, ctx->capture);
+      if (ctx->timing) CK(cudaEventRecordWithFlags(ctx->tev[2 * s + 1], ctx->capture, cudaEventRecordExternal));
+      launch_flux(ctx->d, ctx->fp32 ? 1 : 0, a, ctx->flux_block, ctx->capture);
+      if (ctx->timing) CK(cudaEventRecordWithFlags(ctx->tev[2 * s + 2], ctx->capture, cudaEventRecordExternal));
+    }
+    cudaError_t e = cudaStreamEndCapture(ctx->capture, &ctx->graph);
+    if (e != cudaSuccess) return fail(ctx, CTENO_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    CK(cudaGraphInstantiate(&ctx->graph_exec, ctx->graph, 0));
+  }
+  for (int k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+  return CTENO_OK;
+}
+
+int cteno_get_state(cteno_ctx *ctx, int32_t mesh_id, double *U_out, int is_device) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if ((rc = check_mesh(ctx, mesh_id))) return rc;
+  if (!U_out) return fail(ctx, CTENO_ERR_ARG, "null output");
+  const Mesh &m = ctx->meshes[mesh_id];
+  const size_t cnt = (size_t)ctx->nv * m.ncells;
+  if (is_device) {
+    launch_permute_out(ctx->nv, m.ncells, ctx->N, m.offset, ctx->d_rank[mesh_id], ctx->U, U_out, ctx->stream);
+    CK(cudaGetLastError());
+    return CTENO_OK;
+  }
+  if ((rc = ensure_stage_buf(ctx, cnt))) return rc;
+  launch_permute_out(ctx->nv, m.ncells, ctx->N, m.offset, ctx->d_rank[mesh_id], ctx->U, ctx->stage_buf, ctx->stream);
+  CK(cudaMemcpyAsync(U_out, ctx->stage_buf, cnt * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return device_status(ctx);
+}
+
+int cteno_get_dt(cteno_ctx *ctx, double *dt_out) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (!dt_out) return fail(ctx, CTENO_ERR_ARG, "null output");
+  CK(cudaMemcpyAsync(dt_out, ctx->dt, sizeof(double) * ctx->meshes.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CTENO_OK;
+}
+
+int cteno_record_flags(cteno_ctx *ctx, int enable) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (enable && !ctx->flags) {
+    CK(dalloc(ctx, &ctx->flags, (size_t)ctx->nv * ctx->N));
+    CK(cudaMemsetAsync(ctx->flags, 0, (size_t)ctx->nv * ctx->N, ctx->stream));
+  }
+  if ((bool)enable != ctx->record_flags) drop_graph(ctx);
+  ctx->record_flags = enable != 0;
+  return CTENO_OK;
+}
+
+int cteno_get_flags(cteno_ctx *ctx, int32_t mesh_id, uint8_t *out) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if ((rc = check_mesh(ctx, mesh_id))) return rc;
+  if (!out) return fail(ctx, CTENO_ERR_ARG, "null output");
+  if (!ctx->flags) return fail(ctx, CTENO_ERR_STATE, "flag recording is off");
+  const Mesh &m = ctx->meshes[mesh_id];
+  const int64_t N = ctx->N;
+  std::vector<uint8_t> h((size_t)ctx->nv * m.ncells);
+  for (int v = 0; v < ctx->nv; ++v)
+    CK(cudaMemcpyAsync(h.data() + (size_t)v * m.ncells, ctx->flags + (size_t)v * N + m.offset, m.ncells,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int64_t c = 0; c < m.ncells; ++c)
+    for (int v = 0; v < ctx->nv; ++v) out[c * ctx->nv + v] = h[(size_t)v * m.ncells + m.rank[c]];
+  return CTENO_OK;
+}
+
+int cteno_get_face_states(cteno_ctx *ctx, int32_t mesh_id, double *out) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if ((rc = check_mesh(ctx, mesh_id))) return rc;
+  if (!out) return fail(ctx, CTENO_ERR_ARG, "null output");
+  const Mesh &m = ctx->meshes[mesh_id];
+  const int64_t N = ctx->N, n = m.ncells;
+  const int rows = ctx->nf * ctx->nq * ctx->nv;
+  const size_t sT = ctx->fp32 ? 4 : 8;
+  std::vector<unsigned char> h((size_t)rows * n * sT);
+  for (int r = 0; r < rows; ++r)
+    CK(cudaMemcpyAsync(h.data() + (size_t)r * n * sT, (const char *)ctx->Uf + ((size_t)r * N + m.offset) * sT,
+                       n * sT, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int64_t c = 0; c < n; ++c)
+    for (int r = 0; r < rows; ++r) {
+      const size_t idx = (size_t)r * n + m.rank[c];
+      out[c * rows + r] = ctx->fp32 ? (double)((const float *)h.data())[idx] : ((const double *)h.data())[idx];
+    }
+  return CTENO_OK;
+}
+
+int cteno_get_stencil(cteno_ctx *ctx, int32_t mesh_id, int64_t cell, int32_t *central, int32_t *dir,
+                      int32_t *dok) {
+  if (!ctx) return CTENO_ERR_ARG;
+  if (!ctx->stencils) return fail(ctx, CTENO_ERR_STATE, "cteno_stencil_build has not run");
+  int rc = check_mesh(ctx, mesh_id);
+  if (rc) return rc;
+  const Mesh &m = ctx->meshes[mesh_id];
+  if (cell < 0 || cell >= m.ncells || !central || !dir) return fail(ctx, CTENO_ERR_ARG, "bad cell");
+  const int nf = ctx->nf, nd = ctx->nd, M = ctx->M;
+  for (int p = 0; p < M; ++p) central[p] = m.central[cell * M + p];
+  for (int f = 0; f < nf; ++f)
+    for (int j = 0; j < nd; ++j) dir[f * nd + j] = m.dirpos[(cell * nf + f) * nd + j];
+  if (dok) {
+    if (!ctx->built) return fail(ctx, CTENO_ERR_STATE, "admissibility is known after cteno_lsq_build");
+    const uint32_t info = ctx->h_cinfo[m.offset + m.rank[cell]];
+    for (int f = 0; f < nf; ++f) dok[f] = (info >> (kInfoAdmShift + f)) & 1u;
+  }
+  return CTENO_OK;
+}
+
+int cteno_info(cteno_ctx *ctx, int32_t mesh_id, int64_t *out) {
+  if (!ctx || !out) return CTENO_ERR_ARG;
+  out[0] = (int64_t)ctx->meshes.size();
+  int64_t tot = 0;
+  for (auto &m : ctx->meshes) tot += m.ncells;
+  out[1] = tot;
+  out[2] = ctx->M;
+  out[3] = ctx->nk;
+  out[4] = ctx->nv;
+  out[5] = ctx->nf;
+  out[6] = ctx->nq;
+  out[7] = (mesh_id >= 0 && mesh_id < (int32_t)ctx->meshes.size()) ? ctx->meshes[mesh_id].ncells : 0;
+  return CTENO_OK;
+}
+
+int cteno_sync(cteno_ctx *ctx, int64_t *guard_count) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  unsigned long long g = 0;
+  CK(cudaMemcpyAsync(&g, ctx->guard, sizeof(g), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemsetAsync(ctx->guard, 0, sizeof(g), ctx->stream));
+  rc = device_status(ctx);
+  if (guard_count) *guard_count = (int64_t)g;
+  return rc;
+}
+
+int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
+  if (!ctx) return CTENO_ERR_ARG;
+  auto ok = [](int b) { return b == 0 || (b >= 32 && b <= 256 && b % 32 == 0); };
+  if (!ok(recon_block) || !ok(flux_block)) return fail(ctx, CTENO_ERR_ARG, "block size must be a multiple of 32 in [32, 256]");
+  if (recon_block) ctx->recon_block = recon_block;
+  if (flux_block) ctx->flux_block = flux_block;
+  drop_graph(ctx);
+  return CTENO_OK;
+}
+
+int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  const size_t cnt = (size_t)ctx->nv * ctx->N;
+  const size_t nm = ctx->meshes.size();
+  // backup: U (FP64), the FP32 shadow and the time steps
+  const size_t bytes = cnt * sizeof(double) + cnt * sizeof(float) + 2 * nm * sizeof(double);
+  if (!ctx->backup) CK(cudaMalloc(&ctx->backup, bytes));
+  double *bU = ctx->backup, *bdt = ctx->backup + cnt;
+  float *b32 = (float *)(bdt + 2 * nm);
+  auto save_restore = [&](bool save) -> cudaError_t {
+    cudaError_t e;
+    e = cudaMemcpyAsync(save ? bU : ctx->U, save ? ctx->U : bU, cnt * sizeof(double),
+                        cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return e;
+    if (ctx->U32) {
+      e = cudaMemcpyAsync(save ? b32 : ctx->U32, save ? ctx->U32 : b32, cnt * sizeof(float),
+                          cudaMemcpyDeviceToDevice, ctx->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaMemcpyAsync(save ? bdt : ctx->dt, save ? ctx->dt : bdt, 2 * nm * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ctx->stream);
+  };
+  CK(save_restore(true));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int cand[] = {64, 128, 256};
+  const int reps = 5;
+  float best_r = 1e30f, best_f = 1e30f;
+  int br = ctx->recon_block, bf = ctx->flux_block;
+  const KArgs a = make_args(ctx, 1, 0);  // stage 1: reads U^n, writes U only
+  for (int b : cand) {  // the reconstruction writes only face states: no restore needed
+    launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, b, ctx->stream);
+    CK(cudaEventRecord(e0, ctx->stream));
+    for (int r = 0; r < reps; ++r) launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, b, ctx->stream);
+    CK(cudaEventRecord(e1, ctx->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_r) best_r = ms, br = b;
+  }
+  for (int b : cand) {
+    float tot = 0;
+    for (int r = 0; r < reps; ++r) {
+      CK(save_restore(false));
+      CK(cudaEventRecord(e0, ctx->stream));
+      launch_flux(ctx->d, ctx->fp32, a, b, ctx->stream);
+      CK(cudaEventRecord(e1, ctx->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      tot += ms;
+    }
+    if (tot < best_f) best_f = tot, bf = b;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(save_restore(false));
+  ctx->recon_block = br;
+  ctx->flux_block = bf;
+  drop_graph(ctx);
+  if (best_out) {
+    best_out[0] = br;
+    best_out[1] = bf;
+  }
+  return device_status(ctx);
+}
+
+int cteno_kernel_stats(cteno_ctx *ctx, double *out) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (!out) return fail(ctx, CTENO_ERR_ARG, "null output");
+  const double N = (double)ctx->N, s = ctx->fp32 ? 4.0 : 8.0;
+  const int nk = ctx->nk, M = ctx->M, nv = ctx->nv, nf = ctx->nf, nq = ctx->nq, d = ctx->d;
+  const double members = (double)ctx->member_sum;
+  // reconstruction: pseudo-inverses, stencil ids, cell info, own means, face-state writes
+  // (neighbour means are re-reads of data counted once as "own means")
+  out[0] = N * (nk * M * s + M * 4.0 + 4.0 + nv * s + nf * nq * nv * s) + members * d * s +
+           (ctx->record_flags ? N * nv : 0.0);
+  // flux/update: face states (each read by both of its cells, counted once), neighbour ids,
+  // face meta, normals and areas, volume, U, U^n and the shadow
+  out[1] = N * (nf * nq * nv * s + nf * 4.0 + 4.0 + nf * d * s + nf * s + 8.0 + 3 * nv * 8.0 +
+                (ctx->fp32 ? 2 * nv * 4.0 : 0.0));
+  // FLOPs: central and directional products, p_1, SI, selection (~30 per stencil), face values
+  const double st = 1.0 + (N > 0 ? members / N / d : 0.0);
+  out[2] = N * (2.0 * nk * M * nv + 2.0 * nv * (nk * nk + nk) + nv * 30.0 * st + 2.0 * nv * nf * nq * nk) +
+           members * 2.0 * d * nv;
+  // HLLC ~ 90 + 20 d operations per Gauss point, plus accumulation and the update
+  out[3] = N * (nf * nq * (90.0 + 20.0 * d + 3.0 * nv) + 6.0 * nv);
+  return CTENO_OK;
+}
+
+int cteno_profile_step(cteno_ctx *ctx, int nsteps, double *ms_out) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (!ms_out || nsteps <= 0) return fail(ctx, CTENO_ERR_ARG, "bad arguments");
+  cudaEvent_t ev[7];
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  double tr = 0.0, tf = 0.0;
+  for (int k = 0; k < nsteps; ++k) {
+    for (int s = 0; s < 3; ++s) {
+      const KArgs a = make_args(ctx, s, s == 0 ? 1 : 0);
+      CK(cudaEventRecord(ev[2 * s], ctx->stream));
+      launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, ctx->recon_block, ctx->stream);
+      CK(cudaEventRecord(ev[2 * s + 1], ctx->stream));
+      launch_flux(ctx->d, ctx->fp32, a, ctx->flux_block, ctx->stream);
+    }
+    CK(cudaEventRecord(ev[6], ctx->stream));
+    CK(cudaEventSynchronize(ev[6]));
+    for (int s = 0; s < 3; ++s) {
+      float a = 0, b = 0;
+      CK(cudaEventElapsedTime(&a, ev[2 * s], ev[2 * s + 1]));
+      CK(cudaEventElapsedTime(&b, ev[2 * s + 1], (s < 2) ? ev[2 * s + 2] : ev[6]));
+      tr += a;
+      tf += b;
+    }
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  ms_out[0] = tr / nsteps;
+  ms_out[1] = tf / nsteps;
+  return device_status(ctx);
+}
+
+int cteno_set_timing(cteno_ctx *ctx, int enable) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (enable && !ctx->tev[0])
+    for (auto &e : ctx->tev) CK(cudaEventCreate(&e));
+  if ((bool)enable != ctx->timing) drop_graph(ctx);
+  ctx->timing = enable != 0;
+  return CTENO_OK;
+}
+
+int cteno_last_kernel_ms(cteno_ctx *ctx, double *ms_out) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (!ms_out) return fail(ctx, CTENO_ERR_ARG, "null output");
+  if (!ctx->timing || !ctx->graph_exec) return fail(ctx, CTENO_ERR_STATE, "timing is off or no step has run");
+  CK(cudaEventSynchronize(ctx->tev[6]));
+  double r = 0.0, f = 0.0;
+  for (int s = 0; s < 3; ++s) {
+    float a = 0, b = 0;
+    CK(cudaEventElapsedTime(&a, ctx->tev[2 * s], ctx->tev[2 * s + 1]));
+    CK(cudaEventElapsedTime(&b, ctx->tev[2 * s + 1], ctx->tev[2 * s + 2]));
+    r += a;
+    f += b;
+  }
+  ms_out[0] = r;
+  ms_out[1] = f;
+  return CTENO_OK;
+}
+
+const char *cteno_last_error(cteno_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void cteno_destroy(cteno_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->stream || ctx->built) cudaStreamSynchronize(ctx->stream);
+  drop_graph(ctx);
+  for (void *p : ctx->allocations) cudaFree(p);
+  if (ctx->stage_buf) cudaFree(ctx->stage_buf);
+  if (ctx->backup) cudaFree(ctx->backup);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  for (auto &e : ctx->tev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry point of
+include/cteno.h, validates its arguments, and its host-side stencil search (integer results)
+agrees exactly with the oracle's."""
+from __future__ import annotations
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cteno.h")
+
+
+def _lib():
+    from paper_2312_17042_gb300 import build, native
+    build.build()
+    return native
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cteno_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    native = _lib()
+    lib = native.load_library()
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_parameter_validation_without_gpu():
+    native = _lib()
+    p = native.cteno_default_params()
+    assert (p.dim, p.degree, p.C_T, p.lambda1p, p.eps) == (2, 2, 1e-6, 1e15, 1e-40)
+    p.degree = 5
+    with pytest.raises(native.CtenoError):
+        native.cteno_create(p)
+    p = native.cteno_default_params()
+    ctx = native.cteno_create(p)
+    # rk_stage before lsq_build is an ordering error, not a crash
+    with pytest.raises(native.CtenoError) as e:
+        native.cteno_rk_stage(ctx, 0, [1e-3])
+    assert e.value.code == -2
+    # degenerate cell
+    xyz = np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0]])
+    with pytest.raises(native.CtenoError) as e:
+        native.cteno_mesh_build(ctx, xyz, np.array([[0, 1, 2]]))
+    assert e.value.code == -3
+    # mesh too small for M = 12
+    m = W.tri_mesh(2, 2, periodic=False)
+    native.cteno_mesh_build(ctx, m.xyz, m.cells, m.period)
+    with pytest.raises(native.CtenoError) as e:
+        native.cteno_stencil_build(ctx)
+    assert e.value.code == -4
+    native.cteno_destroy(ctx)
+
+
+@pytest.mark.parametrize("mesh,degree", [
+    (W.tri_mesh(12, 12, periodic=True, seed=1), 2),
+    (W.tri_mesh(14, 9, periodic=False, seed=2), 3),
+    (W.tet_mesh(6, periodic=True, seed=3), 2),
+    (W.tet_mesh(5, periodic=False, seed=4), 3),
+], ids=["tri-per-r2", "tri-r3", "tet-per-r2", "tet-r3"])
+def test_host_stencils_match_oracle_exactly(mesh, degree):
+    """Central stencils (ids, nearest-first order) and directional member positions are integer
+    results of the same readings, computed independently: they must agree exactly."""
+    native = _lib()
+    from oracle import Oracle
+    o = Oracle(mesh, degree=degree)
+    p = native.cteno_default_params()
+    p.dim, p.degree = mesh.dim, degree
+    ctx = native.cteno_create(p)
+    mid = native.cteno_mesh_build(ctx, mesh.xyz, mesh.cells, mesh.period)
+    native.cteno_stencil_build(ctx)
+    for i in range(mesh.ncells):
+        c_lib, d_lib, _ = native.cteno_get_stencil(ctx, mid, i, with_admissibility=False)
+        c_orc, d_orc, _ = o.stencil(i)
+        assert np.array_equal(c_lib, c_orc), i
+        assert np.array_equal(d_lib, d_orc), i
+    native.cteno_destroy(ctx)

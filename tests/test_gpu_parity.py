@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle on the same
+seeded inputs.
+
+Tolerances: the FP64 path must match the oracle to max relative 1e-12 (per state component,
+relative to the component's max magnitude) after 10 steps; reconstructed face states of one stage
+to 1e-12; selection flags exactly. The mixed path (FP32 reconstruction and flux, FP64
+accumulation) keeps flags equal except where the oracle's indicator ratio is within 1e-4 of the
+cut-off, and its L1 density error within 1.05x of the FP64 path's on smooth problems.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def _native():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_17042_gb300 import build, native
+    build.build()
+    return native
+
+
+def _solver(native, meshes, dim, **kw):
+    import torch
+    return native.Solver(meshes, dim, stream=torch.cuda.current_stream().cuda_stream, **kw)
+
+
+def _relerr(a, b):
+    scale = np.maximum(np.abs(b).max(axis=-1, keepdims=True), 1e-300)
+    return float((np.abs(a - b) / scale).max())
+
+
+CASES = [
+    ("tri-per-r2", lambda: W.density_wave_2d(16), 2),
+    ("tri-r3", lambda: W.shock_tube_2d(24, 8), 3),
+    ("tri-r2-sod", lambda: W.shock_tube_2d(32, 8), 2),
+    ("tet-per-r2", lambda: W.density_wave_3d(6), 2),
+    ("tet-r3", lambda: W.blast_3d(5), 3),
+]
+
+
+@pytest.mark.parametrize("scheme", [0, 1], ids=["CTENO", "CTENOZ"])
+@pytest.mark.parametrize("name,make,degree", CASES, ids=[c[0] for c in CASES])
+def test_one_stage_face_states_flags_and_update(name, make, degree, scheme):
+    native = _native()
+    from oracle import Oracle
+    wl = make()
+    d = wl.mesh.dim
+    o = Oracle(wl.mesh, degree=degree, scheme=scheme)
+    o.set_state(wl.U0)
+    dt = 0.5 * o.dt()
+    s = _solver(native, [wl.mesh], d, degree=degree, scheme=scheme)
+    native.cteno_record_flags(s.ctx, True)
+    s.set_state(wl.U0)
+    s.stage(0, dt)
+    fs_gpu = native.cteno_get_face_states(s.ctx, 0)
+    fl_gpu = native.cteno_get_flags(s.ctx, 0)
+    U_gpu = s.get_state()
+    o.stage(0, dt)
+    fs_orc = o.face_states()
+    assert _relerr(fs_gpu.reshape(-1, d + 2).T, fs_orc.reshape(-1, d + 2).T) < FP64_TOL
+    assert np.array_equal(fl_gpu, o.flags())
+    assert _relerr(U_gpu, o.get_state()) < FP64_TOL
+    # admissibility of the directional stencils agrees
+    for i in range(0, wl.mesh.ncells, 17):
+        _, _, dok = native.cteno_get_stencil(s.ctx, 0, i)
+        _, _, dok_o = o.stencil(i)
+        assert np.array_equal(dok, dok_o)
+    s.close()
+
+
+def test_density_wave_10_steps_fp64_matches_oracle():
+    """32x32 periodic square, 2048 triangles, CTENO degree 2, CFL 0.5, 10 steps, FP64."""
+    native = _native()
+    from oracle import Oracle
+    wl = W.density_wave_2d(32)
+    o = Oracle(wl.mesh, degree=2, scheme=0, cfl=0.5)
+    o.set_state(wl.U0)
+    dts = o.run(10)
+    s = _solver(native, [wl.mesh], 2, degree=2, scheme=0, cfl=0.5)
+    s.set_state(wl.U0)
+    s.run(10)
+    U = s.get_state()
+    assert abs(s.dt()[0] - dts[-1]) < 1e-14 * dts[-1]
+    assert _relerr(U, o.get_state()) < FP64_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("scheme,degree", [(0, 2), (1, 2), (0, 3), (1, 3)])
+def test_shock_tube_fp64_matches_oracle(scheme, degree):
+    """Sod states on a reduced copy of the 512x128 shock-tube mesh (same construction), CFL 0.4,
+    10 steps."""
+    native = _native()
+    from oracle import Oracle
+    wl = W.shock_tube_2d(64, 16)
+    o = Oracle(wl.mesh, degree=degree, scheme=scheme, cfl=0.4)
+    o.set_state(wl.U0)
+    o.run(10)
+    s = _solver(native, [wl.mesh], 2, degree=degree, scheme=scheme, cfl=0.4)
+    s.set_state(wl.U0)
+    s.run(10)
+    assert _relerr(s.get_state(), o.get_state()) < FP64_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_periodic_conservation(precision):
+    """Both cells of a face evaluate the flux with identical operands: sum |V| U is conserved to
+    the rounding of the final sum."""
+    native = _native()
+    wl = W.density_wave_2d(24)
+    s = _solver(native, [wl.mesh], 2, degree=2, scheme=1, precision=precision)
+    s.set_state(wl.U0)
+    s.run(20)
+    vol = W.cell_volumes(wl.mesh)
+    before, after = wl.U0 @ vol, s.get_state() @ vol
+    assert np.all(np.abs(after - before) <= 1e-13 * np.abs(before).max())
+    s.close()
+
+
+def test_free_stream_gpu():
+    native = _native()
+    for mesh in (W.tri_mesh(10, 10, periodic=False), W.tet_mesh(5, periodic=True)):
+        d = mesh.dim
+        U = W.uniform_state(mesh, [1.3] + [0.7, -0.4, 0.2][:d] + [2.1])
+        for precision in (0, 1):
+            s = _solver(native, [mesh], d, degree=2, precision=precision)
+            s.set_state(U)
+            s.run(3)
+            tol = 1e-13 if precision == 0 else 1e-6
+            assert np.abs(s.get_state() - U).max() < tol * np.abs(U).max()
+            s.close()
+
+
+def test_batched_meshes_match_independent_oracles():
+    """Several independent meshes of uneven size in one context: each equals its own oracle."""
+    native = _native()
+    from oracle import Oracle
+    wls = W.quadrants_batch(n_meshes=4, seed=3, nmin=8, nmax=20)
+    s = _solver(native, [w.mesh for w in wls], 2, degree=2, scheme=1, cfl=0.4)
+    for k, w in enumerate(wls):
+        s.set_state(w.U0, k)
+    s.run(5)
+    dts = s.dt()
+    for k, w in enumerate(wls):
+        o = Oracle(w.mesh, degree=2, scheme=1, cfl=0.4)
+        o.set_state(w.U0)
+        d_o = o.run(5)
+        assert abs(dts[k] - d_o[-1]) < 1e-13 * d_o[-1]
+        assert _relerr(s.get_state(k), o.get_state()) < FP64_TOL
+    s.close()
+
+
+def test_mixed_precision_flags_and_accuracy_on_density_wave():
+    """Mixed path on the smooth 2D wave: L1 density error within 1.05x of the FP64 path, and the
+    selection flags equal the FP64 oracle's."""
+    native = _native()
+    from oracle import Oracle
+    wl = W.density_wave_2d(32)
+    T = 0.05
+    errs = {}
+    for precision in (0, 1):
+        s = _solver(native, [wl.mesh], 2, degree=2, precision=precision, cfl=0.5)
+        s.set_state(wl.U0)
+        o = Oracle(wl.mesh, degree=2)
+        o.set_state(wl.U0)
+        nst = int(np.ceil(T / o.dt()))
+        for _ in range(nst):
+            s.step(T / nst)
+        vol = W.cell_volumes(wl.mesh)
+        errs[precision] = np.sum(vol * np.abs(s.get_state()[0] - wl.exact(T)[0])) / vol.sum()
+        s.close()
+    assert errs[1] <= 1.05 * errs[0], errs
+    # flags of one reconstruction from the same state
+    o = Oracle(wl.mesh, degree=2)
+    o.set_state(wl.U0)
+    o.residual()
+    s = _solver(native, [wl.mesh], 2, degree=2, precision=1)
+    native.cteno_record_flags(s.ctx, True)
+    s.set_state(wl.U0)
+    s.stage(0, 1e-4)
+    assert np.array_equal(native.cteno_get_flags(s.ctx, 0), o.flags())
+    s.close()
+
+
+@pytest.mark.parametrize("scheme", [0, 1], ids=["CTENO", "CTENOZ"])
+def test_mixed_precision_flags_at_shocks(scheme):
+    """Sod: mixed-path flags equal the oracle's except where the oracle's chi_1 lies within 1e-4
+    (relative) of the cut-off."""
+    native = _native()
+    from oracle import Oracle
+    wl = W.shock_tube_2d(64, 16)
+    o = Oracle(wl.mesh, degree=2, scheme=scheme)
+    o.set_state(wl.U0)
+    o.run(5)
+    U = o.get_state()
+    o.residual()
+    s = _solver(native, [wl.mesh], 2, degree=2, scheme=scheme, precision=1)
+    native.cteno_record_flags(s.ctx, True)
+    s.set_state(U)
+    s.stage(0, 1e-5)
+    fl = native.cteno_get_flags(s.ctx, 0)
+    ref = o.flags()
+    diff = fl != ref
+    if diff.any():
+        near = _near_cutoff(o, scheme)
+        assert not (diff & ~near).any(), np.argwhere(diff & ~near)[:10]
+    s.close()
+
+
+def _near_cutoff(o, scheme, rel=1e-4):
+    """Cells/variables where some chi_s of the oracle is within rel of C_T."""
+    SI = o.smoothness_indicators()
+    mask = o.stencil_mask()
+    out = np.zeros(SI.shape[:2], bool)
+    C_T, eps = o.p["C_T"], o.p["eps"]
+    lam1 = 1 - 1 / o.p["lambda1p"]
+    for i in range(SI.shape[0]):
+        adm = [0] + [1 + f for f in range(o.nf) if mask[i] >> (1 + f) & 1]
+        st = len(adm)
+        lams = (1 - lam1) / (st - 1) if st > 1 else 0.0
+        for v in range(SI.shape[1]):
+            si = SI[i, v, adm]
+            if scheme == 0:
+                g = 1.0 / (si + eps) ** 6
+            else:
+                tau = (np.abs(si[1:] - si[0]).sum() / (st - 1)) ** 6 if st > 1 else 0.0
+                g = 1 + tau / (si + eps)
+            g = g * np.array([lam1] + [lams] * (st - 1))
+            chi = g / g.sum()
+            out[i, v] = np.any(np.abs(chi - C_T) <= rel * C_T)
+    return out
+
+
+def test_full_size_shock_tube_sampled_residual():
+    """512x128 shock tube (131072 cells), the launch configuration the benchmark times: one
+    FP64 stage on the GPU against the oracle's residual at sampled cells near the discontinuity
+    and elsewhere."""
+    native = _native()
+    from oracle import Oracle
+    wl = W.shock_tube_2d(512, 128)
+    for scheme, degree in ((0, 2), (1, 3)):
+        s = _solver(native, [wl.mesh], 2, degree=degree, scheme=scheme, cfl=0.4)
+        s.set_state(wl.U0)
+        dt = 1e-4
+        s.stage(0, dt)
+        R_gpu = (s.get_state() - wl.U0) / dt
+        o = Oracle(wl.mesh, setup=False, degree=degree, scheme=scheme)
+        o.set_state(wl.U0)
+        cen = W.cell_centroids(wl.mesh)
+        rng = np.random.default_rng(5)
+        near = np.where(np.abs(cen[:, 0] - 0.5) < 0.01)[0]
+        ids = np.concatenate([rng.choice(near, 40, replace=False),
+                              rng.choice(wl.mesh.ncells, 40, replace=False)])
+        R_orc = o.residual_cells(ids)
+        scale = np.abs(R_orc).max(axis=0) + 1e-300
+        assert (np.abs(R_gpu[:, ids].T - R_orc) / scale).max() < 1e-11
+        s.close()
+
+
+def test_rejects_bad_calls_without_faulting():
+    native = _native()
+    wl = W.density_wave_2d(8)
+    s = _solver(native, [wl.mesh], 2)
+    with pytest.raises(native.CtenoError):
+        native.cteno_set_state(s.ctx, 3, wl.U0)          # no such mesh
+    with pytest.raises(native.CtenoError):
+        native.cteno_rk_stage(s.ctx, 5, [1e-3])          # no such stage
+    with pytest.raises(native.CtenoError):
+        native.cteno_set_launch(s.ctx, 100, 0)           # not a multiple of 32
+    s.set_state(wl.U0)
+    s.run(1)
+    assert s.sync() == 0
+    s.close()
