@@ -320,7 +320,7 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   CK(dalloc(ctx, &ctx->d_mesh_off, sizeof(int64_t) * (nmesh + 1)));
   CK(dalloc(ctx, &ctx->U, sizeof(double) * ctx->nv * N));
   CK(dalloc(ctx, &ctx->Un, sizeof(double) * ctx->nv * N));
-  if (ctx->fp32) CK(dalloc(ctx, &ctx->U32, sizeof(float) * ctx->nv * N));
+  if (ctx->fp32) CK(dalloc(ctx, &ctx->U32, 2 * sizeof(float) * ctx->nv * N));
   CK(dalloc(ctx, &ctx->st, sizeof(int32_t) * M * N));
   CK(dalloc(ctx, &ctx->nbr, sizeof(int32_t) * nf * N));
   CK(dalloc(ctx, &ctx->cinfo, sizeof(uint32_t) * N));
@@ -600,7 +600,7 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
   const size_t cnt = (size_t)ctx->nv * ctx->N;
   const size_t nm = ctx->meshes.size();
   // backup: U (FP64), the FP32 shadow and the time steps
-  const size_t bytes = cnt * sizeof(double) + cnt * sizeof(float) + 2 * nm * sizeof(double);
+  const size_t bytes = cnt * sizeof(double) + 2 * cnt * sizeof(float) + 2 * nm * sizeof(double);
   if (!ctx->backup) CK(cudaMalloc(&ctx->backup, bytes));
   double *bU = ctx->backup, *bdt = ctx->backup + cnt;
   float *b32 = (float *)(bdt + 2 * nm);
@@ -610,7 +610,7 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
                         cudaMemcpyDeviceToDevice, ctx->stream);
     if (e != cudaSuccess) return e;
     if (ctx->U32) {
-      e = cudaMemcpyAsync(save ? b32 : ctx->U32, save ? ctx->U32 : b32, cnt * sizeof(float),
+      e = cudaMemcpyAsync(save ? b32 : ctx->U32, save ? ctx->U32 : b32, 2 * cnt * sizeof(float),
                           cudaMemcpyDeviceToDevice, ctx->stream);
       if (e != cudaSuccess) return e;
     }
@@ -672,12 +672,12 @@ int cteno_kernel_stats(cteno_ctx *ctx, double *out) {
   const double members = (double)ctx->member_sum;
   // reconstruction: pseudo-inverses, stencil ids, cell info, own means, face-state writes
   // (neighbour means are re-reads of data counted once as "own means")
-  out[0] = N * (nk * M * s + M * 4.0 + 4.0 + nv * s + nf * nq * nv * s) + members * d * s +
+  out[0] = N * (nk * M * s + M * 4.0 + 4.0 + nv * 8.0 + nf * nq * nv * s) + members * d * s +
            (ctx->record_flags ? N * nv : 0.0);
   // flux/update: face states (each read by both of its cells, counted once), neighbour ids,
   // face meta, normals and areas, volume, U, U^n and the shadow
   out[1] = N * (nf * nq * nv * s + nf * 4.0 + 4.0 + nf * d * s + nf * s + 8.0 + 3 * nv * 8.0 +
-                (ctx->fp32 ? 2 * nv * 4.0 : 0.0));
+                (ctx->fp32 ? 2 * nv * 8.0 : 0.0));
   // FLOPs: central and directional products, p_1, SI, selection (~30 per stencil), face values
   const double st = 1.0 + (N > 0 ? members / N / d : 0.0);
   out[2] = N * (2.0 * nk * M * nv + 2.0 * nv * (nk * nk + nk) + nv * 30.0 * st + 2.0 * nv * nf * nq * nk) +

@@ -46,7 +46,7 @@ struct KArgs {
   // state
   double *U;                // [nv][N] FP64 cell means of the current stage
   double *Un;               // [nv][N] U^n, start of the step
-  float *U32;               // [nv][N] FP32 shadow of U (mixed path)
+  float *U32;               // [nv][N] float2 (hi, lo) split of U: hi = fl32(U), lo = fl32(U - hi)
   // stencils and least-squares operators
   const int32_t *st;        // [M][N] device stencil ids (directional members first)
   const uint32_t *cinfo;    // [N]

@@ -124,12 +124,18 @@ __global__ void __launch_bounds__(256) flux_kernel(const KArgs a) {
   const T *__restrict__ Uf = (const T *)a.Uf;
   const T *__restrict__ fnT = (sizeof(T) == 4) ? (const T *)a.fn32 : (const T *)a.fn;
   const T *__restrict__ faT = (sizeof(T) == 4) ? (const T *)a.fa32 : (const T *)a.fa;
-  const T *__restrict__ Ut = (sizeof(T) == 4) ? (const T *)a.U32 : (const T *)a.U;
   const T g = (T)a.gamma;
   const uint32_t meta = a.fmeta[i];
-  T Ui[NV];
+  T Ui[NV];  // cell mean, the outside state of a transmissive face
 #pragma unroll
-  for (int v = 0; v < NV; ++v) Ui[v] = Ut[v * N + i];
+  for (int v = 0; v < NV; ++v) {
+    if constexpr (sizeof(T) == 4) {
+      const float2 h = ((const float2 *)a.U32)[v * N + i];
+      Ui[v] = h.x + h.y;
+    } else {
+      Ui[v] = a.U[v * N + i];
+    }
+  }
   double acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
@@ -180,7 +186,10 @@ __global__ void __launch_bounds__(256) flux_kernel(const KArgs a) {
     un[v] = res;
     finite = finite && isfinite(res);
     a.U[v * N + i] = res;
-    if (a.U32) a.U32[v * N + i] = (float)res;
+    if (a.U32) {
+      const float hi = (float)res;
+      ((float2 *)a.U32)[v * N + i] = make_float2(hi, (float)(res - (double)hi));
+    }
   }
   if (!finite) atomicOr(a.err, kErrNonFinite);
   if (a.stage == 2 && finite) atomic_min_pos(&a.dt[a.nmesh + mesh], a.cfl * local_dt<D>(a, i, un));
@@ -211,7 +220,10 @@ __global__ void permute_in_kernel(int nv, int64_t n, int64_t N, int64_t off, con
   for (int v = 0; v < nv; ++v) {
     const double x = src[v * n + c];
     U[v * N + g] = x;
-    if (U32) U32[v * N + g] = (float)x;
+    if (U32) {
+      const float hi = (float)x;
+      ((float2 *)U32)[v * N + g] = make_float2(hi, (float)(x - (double)hi));
+    }
   }
 }
 

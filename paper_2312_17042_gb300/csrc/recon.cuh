@@ -116,14 +116,38 @@ __global__ void __launch_bounds__(256) recon_kernel(const KArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
 
-  const T *__restrict__ Ut = (sizeof(T) == 4) ? (const T *)a.U32 : (const T *)a.U;
+  // cell means: FP64 directly, or (mixed path) the FP32 pair hi + lo of every FP64 value, so
+  // that U_m - U_0 = (hi_m - hi_0) + (lo_m - lo_0) keeps FP64 accuracy in FP32 arithmetic
+  const double *__restrict__ U64 = a.U;
+  const float2 *__restrict__ U2 = (const float2 *)a.U32;
   const T *__restrict__ Pc = (const T *)a.Pc;
   const T *__restrict__ Pd = (const T *)a.Pd;
   const int32_t *__restrict__ st = a.st;
 
   T U0[NV];
+  float L0[NV];  // low parts (mixed path)
 #pragma unroll
-  for (int v = 0; v < NV; ++v) U0[v] = Ut[v * N + i];
+  for (int v = 0; v < NV; ++v) {
+    if constexpr (sizeof(T) == 4) {
+      const float2 h = U2[v * N + i];
+      U0[v] = (T)h.x;
+      L0[v] = h.y;
+    } else {
+      U0[v] = (T)U64[v * N + i];
+      L0[v] = 0.0f;
+    }
+  }
+  auto delta = [&](int64_t j, T *du) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if constexpr (sizeof(T) == 4) {
+        const float2 h = U2[v * N + j];
+        du[v] = (T)((h.x - (float)U0[v]) + (h.y - L0[v]));
+      } else {
+        du[v] = (T)(U64[v * N + j] - (double)U0[v]);
+      }
+    }
+  };
 
   // 1-2: central coefficients a_opt = P_c (U_m - U_0)
   T ao[NK][NV];
@@ -135,8 +159,7 @@ __global__ void __launch_bounds__(256) recon_kernel(const KArgs a) {
   for (int m = 0; m < M; ++m) {
     const int64_t j = st[m * N + i];
     T du[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) du[v] = Ut[v * N + j] - U0[v];
+    delta(j, du);
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
       const T p = Pc[((int64_t)k * M + m) * N + i];
@@ -165,8 +188,7 @@ __global__ void __launch_bounds__(256) recon_kernel(const KArgs a) {
         if (jj < nm) {
           const int64_t j = st[(int64_t)(off + jj) * N + i];
           T du[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) du[v] = Ut[v * N + j] - U0[v];
+          delta(j, du);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             const T p = Pd[((int64_t)(f * D + k) * ND + jj) * N + i];
@@ -280,9 +302,10 @@ __global__ void __launch_bounds__(256) recon_kernel(const KArgs a) {
       const T *ph = &sPhi[((f * NP + p) * NQ) * NK];
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
-        T val = U0[v];
+        T val = (T)L0[v];
 #pragma unroll
         for (int k = 0; k < NK; ++k) val += ph[q * NK + k] * af[k];
+        val += U0[v];
         Uf[((int64_t)(f * NQ + q) * NV + v) * N + i] = val;
       }
     }
@@ -311,7 +334,7 @@ __global__ void __launch_bounds__(256) recon_kernel(const KArgs a) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
-          for (int v = 0; v < NV; ++v) Uf[((int64_t)(f * NQ + q) * NV + v) * N + i] = U0[v];
+          for (int v = 0; v < NV; ++v) Uf[((int64_t)(f * NQ + q) * NV + v) * N + i] = U0[v] + (T)L0[v];
       atomicAdd(a.guard, 1ull);
     }
   }

@@ -4,8 +4,15 @@ seeded inputs.
 Tolerances: the FP64 path must match the oracle to max relative 1e-12 (per state component,
 relative to the component's max magnitude) after 10 steps; reconstructed face states of one stage
 to 1e-12; selection flags exactly. The mixed path (FP32 reconstruction and flux, FP64
-accumulation) keeps flags equal except where the oracle's indicator ratio is within 1e-4 of the
-cut-off, and its L1 density error within 1.05x of the FP64 path's on smooth problems.
+accumulation) keeps flags equal except where the oracle's decision is ambiguous (chi within 1e-4
+of the cut-off, or a decision that changes when the smoothness indicators move by the rounding
+floor of the data), and its L1 density error within 1.05x of the FP64 path's on smooth problems.
+
+Multi-step FP64 comparisons of CTENOZ on discontinuous data use eps = 1e-24. With eps = 1e-40 the
+CTENOZ decision in a cell whose directional stencil is flat to rounding compares tau with that
+stencil's rounding-noise indicator (~1e-35); two correct FP64 evaluations can then choose
+differently (the oracle's own choice depends on its rounding). eps = 1e-24 lies above the FP64
+rounding floor of the indicators for |U| <= 25, so the decision depends on resolved data only.
 """
 from __future__ import annotations
 
@@ -101,10 +108,27 @@ def test_shock_tube_fp64_matches_oracle(scheme, degree):
     native = _native()
     from oracle import Oracle
     wl = W.shock_tube_2d(64, 16)
-    o = Oracle(wl.mesh, degree=degree, scheme=scheme, cfl=0.4)
+    eps = 1e-40 if scheme == 0 else 1e-24
+    o = Oracle(wl.mesh, degree=degree, scheme=scheme, cfl=0.4, eps=eps)
     o.set_state(wl.U0)
     o.run(10)
-    s = _solver(native, [wl.mesh], 2, degree=degree, scheme=scheme, cfl=0.4)
+    s = _solver(native, [wl.mesh], 2, degree=degree, scheme=scheme, cfl=0.4, eps=eps)
+    s.set_state(wl.U0)
+    s.run(10)
+    assert _relerr(s.get_state(), o.get_state()) < FP64_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("make,degree", [(lambda: W.density_wave_3d(6), 2), (lambda: W.blast_3d(5), 3)],
+                         ids=["tet-per-r2-wave", "tet-r3-blast"])
+def test_3d_fp64_10_steps_match_oracle(make, degree):
+    native = _native()
+    from oracle import Oracle
+    wl = make()
+    o = Oracle(wl.mesh, degree=degree, scheme=0, cfl=0.3)
+    o.set_state(wl.U0)
+    o.run(10)
+    s = _solver(native, [wl.mesh], 3, degree=degree, scheme=0, cfl=0.3)
     s.set_state(wl.U0)
     s.run(10)
     assert _relerr(s.get_state(), o.get_state()) < FP64_TOL
@@ -145,13 +169,13 @@ def test_batched_meshes_match_independent_oracles():
     native = _native()
     from oracle import Oracle
     wls = W.quadrants_batch(n_meshes=4, seed=3, nmin=8, nmax=20)
-    s = _solver(native, [w.mesh for w in wls], 2, degree=2, scheme=1, cfl=0.4)
+    s = _solver(native, [w.mesh for w in wls], 2, degree=2, scheme=1, cfl=0.4, eps=1e-24)
     for k, w in enumerate(wls):
         s.set_state(w.U0, k)
     s.run(5)
     dts = s.dt()
     for k, w in enumerate(wls):
-        o = Oracle(w.mesh, degree=2, scheme=1, cfl=0.4)
+        o = Oracle(w.mesh, degree=2, scheme=1, cfl=0.4, eps=1e-24)
         o.set_state(w.U0)
         d_o = o.run(5)
         assert abs(dts[k] - d_o[-1]) < 1e-13 * d_o[-1]
@@ -210,33 +234,47 @@ def test_mixed_precision_flags_at_shocks(scheme):
     fl = native.cteno_get_flags(s.ctx, 0)
     ref = o.flags()
     diff = fl != ref
-    if diff.any():
-        near = _near_cutoff(o, scheme)
-        assert not (diff & ~near).any(), np.argwhere(diff & ~near)[:10]
+    amb = _ambiguous(o, scheme, U)
+    assert not (diff & ~amb).any(), np.argwhere(diff & ~amb)[:10]
+    # not vacuous: resolved decisions that drop the central stencil are among those compared
+    assert (~amb & ((ref & 1) == 0)).sum() >= 20
     s.close()
 
 
-def _near_cutoff(o, scheme, rel=1e-4):
-    """Cells/variables where some chi_s of the oracle is within rel of C_T."""
+def _chi(si, st, scheme, eps, lam1):
+    lams = (1 - lam1) / (st - 1) if st > 1 else 0.0
+    if scheme == 0:
+        g = 1.0 / (si + eps) ** 6
+    else:
+        tau = (np.abs(si[1:] - si[0]).sum() / (st - 1)) ** 6 if st > 1 else 0.0
+        g = 1 + tau / (si + eps)
+    g = g * np.array([lam1] + [lams] * (st - 1))
+    return g / g.sum()
+
+
+def _ambiguous(o, scheme, U, rel=1e-4, noise=1e-12):
+    """Cells/variables whose oracle decision is not resolved: some chi_s within rel of C_T, or a
+    delta that changes when the indicators move by the rounding floor (noise * max|U_v|)^2."""
     SI = o.smoothness_indicators()
     mask = o.stencil_mask()
     out = np.zeros(SI.shape[:2], bool)
     C_T, eps = o.p["C_T"], o.p["eps"]
     lam1 = 1 - 1 / o.p["lambda1p"]
+    floor = (noise * np.abs(U).max(axis=1)) ** 2
     for i in range(SI.shape[0]):
         adm = [0] + [1 + f for f in range(o.nf) if mask[i] >> (1 + f) & 1]
         st = len(adm)
-        lams = (1 - lam1) / (st - 1) if st > 1 else 0.0
         for v in range(SI.shape[1]):
             si = SI[i, v, adm]
-            if scheme == 0:
-                g = 1.0 / (si + eps) ** 6
-            else:
-                tau = (np.abs(si[1:] - si[0]).sum() / (st - 1)) ** 6 if st > 1 else 0.0
-                g = 1 + tau / (si + eps)
-            g = g * np.array([lam1] + [lams] * (st - 1))
-            chi = g / g.sum()
-            out[i, v] = np.any(np.abs(chi - C_T) <= rel * C_T)
+            chi = _chi(si, st, scheme, eps, lam1)
+            base = chi >= C_T
+            amb = bool(np.any(np.abs(chi - C_T) <= rel * C_T))
+            for sc, sd in ((1, 1), (-1, -1), (1, -1), (-1, 1)):
+                pert = si.copy()
+                pert[0] = max(pert[0] + sc * floor[v], 0.0)
+                pert[1:] = np.maximum(pert[1:] + sd * floor[v], 0.0)
+                amb = amb or bool(np.any((_chi(pert, st, scheme, eps, lam1) >= C_T) != base))
+            out[i, v] = amb
     return out
 
 
