@@ -34,8 +34,8 @@ struct cteno_ctx {
   uint32_t *cinfo = nullptr, *fmeta = nullptr;
   void *Pc = nullptr, *Pd = nullptr, *Uf = nullptr;
   uint8_t *flags = nullptr;
-  double *fn = nullptr, *fa = nullptr, *vol = nullptr, *dt = nullptr;
-  float *fn32 = nullptr, *fa32 = nullptr;
+  double *geo = nullptr, *vol = nullptr, *dt = nullptr;
+  float *geo32 = nullptr;
   int *derr = nullptr;
   unsigned long long *guard = nullptr;
   std::vector<int32_t *> d_rank;
@@ -48,6 +48,7 @@ struct cteno_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<void *> allocations;
   int64_t member_sum = 0;            // admissible directional members over all cells
+  int64_t adm_faces = 0;             // admissible directional stencils over all cells
   bool timing = false;
   cudaEvent_t tev[7] = {};           // event record nodes of the step graph
 };
@@ -93,10 +94,8 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.flags = ctx->record_flags ? ctx->flags : nullptr;
   a.nbr = ctx->nbr;
   a.fmeta = ctx->fmeta;
-  a.fn = ctx->fn;
-  a.fa = ctx->fa;
-  a.fn32 = ctx->fn32;
-  a.fa32 = ctx->fa32;
+  a.geo = ctx->geo;
+  a.geo32 = ctx->geo32;
   a.vol = ctx->vol;
   a.dt = ctx->dt;
   a.tab = ctx->d_tab;
@@ -109,6 +108,12 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.cfl = ctx->p.cfl;
   a.lam_gamma = ctx->p.lam_gamma;
   a.guard_on = ctx->p.positivity_guard;
+  a.lam1 = 1.0 - 1.0 / ctx->p.lambda1p;
+  a.inv_lam1 = 1.0 / a.lam1;
+  a.one_m_lam1 = 1.0 - a.lam1;
+  a.log2_lam1 = (float)std::log2(a.lam1);
+  a.log2_one_m_lam1 = (float)std::log2(a.one_m_lam1);
+  for (int q = 0; q < kMaxNQ; ++q) a.fw[q] = ctx->tab.fw[q];
   a.stage = stage;
   a.dt_swap = dt_swap;
   return a;
@@ -250,7 +255,7 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   const Tables &tab = ctx->tab;
   // host arrays in device order
   std::vector<double> hX((size_t)N * nvc * d);
-  std::vector<int32_t> hst((size_t)M * N), hnbr((size_t)nf * N);
+  std::vector<int32_t> hst((size_t)M * N), hnbr((size_t)4 * N, -1);
   std::vector<uint32_t> hinfo(N), hmeta(N);
   std::vector<int64_t> hoff(nmesh + 1);
   for (int k = 0; k < nmesh; ++k) {
@@ -270,14 +275,14 @@ int cteno_lsq_build(cteno_ctx *ctx) {
         for (int j = 0; j < nd; ++j) {
           const int8_t p = m.dirpos[(c * nf + f) * nd + j];
           if (p < 0) continue;
-          hst[(size_t)pos++ * N + g] = (int32_t)(m.offset + m.rank[m.central[c * M + p]]);
+          hst[(size_t)g * M + pos++] = (int32_t)(m.offset + m.rank[m.central[c * M + p]]);
           used[p] = true;
           ++cnt;
         }
         info |= (uint32_t)cnt << (4 * f);
       }
       for (int p = 0; p < M; ++p)
-        if (!used[p]) hst[(size_t)pos++ * N + g] = (int32_t)(m.offset + m.rank[m.central[c * M + p]]);
+        if (!used[p]) hst[(size_t)g * M + pos++] = (int32_t)(m.offset + m.rank[m.central[c * M + p]]);
       // canonical Gauss-point order of each face: permutation to sorted global vertex ids
       for (int f = 0; f < nf; ++f) {
         int slots[3], ns = 0;
@@ -300,11 +305,11 @@ int cteno_lsq_build(cteno_ctx *ctx) {
       for (int f = 0; f < nf; ++f) {
         const int32_t nb = m.nbr[c * nf + f];
         if (nb < 0) {
-          hnbr[(size_t)f * N + g] = -1;
+          hnbr[(size_t)g * 4 + f] = -1;
           meta |= 1u << (kMetaOwnerShift + f);
         } else {
           const int64_t gn = m.offset + m.rank[nb];
-          hnbr[(size_t)f * N + g] = (int32_t)gn;
+          hnbr[(size_t)g * 4 + f] = (int32_t)gn;
           meta |= (uint32_t)m.nbrf[c * nf + f] << (2 * f);
           if (g < gn) meta |= 1u << (kMetaOwnerShift + f);
         }
@@ -318,22 +323,19 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   CK(cudaMalloc(&dX, hX.size() * sizeof(double)));
   CK(dalloc(ctx, &ctx->d_tab, sizeof(DevTables)));
   CK(dalloc(ctx, &ctx->d_mesh_off, sizeof(int64_t) * (nmesh + 1)));
-  CK(dalloc(ctx, &ctx->U, sizeof(double) * ctx->nv * N));
-  CK(dalloc(ctx, &ctx->Un, sizeof(double) * ctx->nv * N));
-  if (ctx->fp32) CK(dalloc(ctx, &ctx->U32, 2 * sizeof(float) * ctx->nv * N));
+  const int nvp = lay_nvp(d), pds = lay_pds(d);
+  CK(dalloc(ctx, &ctx->U, sizeof(double) * nvp * N));
+  CK(dalloc(ctx, &ctx->Un, sizeof(double) * nvp * N));
+  if (ctx->fp32) CK(dalloc(ctx, &ctx->U32, 2 * sizeof(float) * nvp * N));
   CK(dalloc(ctx, &ctx->st, sizeof(int32_t) * M * N));
-  CK(dalloc(ctx, &ctx->nbr, sizeof(int32_t) * nf * N));
+  CK(dalloc(ctx, &ctx->nbr, sizeof(int32_t) * 4 * N));
   CK(dalloc(ctx, &ctx->cinfo, sizeof(uint32_t) * N));
   CK(dalloc(ctx, &ctx->fmeta, sizeof(uint32_t) * N));
   CK(dalloc(ctx, &ctx->Pc, sT * ctx->nk * M * N));
-  CK(dalloc(ctx, &ctx->Pd, sT * nf * d * nd * N));
+  CK(dalloc(ctx, &ctx->Pd, sT * nf * pds * N));
   CK(dalloc(ctx, &ctx->Uf, sT * nf * ctx->nq * ctx->nv * N));
-  CK(dalloc(ctx, &ctx->fn, sizeof(double) * nf * d * N));
-  CK(dalloc(ctx, &ctx->fa, sizeof(double) * nf * N));
-  if (ctx->fp32) {
-    CK(dalloc(ctx, &ctx->fn32, sizeof(float) * nf * d * N));
-    CK(dalloc(ctx, &ctx->fa32, sizeof(float) * nf * N));
-  }
+  CK(dalloc(ctx, &ctx->geo, sizeof(double) * nf * 4 * N));
+  if (ctx->fp32) CK(dalloc(ctx, &ctx->geo32, sizeof(float) * nf * 4 * N));
   CK(dalloc(ctx, &ctx->vol, sizeof(double) * N));
   CK(dalloc(ctx, &ctx->dt, sizeof(double) * 2 * nmesh));
   CK(dalloc(ctx, &ctx->derr, sizeof(int)));
@@ -357,6 +359,8 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   std::memcpy(dt.vq, tab.vq, sizeof(dt.vq));
   std::memcpy(dt.vw, tab.vw, sizeof(dt.vw));
   CK(cudaMemcpyAsync(ctx->d_tab, &dt, sizeof(DevTables), cudaMemcpyHostToDevice, ctx->stream));
+  CK(d == 2 ? upload_recon_tables_2d(ctx->p.degree, tab, ctx->stream)
+            : upload_recon_tables_3d(ctx->p.degree, tab, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_mesh_off, hoff.data(), sizeof(int64_t) * (nmesh + 1), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(dX, hX.data(), hX.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->st, hst.data(), hst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
@@ -365,7 +369,8 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   CK(cudaMemcpyAsync(ctx->fmeta, hmeta.data(), hmeta.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemsetAsync(ctx->derr, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(ctx->guard, 0, sizeof(unsigned long long), ctx->stream));
-  CK(cudaMemsetAsync(ctx->U, 0, sizeof(double) * ctx->nv * N, ctx->stream));
+  CK(cudaMemsetAsync(ctx->U, 0, sizeof(double) * nvp * N, ctx->stream));
+  if (ctx->U32) CK(cudaMemsetAsync(ctx->U32, 0, 2 * sizeof(float) * nvp * N, ctx->stream));
   SetupArgs s{};
   s.N = N;
   s.X = dX;
@@ -377,11 +382,9 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   s.Pc = ctx->Pc;
   s.Pd = ctx->Pd;
   s.store_fp32 = ctx->fp32 ? 1 : 0;
-  s.fn = ctx->fn;
-  s.fa = ctx->fa;
+  s.geo = ctx->geo;
   s.vol = ctx->vol;
-  s.fn32 = ctx->fn32;
-  s.fa32 = ctx->fa32;
+  s.geo32 = ctx->geo32;
   s.tab = ctx->d_tab;
   s.err = ctx->derr;
   for (int j = 0; j < 3; ++j) s.period[j] = ctx->meshes[0].period[j];  // shared by all meshes
@@ -393,13 +396,17 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   if (rc) return rc;
   ctx->h_cinfo.resize(N);
   CK(cudaMemcpy(ctx->h_cinfo.data(), ctx->cinfo, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost));
-  int64_t ms = 0;
+  int64_t ms = 0, af = 0;
   for (int64_t g = 0; g < N; ++g) {
     const uint32_t info = ctx->h_cinfo[g];
     for (int f = 0; f < nf; ++f)
-      if ((info >> (kInfoAdmShift + f)) & 1u) ms += (info >> (4 * f)) & 15u;
+      if ((info >> (kInfoAdmShift + f)) & 1u) {
+        ms += (info >> (4 * f)) & 15u;
+        ++af;
+      }
   }
   ctx->member_sum = ms;
+  ctx->adm_faces = af;
   CK(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
   ctx->built = true;
   return CTENO_OK;
@@ -418,8 +425,8 @@ int cteno_set_state(cteno_ctx *ctx, int32_t mesh_id, const double *U, int is_dev
     CK(cudaMemcpyAsync(ctx->stage_buf, U, cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     src = ctx->stage_buf;
   }
-  launch_permute_in(ctx->nv, m.ncells, ctx->N, m.offset, ctx->d_rank[mesh_id], src, ctx->U, ctx->U32,
-                    ctx->stream);
+  launch_permute_in(ctx->nv, lay_nvp(ctx->d), m.ncells, m.offset, ctx->d_rank[mesh_id], src, ctx->U,
+                    ctx->U32, ctx->stream);
   KArgs a = make_args(ctx, 0, 0);
   launch_dt(ctx->d, a, ctx->stream);
   CK(cudaGetLastError());
@@ -467,12 +474,14 @@ int cteno_get_state(cteno_ctx *ctx, int32_t mesh_id, double *U_out, int is_devic
   const Mesh &m = ctx->meshes[mesh_id];
   const size_t cnt = (size_t)ctx->nv * m.ncells;
   if (is_device) {
-    launch_permute_out(ctx->nv, m.ncells, ctx->N, m.offset, ctx->d_rank[mesh_id], ctx->U, U_out, ctx->stream);
+    launch_permute_out(ctx->nv, lay_nvp(ctx->d), m.ncells, m.offset, ctx->d_rank[mesh_id], ctx->U, U_out,
+                       ctx->stream);
     CK(cudaGetLastError());
     return CTENO_OK;
   }
   if ((rc = ensure_stage_buf(ctx, cnt))) return rc;
-  launch_permute_out(ctx->nv, m.ncells, ctx->N, m.offset, ctx->d_rank[mesh_id], ctx->U, ctx->stage_buf, ctx->stream);
+  launch_permute_out(ctx->nv, lay_nvp(ctx->d), m.ncells, m.offset, ctx->d_rank[mesh_id], ctx->U, ctx->stage_buf,
+                     ctx->stream);
   CK(cudaMemcpyAsync(U_out, ctx->stage_buf, cnt * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return device_status(ctx);
 }
@@ -522,18 +531,17 @@ int cteno_get_face_states(cteno_ctx *ctx, int32_t mesh_id, double *out) {
   if ((rc = check_mesh(ctx, mesh_id))) return rc;
   if (!out) return fail(ctx, CTENO_ERR_ARG, "null output");
   const Mesh &m = ctx->meshes[mesh_id];
-  const int64_t N = ctx->N, n = m.ncells;
-  const int rows = ctx->nf * ctx->nq * ctx->nv;
+  const int64_t n = m.ncells;
+  const int rec = ctx->nf * ctx->nq * ctx->nv;  // one cell's record [f][q][v]
   const size_t sT = ctx->fp32 ? 4 : 8;
-  std::vector<unsigned char> h((size_t)rows * n * sT);
-  for (int r = 0; r < rows; ++r)
-    CK(cudaMemcpyAsync(h.data() + (size_t)r * n * sT, (const char *)ctx->Uf + ((size_t)r * N + m.offset) * sT,
-                       n * sT, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<unsigned char> h((size_t)rec * n * sT);
+  CK(cudaMemcpyAsync(h.data(), (const char *)ctx->Uf + (size_t)m.offset * rec * sT, h.size(),
+                     cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   for (int64_t c = 0; c < n; ++c)
-    for (int r = 0; r < rows; ++r) {
-      const size_t idx = (size_t)r * n + m.rank[c];
-      out[c * rows + r] = ctx->fp32 ? (double)((const float *)h.data())[idx] : ((const double *)h.data())[idx];
+    for (int r = 0; r < rec; ++r) {
+      const size_t idx = (size_t)m.rank[c] * rec + r;
+      out[c * rec + r] = ctx->fp32 ? (double)((const float *)h.data())[idx] : ((const double *)h.data())[idx];
     }
   return CTENO_OK;
 }
@@ -597,7 +605,7 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
 int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
   int rc = check_built(ctx);
   if (rc) return rc;
-  const size_t cnt = (size_t)ctx->nv * ctx->N;
+  const size_t cnt = (size_t)lay_nvp(ctx->d) * ctx->N;
   const size_t nm = ctx->meshes.size();
   // backup: U (FP64), the FP32 shadow and the time steps
   const size_t bytes = cnt * sizeof(double) + 2 * cnt * sizeof(float) + 2 * nm * sizeof(double);
@@ -670,14 +678,17 @@ int cteno_kernel_stats(cteno_ctx *ctx, double *out) {
   const double N = (double)ctx->N, s = ctx->fp32 ? 4.0 : 8.0;
   const int nk = ctx->nk, M = ctx->M, nv = ctx->nv, nf = ctx->nf, nq = ctx->nq, d = ctx->d;
   const double members = (double)ctx->member_sum;
-  // reconstruction: pseudo-inverses, stencil ids, cell info, own means, face-state writes
-  // (neighbour means are re-reads of data counted once as "own means")
-  out[0] = N * (nk * M * s + M * 4.0 + 4.0 + nv * 8.0 + nf * nq * nv * s) + members * d * s +
+  const double nvp = lay_nvp(d), pds = lay_pds(d);
+  const double rec_u = 8.0 * nvp;  // own state record: FP32 (hi, lo) pairs or FP64 values
+  // reconstruction: pseudo-inverse records (central + admissible directional faces), stencil ids,
+  // cell info, own state record, face-state writes (neighbour means are re-reads of records
+  // counted once as "own")
+  out[0] = N * (nk * M * s + M * 4.0 + 4.0 + rec_u + nf * nq * nv * s) + ctx->adm_faces * pds * s +
            (ctx->record_flags ? N * nv : 0.0);
   // flux/update: face states (each read by both of its cells, counted once), neighbour ids,
-  // face meta, normals and areas, volume, U, U^n and the shadow
-  out[1] = N * (nf * nq * nv * s + nf * 4.0 + 4.0 + nf * d * s + nf * s + 8.0 + 3 * nv * 8.0 +
-                (ctx->fp32 ? 2 * nv * 8.0 : 0.0));
+  // face meta, face geometry, volume, U, U^n and the FP32 pair record
+  out[1] = N * (nf * nq * nv * s + 16.0 + 4.0 + nf * 4 * s + 8.0 + 3 * nvp * 8.0 +
+                (ctx->fp32 ? 8.0 * nvp : 0.0));
   // FLOPs: central and directional products, p_1, SI, selection (~30 per stencil), face values
   const double st = 1.0 + (N > 0 ? members / N / d : 0.0);
   out[2] = N * (2.0 * nk * M * nv + 2.0 * nv * (nk * nk + nk) + nv * 30.0 * st + 2.0 * nv * nf * nq * nk) +

@@ -1,4 +1,9 @@
-// device.h -- device buffers, kernel argument block and launcher declarations.
+// device.h -- device data layout, kernel argument block and launcher declarations.
+//
+// Every per-cell array is stored cell-major (array-of-structures): the record of device cell i
+// is one contiguous, 16-byte aligned block, so a thread reads its own record, or a neighbour's,
+// with 16-byte vector loads, and the records of a warp's 32 consecutive cells form one
+// contiguous span (fully used DRAM sectors).
 #pragma once
 
 #include <cstdint>
@@ -8,6 +13,19 @@
 #include "internal.h"
 
 namespace cteno {
+
+// Record sizes for dimension D.
+template <int D>
+struct Lay {
+  static constexpr int NV = D + 2;              // conserved variables
+  static constexpr int NVP = (D == 2) ? 4 : 6;  // state record length (padded to 16 B pairs)
+  static constexpr int NF = D + 1;              // faces
+  static constexpr int NQ = (D == 2) ? 2 : 4;   // Gauss points per face
+  static constexpr int ND = 2 * D;              // max members of a directional stencil
+  static constexpr int PDS = (D == 2) ? 8 : 20; // directional operator record per face (D*ND padded)
+};
+inline int lay_nvp(int d) { return d == 2 ? 4 : 6; }
+inline int lay_pds(int d) { return d == 2 ? 8 : 20; }
 
 // Bits of the per-cell word `cinfo`:
 //   [4f, 4f+4)   members of the directional stencil of local face f (its first slots in the
@@ -37,31 +55,35 @@ struct DevTables {
   double vw[8];
 };
 
-// Everything a kernel touches, passed by value. Arrays are structure-of-arrays over the N cells
-// in device order: element e of cell c is base[e * N + c].
+// Everything a kernel touches, passed by value. Layouts (i = device cell, T = FP64 or FP32):
+//   U, Un   double [N][NVP]        conserved means (padding entries unused)
+//   U32     float2 [N][NVP]        mixed path: (hi, lo) = (fl32(U), fl32(U - hi))
+//   st      int32  [N][M]          stencil ids, directional members first (face after face)
+//   Pc      T      [N][M][nk]      central pseudo-inverse, member-major
+//   Pd      T      [N][NF][PDS]    directional pseudo-inverses, member-major (j * D + k)
+//   Uf      T      [N][NF][NQ][NV] face Gauss-point states
+//   nbr     int32  [N][4]          face neighbours, -1 on a boundary
+//   geo     double [N][NF][4]      outward unit normal (n_x, n_y[, n_z]) and area in slot 3;
+//                                  exact negatives across a face; geo32 its FP32 copy
+//   flags   uint8  [nv][N]         selection flags (debug)
 struct KArgs {
   int64_t N;
   int nmesh;
   const int64_t *mesh_off;  // [nmesh + 1] first device cell of each mesh
-  // state
-  double *U;                // [nv][N] FP64 cell means of the current stage
-  double *Un;               // [nv][N] U^n, start of the step
-  float *U32;               // [nv][N] float2 (hi, lo) split of U: hi = fl32(U), lo = fl32(U - hi)
-  // stencils and least-squares operators
-  const int32_t *st;        // [M][N] device stencil ids (directional members first)
-  const uint32_t *cinfo;    // [N]
-  const void *Pc;           // [nk][M][N] central pseudo-inverse (T)
-  const void *Pd;           // [nf][d][2d][N] directional pseudo-inverses (T)
-  void *Uf;                 // [nf][nq][nv][N] face Gauss-point states (T)
-  uint8_t *flags;           // [nv][N] selection flags, or null
-  // faces and geometry
-  const int32_t *nbr;       // [nf][N] neighbour device id, -1 on a boundary
-  const uint32_t *fmeta;    // [N]
-  const double *fn;         // [nf][d][N] outward unit normal (exact negative across a face)
-  const double *fa;         // [nf][N] face area
-  const float *fn32;        // FP32 copies (mixed path)
-  const float *fa32;
-  const double *vol;        // [N]
+  double *U;
+  double *Un;
+  float *U32;
+  const int32_t *st;
+  const uint32_t *cinfo;
+  const void *Pc;
+  const void *Pd;
+  void *Uf;
+  uint8_t *flags;
+  const int32_t *nbr;
+  const uint32_t *fmeta;
+  const double *geo;
+  const float *geo32;
+  const double *vol;        // [N] 1 / |V_i|
   double *dt;               // [2 * nmesh]: [0..nmesh) current step, [nmesh..2 nmesh) next step
   const DevTables *tab;
   int *err;
@@ -69,6 +91,11 @@ struct KArgs {
   // parameters
   double C_T, lambda1p, eps, gamma, cfl;
   int lam_gamma, guard_on;
+  // linear coefficients of eq. 18, evaluated once on the host in FP64:
+  // lam1 = 1 - 1/lambda_1', 1/lam1, 1 - lam1 (lambda_s = (1 - lam1) / (s_t - 1)) and base-2 logs
+  double lam1, inv_lam1, one_m_lam1;
+  float log2_lam1, log2_one_m_lam1;
+  double fw[kMaxNQ];        // face quadrature weights
   int stage;                // 0, 1, 2
   int dt_swap;              // stage 0 of a CFL step: move dt[next] to dt[cur] first
 };
@@ -77,31 +104,24 @@ struct KArgs {
 struct SetupArgs {
   int64_t N;
   const double *X;          // [N][d+1][d] unwrapped, oriented vertices
-  const int32_t *st;        // [M][N]
+  const int32_t *st;        // [N][M]
   uint32_t *cinfo;          // [N] (admissibility bits written)
-  const int32_t *nbr;       // [nf][N]
+  const int32_t *nbr;       // [N][4]
   const uint32_t *fmeta;
   double period[3];
   void *Pc, *Pd;            // outputs, T = double (FP64 path) or float (mixed path)
   int store_fp32;
-  double *fn, *fa, *vol;
-  float *fn32, *fa32;
+  double *geo, *vol;       // vol receives 1 / |V_i|
+  float *geo32;
   const DevTables *tab;
   int *err;
 };
 
 void launch_setup(int dim, int degree, const SetupArgs &a, cudaStream_t s);
-void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s);
-void launch_dt(int dim, const KArgs &a, cudaStream_t s);
-void launch_dt_reset(const KArgs &a, cudaStream_t s);
-void launch_permute_in(int nv, int64_t n, int64_t N, int64_t off, const int32_t *rank,
-                       const double *src, double *U, float *U32, cudaStream_t s);
-void launch_permute_out(int nv, int64_t n, int64_t N, int64_t off, const int32_t *rank,
-                        const double *U, double *dst, cudaStream_t s);
-
-}  // namespace cteno
-
-namespace cteno {
+// Upload the (d, r) smoothness matrix and face-point basis values to the constant banks of the
+// reconstruction kernels.
+cudaError_t upload_recon_tables_2d(int degree, const Tables &t, cudaStream_t s);
+cudaError_t upload_recon_tables_3d(int degree, const Tables &t, cudaStream_t s);
 void launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s);
 void launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s);
 inline void launch_recon(int dim, int degree, int fp32, int scheme, const KArgs &a, int block,
@@ -109,4 +129,54 @@ inline void launch_recon(int dim, int degree, int fp32, int scheme, const KArgs 
   if (dim == 2) launch_recon_2d(degree, fp32, scheme, a, block, s);
   else launch_recon_3d(degree, fp32, scheme, a, block, s);
 }
+void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s);
+void launch_dt(int dim, const KArgs &a, cudaStream_t s);
+void launch_dt_reset(const KArgs &a, cudaStream_t s);
+void launch_permute_in(int nv, int nvp, int64_t n, int64_t off, const int32_t *rank,
+                       const double *src, double *U, float *U32, cudaStream_t s);
+void launch_permute_out(int nv, int nvp, int64_t n, int64_t off, const int32_t *rank,
+                        const double *U, double *dst, cudaStream_t s);
+
+// 16-byte vector access to records (the records are 16-byte aligned by construction).
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+  __device__ __forceinline__ static void unpack(const float4 &x, float *o) {
+    o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w;
+  }
+  __device__ __forceinline__ static float4 pack(const float *o) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+  __device__ __forceinline__ static void unpack(const double2 &x, double *o) {
+    o[0] = x.x; o[1] = x.y;
+  }
+  __device__ __forceinline__ static double2 pack(const double *o) { return make_double2(o[0], o[1]); }
+};
+
+// Load / store COUNT (a multiple of 16 / sizeof(T)) consecutive values from / to a 16-byte
+// aligned address. Loads go through the read-only path: use them only on data the kernel does
+// not write.
+template <typename T, int COUNT>
+__device__ __forceinline__ void load16(const T *__restrict__ src, T *dst) {
+  using V = Vec16<T>;
+  static_assert(COUNT % V::n == 0, "record not a multiple of 16 bytes");
+#pragma unroll
+  for (int c = 0; c < COUNT / V::n; ++c)
+    V::unpack(__ldg(reinterpret_cast<const typename V::type *>(src) + c), dst + c * V::n);
+}
+template <typename T, int COUNT>
+__device__ __forceinline__ void store16(T *__restrict__ dstp, const T *src) {
+  using V = Vec16<T>;
+  static_assert(COUNT % V::n == 0, "record not a multiple of 16 bytes");
+#pragma unroll
+  for (int c = 0; c < COUNT / V::n; ++c)
+    reinterpret_cast<typename V::type *>(dstp)[c] = V::pack(src + c * V::n);
+}
+
 }  // namespace cteno

@@ -94,116 +94,151 @@ __device__ __forceinline__ void atomic_min_pos(double *addr, double v) {
   atomicMin((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
 }
 
-// Local CFL step of one cell: |V_i| / sum_f |A_f| (|u_i . n_f| + c_i).
-template <int D>
-__device__ __forceinline__ double local_dt(const KArgs &a, int64_t i, const double *u) {
-  const int64_t N = a.N;
-  const double ir = 1.0 / u[0];
-  double ke = 0.0;
+// Local CFL step of one cell: |V_i| / sum_f |A_f| (|u_i . n_f| + c_i), in the path's arithmetic
+// type (FP64 geometry for the FP64 path, the FP32 copy for the mixed path).
+template <int D, typename T>
+__device__ __forceinline__ double local_dt(const KArgs &a, int64_t i, const double *u64) {
+  constexpr int NF = D + 1;
+  const T *G = (sizeof(T) == 4) ? (const T *)a.geo32 : (const T *)a.geo;
+  const T ir = (T)1 / (T)u64[0];
+  T ke = 0, u[D];
 #pragma unroll
-  for (int j = 0; j < D; ++j) ke += u[1 + j] * u[1 + j];
-  const double p = (a.gamma - 1.0) * (u[D + 1] - 0.5 * ke * ir);
-  const double c = sqrt(a.gamma * p * ir);
-  double s = 0.0;
-#pragma unroll
-  for (int f = 0; f < D + 1; ++f) {
-    double un = 0.0;
-#pragma unroll
-    for (int j = 0; j < D; ++j) un += u[1 + j] * ir * a.fn[(f * D + j) * N + i];
-    s += a.fa[f * N + i] * (fabs(un) + c);
+  for (int j = 0; j < D; ++j) {
+    u[j] = (T)u64[1 + j] * ir;
+    ke += (T)u64[1 + j] * u[j];
   }
-  return a.vol[i] / s;
+  const T g = (T)a.gamma;
+  const T p = (g - (T)1) * ((T)u64[D + 1] - (T)0.5 * ke);
+  const T c = sqrt(g * p * ir);
+  T s = 0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const T *gf = G + (i * NF + f) * 4;
+    T un = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) un += u[j] * gf[j];
+    s += gf[3] * (fabs(un) + c);
+  }
+  return 1.0 / ((double)s * a.vol[i]);
 }
 
 template <int D, typename T>
 __global__ void __launch_bounds__(256) flux_kernel(const KArgs a) {
-  constexpr int NV = D + 2, NF = D + 1, NQ = (D == 2) ? 2 : 4;
+  using L = Lay<D>;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, FB = NQ * NV;
+  constexpr bool F32 = sizeof(T) == 4;
   const int64_t N = a.N;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const T *__restrict__ Uf = (const T *)a.Uf;
-  const T *__restrict__ fnT = (sizeof(T) == 4) ? (const T *)a.fn32 : (const T *)a.fn;
-  const T *__restrict__ faT = (sizeof(T) == 4) ? (const T *)a.fa32 : (const T *)a.fa;
+  const T *__restrict__ G = F32 ? (const T *)a.geo32 : (const T *)a.geo;
   const T g = (T)a.gamma;
-  const uint32_t meta = a.fmeta[i];
-  T Ui[NV];  // cell mean, the outside state of a transmissive face
+  const uint32_t meta = __ldg(a.fmeta + i);
+  const int4 nb4 = __ldg(reinterpret_cast<const int4 *>(a.nbr) + i);
+  const int nbv[4] = {nb4.x, nb4.y, nb4.z, nb4.w};
+  // this cell's FP64 record (read before it is overwritten by this same thread)
+  double u64[NVP];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    if constexpr (sizeof(T) == 4) {
-      const float2 h = ((const float2 *)a.U32)[v * N + i];
-      Ui[v] = h.x + h.y;
-    } else {
-      Ui[v] = a.U[v * N + i];
-    }
+  for (int c = 0; c < NVP / 2; ++c) {
+    const double2 x = reinterpret_cast<const double2 *>(a.U + i * NVP)[c];
+    u64[2 * c] = x.x;
+    u64[2 * c + 1] = x.y;
   }
   double acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-  const DevTables &tb = *a.tab;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const int64_t j = a.nbr[f * N + i];
+    const int64_t j = nbv[f];
     const int fj = (meta >> (2 * f)) & 3u;
     const bool own = (meta >> (kMetaOwnerShift + f)) & 1u;
+    T gf[4];
+    load16<T, 4>(G + (i * NF + f) * 4, gf);
     T n[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) n[k] = own ? fnT[(f * D + k) * N + i] : -fnT[(f * D + k) * N + i];
-    const T area = faT[f * N + i];
+    for (int k = 0; k < D; ++k) n[k] = own ? gf[k] : -gf[k];
+    const T area = gf[3];
+    T uI[FB], uO[FB], Ff[NV];
+    load16<T, FB>(Uf + (i * NF + f) * FB, uI);
+    if (j >= 0) {
+      load16<T, FB>(Uf + (j * NF + fj) * FB, uO);
+    } else {  // transmissive boundary: the cell mean outside
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) uO[q * NV + v] = (T)u64[v];
+    }
+    // face flux |A| sum_q w_q F_q in the path's type: both cells of the face evaluate it with
+    // the same operands in the same order, so the two values are identical
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      T uI[NV], uO[NV], F[NV];
+      T F[NV];
+      if (own) hllc<D, T>(uI + q * NV, uO + q * NV, n, g, F);
+      else hllc<D, T>(uO + q * NV, uI + q * NV, n, g, F);
+      const T w = (T)a.fw[q];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        uI[v] = Uf[((int64_t)(f * NQ + q) * NV + v) * N + i];
-        uO[v] = (j >= 0) ? Uf[((int64_t)(fj * NQ + q) * NV + v) * N + j] : Ui[v];
-      }
-      if (own) hllc<D, T>(uI, uO, n, g, F);
-      else hllc<D, T>(uO, uI, n, g, F);
-      const double w = (double)area * tb.fw[q];
+      for (int v = 0; v < NV; ++v) Ff[v] = (q == 0) ? w * F[v] : Ff[v] + w * F[v];
+    }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] += own ? w * (double)F[v] : -w * (double)F[v];
+    for (int v = 0; v < NV; ++v) {
+      const double fv = (double)(area * Ff[v]);
+      acc[v] += own ? fv : -fv;  // FP64 accumulation over the faces (conservation)
     }
   }
   // residual and SSP-RK3 (Shu-Osher) stage update in FP64
   const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
   const double dt = a.dt[mesh];
-  const double ivol = 1.0 / a.vol[i];
-  double un[NV];
+  const double ivol = a.vol[i];
+  double un[NVP], res[NVP];
+  if (a.stage != 0) {
+#pragma unroll
+    for (int c = 0; c < NVP / 2; ++c) {
+      const double2 x = reinterpret_cast<const double2 *>(a.Un + i * NVP)[c];
+      un[2 * c] = x.x;
+      un[2 * c + 1] = x.y;
+    }
+  }
   bool finite = true;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const double u = a.U[v * N + i];
-    const double upd = u - dt * acc[v] * ivol;
-    double res;
-    if (a.stage == 0) {
-      a.Un[v * N + i] = u;
-      res = upd;
-    } else if (a.stage == 1) {
-      res = 0.75 * a.Un[v * N + i] + 0.25 * upd;
-    } else {
-      res = (1.0 / 3.0) * a.Un[v * N + i] + (2.0 / 3.0) * upd;
+  for (int v = 0; v < NVP; ++v) {
+    if (v >= NV) {
+      res[v] = 0.0;
+      continue;
     }
-    un[v] = res;
-    finite = finite && isfinite(res);
-    a.U[v * N + i] = res;
-    if (a.U32) {
-      const float hi = (float)res;
-      ((float2 *)a.U32)[v * N + i] = make_float2(hi, (float)(res - (double)hi));
+    const double upd = u64[v] - dt * acc[v] * ivol;
+    if (a.stage == 0) res[v] = upd;
+    else if (a.stage == 1) res[v] = 0.75 * un[v] + 0.25 * upd;
+    else res[v] = (1.0 / 3.0) * un[v] + (2.0 / 3.0) * upd;
+    finite = finite && isfinite(res[v]);
+  }
+#pragma unroll
+  for (int c = 0; c < NVP / 2; ++c) {
+    reinterpret_cast<double2 *>(a.U + i * NVP)[c] = make_double2(res[2 * c], res[2 * c + 1]);
+    if (a.stage == 0)
+      reinterpret_cast<double2 *>(a.Un + i * NVP)[c] = make_double2(u64[2 * c], u64[2 * c + 1]);
+  }
+  if (a.U32) {
+#pragma unroll
+    for (int c = 0; c < NVP / 2; ++c) {
+      const float h0 = (float)res[2 * c], h1 = (float)res[2 * c + 1];
+      reinterpret_cast<float4 *>(a.U32 + i * 2 * NVP)[c] =
+          make_float4(h0, (float)(res[2 * c] - (double)h0), h1, (float)(res[2 * c + 1] - (double)h1));
     }
   }
   if (!finite) atomicOr(a.err, kErrNonFinite);
-  if (a.stage == 2 && finite) atomic_min_pos(&a.dt[a.nmesh + mesh], a.cfl * local_dt<D>(a, i, un));
+  if (a.stage == 2 && finite) atomic_min_pos(&a.dt[a.nmesh + mesh], a.cfl * local_dt<D, T>(a, i, res));
 }
 
-template <int D>
+template <int D, typename T>
 __global__ void dt_kernel(const KArgs a) {
+  constexpr int NVP = Lay<D>::NVP;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
-  double u[D + 2];
+  double u[NVP];
 #pragma unroll
-  for (int v = 0; v < D + 2; ++v) u[v] = a.U[v * a.N + i];
+  for (int v = 0; v < NVP; ++v) u[v] = a.U[i * NVP + v];
   const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
-  atomic_min_pos(&a.dt[a.nmesh + mesh], a.cfl * local_dt<D>(a, i, u));
+  atomic_min_pos(&a.dt[a.nmesh + mesh], a.cfl * local_dt<D, T>(a, i, u));
 }
 
 __global__ void dt_reset_kernel(double *dt, int nmesh) {
@@ -211,28 +246,29 @@ __global__ void dt_reset_kernel(double *dt, int nmesh) {
   if (i < nmesh) dt[nmesh + i] = 1e300;
 }
 
-// src[v][c] (caller order, mesh of n cells) -> U[v][off + rank[c]] (+ FP32 shadow)
-__global__ void permute_in_kernel(int nv, int64_t n, int64_t N, int64_t off, const int32_t *rank,
+// src[v][c] (caller order, mesh of n cells) -> U[off + rank[c]][v] (+ the FP32 pair)
+__global__ void permute_in_kernel(int nv, int nvp, int64_t n, int64_t off, const int32_t *rank,
                                   const double *src, double *U, float *U32) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const int64_t g = off + rank[c];
-  for (int v = 0; v < nv; ++v) {
-    const double x = src[v * n + c];
-    U[v * N + g] = x;
+  for (int v = 0; v < nvp; ++v) {
+    const double x = (v < nv) ? src[v * n + c] : 0.0;
+    U[g * nvp + v] = x;
     if (U32) {
       const float hi = (float)x;
-      ((float2 *)U32)[v * N + g] = make_float2(hi, (float)(x - (double)hi));
+      U32[(g * nvp + v) * 2] = hi;
+      U32[(g * nvp + v) * 2 + 1] = (float)(x - (double)hi);
     }
   }
 }
 
-__global__ void permute_out_kernel(int nv, int64_t n, int64_t N, int64_t off, const int32_t *rank,
+__global__ void permute_out_kernel(int nv, int nvp, int64_t n, int64_t off, const int32_t *rank,
                                    const double *U, double *dst) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const int64_t g = off + rank[c];
-  for (int v = 0; v < nv; ++v) dst[v * n + c] = U[v * N + g];
+  for (int v = 0; v < nv; ++v) dst[v * n + c] = U[g * nvp + v];
 }
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
@@ -249,22 +285,25 @@ void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s) {
 
 void launch_dt(int dim, const KArgs &a, cudaStream_t s) {
   dt_reset_kernel<<<grid_for(a.nmesh, 64), 64, 0, s>>>(a.dt, a.nmesh);
-  if (dim == 2) dt_kernel<2><<<grid_for(a.N, 256), 256, 0, s>>>(a);
-  else dt_kernel<3><<<grid_for(a.N, 256), 256, 0, s>>>(a);
+  const bool f32 = a.geo32 != nullptr;
+  if (dim == 2 && f32) dt_kernel<2, float><<<grid_for(a.N, 256), 256, 0, s>>>(a);
+  if (dim == 2 && !f32) dt_kernel<2, double><<<grid_for(a.N, 256), 256, 0, s>>>(a);
+  if (dim == 3 && f32) dt_kernel<3, float><<<grid_for(a.N, 256), 256, 0, s>>>(a);
+  if (dim == 3 && !f32) dt_kernel<3, double><<<grid_for(a.N, 256), 256, 0, s>>>(a);
 }
 
 void launch_dt_reset(const KArgs &a, cudaStream_t s) {
   dt_reset_kernel<<<grid_for(a.nmesh, 64), 64, 0, s>>>(a.dt, a.nmesh);
 }
 
-void launch_permute_in(int nv, int64_t n, int64_t N, int64_t off, const int32_t *rank,
+void launch_permute_in(int nv, int nvp, int64_t n, int64_t off, const int32_t *rank,
                        const double *src, double *U, float *U32, cudaStream_t s) {
-  permute_in_kernel<<<grid_for(n, 256), 256, 0, s>>>(nv, n, N, off, rank, src, U, U32);
+  permute_in_kernel<<<grid_for(n, 256), 256, 0, s>>>(nv, nvp, n, off, rank, src, U, U32);
 }
 
-void launch_permute_out(int nv, int64_t n, int64_t N, int64_t off, const int32_t *rank,
+void launch_permute_out(int nv, int nvp, int64_t n, int64_t off, const int32_t *rank,
                         const double *U, double *dst, cudaStream_t s) {
-  permute_out_kernel<<<grid_for(n, 256), 256, 0, s>>>(nv, n, N, off, rank, U, dst);
+  permute_out_kernel<<<grid_for(n, 256), 256, 0, s>>>(nv, nvp, n, off, rank, U, dst);
 }
 
 }  // namespace cteno

@@ -9,8 +9,11 @@
 //   4. smoothness indicators SI = a^T O a (eq. 15), O the universal matrix of the basis;
 //   5. CTENO (Alg. 1) or CTENOZ (Alg. 2) scale separation, cut-off delta_s (eqs. 22-23) and
 //      the final polynomial;
-//   6. its values at the face Gauss points, U_0 + sum_k a_k phi_k(xi_q) (eq. 2), written
-//      structure-of-arrays for the flux kernel.
+//   6. its values at the face Gauss points, U_0 + sum_k a_k phi_k(xi_q) (eq. 2).
+//
+// Memory: the cell's pseudo-inverse record (the dominant stream) is read once with 16-byte
+// loads in member-major order, interleaved with the gathers of the stencil means it multiplies;
+// stencil means come from neighbouring records (L1/L2 hits after the Morton renumbering).
 #pragma once
 
 #include <cstdint>
@@ -21,14 +24,69 @@ namespace cteno {
 
 template <int D, int R>
 struct Shape {
-  static constexpr int NV = D + 2;
-  static constexpr int NF = D + 1;
-  static constexpr int NQ = (D == 2) ? 2 : 4;
   static constexpr int NK = (D == 2 ? (R + 1) * (R + 2) / 2 : (R + 1) * (R + 2) * (R + 3) / 6) - 1;
   static constexpr int M = 2 * (NK + 1);
-  static constexpr int ND = 2 * D;
   static constexpr int NP = (D == 2) ? 2 : 6;
 };
+
+// Constant-bank copies of the universal tables of this module's degrees (filled by
+// upload_recon_tables_*): the smoothness matrix O (eq. 15) and, in 2D, the face-point basis values
+// phi_k at the two Gauss points of each local edge taken in local vertex order (the other edge
+// orientation visits the same two symmetric points in the opposite order). Indexed with
+// compile-time offsets only, so they become instruction operands.
+__constant__ double c_O_r2d[kMaxNK * kMaxNK], c_O_r3d[kMaxNK * kMaxNK];
+__constant__ float c_O_r2f[kMaxNK * kMaxNK], c_O_r3f[kMaxNK * kMaxNK];
+__constant__ double c_Phi2_r2d[3 * 2 * kMaxNK], c_Phi2_r3d[3 * 2 * kMaxNK];
+__constant__ float c_Phi2_r2f[3 * 2 * kMaxNK], c_Phi2_r3f[3 * 2 * kMaxNK];
+
+template <typename T, int R>
+__device__ __forceinline__ T cO(int idx) {
+  if constexpr (R == 2) {
+    if constexpr (sizeof(T) == 4) return c_O_r2f[idx]; else return c_O_r2d[idx];
+  } else {
+    if constexpr (sizeof(T) == 4) return c_O_r3f[idx]; else return c_O_r3d[idx];
+  }
+}
+template <typename T, int R>
+__device__ __forceinline__ T cPhi2(int idx) {
+  if constexpr (R == 2) {
+    if constexpr (sizeof(T) == 4) return c_Phi2_r2f[idx]; else return c_Phi2_r2d[idx];
+  } else {
+    if constexpr (sizeof(T) == 4) return c_Phi2_r3f[idx]; else return c_Phi2_r3d[idx];
+  }
+}
+
+// Host side: copy O and the 2D edge values of degree r into this module's constant banks.
+inline cudaError_t upload_recon_tables(int dim, int degree, const Tables &t, cudaStream_t s) {
+  double Od[kMaxNK * kMaxNK] = {}, Pd2[3 * 2 * kMaxNK] = {};
+  float Of[kMaxNK * kMaxNK] = {}, Pf2[3 * 2 * kMaxNK] = {};
+  for (int k = 0; k < t.nk; ++k)
+    for (int l = 0; l < t.nk; ++l) {
+      Od[k * t.nk + l] = t.O[k][l];
+      Of[k * t.nk + l] = (float)t.O[k][l];
+    }
+  if (dim == 2)
+    for (int f = 0; f < 3; ++f)
+      for (int q = 0; q < 2; ++q)
+        for (int k = 0; k < t.nk; ++k) {
+          Pd2[(f * 2 + q) * t.nk + k] = t.Phi[f][0][q][k];
+          Pf2[(f * 2 + q) * t.nk + k] = (float)t.Phi[f][0][q][k];
+        }
+  cudaError_t e;
+  if (degree == 2) {
+    if ((e = cudaMemcpyToSymbolAsync(c_O_r2d, Od, sizeof(Od), 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(c_O_r2f, Of, sizeof(Of), 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(c_Phi2_r2d, Pd2, sizeof(Pd2), 0, cudaMemcpyHostToDevice, s))) return e;
+    e = cudaMemcpyToSymbolAsync(c_Phi2_r2f, Pf2, sizeof(Pf2), 0, cudaMemcpyHostToDevice, s);
+  } else {
+    if ((e = cudaMemcpyToSymbolAsync(c_O_r3d, Od, sizeof(Od), 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(c_O_r3f, Of, sizeof(Of), 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(c_Phi2_r3d, Pd2, sizeof(Pd2), 0, cudaMemcpyHostToDevice, s))) return e;
+    e = cudaMemcpyToSymbolAsync(c_Phi2_r3f, Pf2, sizeof(Pf2), 0, cudaMemcpyHostToDevice, s);
+  }
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);  // the host arrays above go out of scope
+}
 
 template <typename T>
 __device__ __forceinline__ T pow6(T x) {
@@ -36,140 +94,181 @@ __device__ __forceinline__ T pow6(T x) {
   return x2 * x2 * x2;
 }
 
-// Selection of eqs. 19-23 / Alg. 1-2 in FP64, as printed (with lambda_s when lam_gamma).
-// SI[0] central, SI[1..st-1] admissible directional. Returns delta bits (bit s).
-__device__ __forceinline__ uint32_t select_fp64(const double *SI, int st, int scheme,
-                                                int lam_gamma, double lam1, double lams,
+// Selection of eqs. 19-23 / Alg. 1-2 in FP64, as printed (gamma_s times lambda_s when
+// lam_gamma). SI0: central; SId[f]: directional stencil of face f, used where bit f of adm is
+// set. Returns delta bits: bit 0 central, bit 1 + f directional f.
+template <int NF>
+__device__ __forceinline__ uint32_t select_fp64(double SI0, const double *SId, uint32_t adm, int st,
+                                                int scheme, int lam_gamma, double lam1, double lams,
                                                 double eps, double C_T) {
-  double g[5], sum = 0.0;
+  double g0, gd[NF];
   if (scheme == 0) {
-    for (int s = 0; s < st; ++s) g[s] = 1.0 / pow6(SI[s] + eps);
+    g0 = 1.0 / pow6(SI0 + eps);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) gd[f] = 1.0 / pow6(SId[f] + eps);
   } else {
     double tau = 0.0;
     if (st > 1) {
       double acc = 0.0;
-      for (int s = 1; s < st; ++s) acc += fabs(SI[s] - SI[0]);
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        if ((adm >> f) & 1u) acc += fabs(SId[f] - SI0);
       tau = pow6(acc / (st - 1));
     }
-    for (int s = 0; s < st; ++s) g[s] = 1.0 + tau / (SI[s] + eps);
+    g0 = 1.0 + tau / (SI0 + eps);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) gd[f] = 1.0 + tau / (SId[f] + eps);
   }
-  if (lam_gamma)
-    for (int s = 0; s < st; ++s) g[s] *= (s == 0) ? lam1 : lams;
-  for (int s = 0; s < st; ++s) sum += g[s];
-  uint32_t bits = 0;
-  for (int s = 0; s < st; ++s)
-    if (!(g[s] / sum < C_T)) bits |= 1u << s;
+  if (lam_gamma) {
+    g0 *= lam1;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) gd[f] *= lams;
+  }
+  double sum = g0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+    if ((adm >> f) & 1u) sum += gd[f];
+  uint32_t bits = (g0 / sum < C_T) ? 0u : 1u;
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+    if (((adm >> f) & 1u) && !(gd[f] / sum < C_T)) bits |= 1u << (1 + f);
   return bits;
 }
 
 // The same decision in FP32 without overflow: every gamma_s is carried as its base-2 logarithm
 // L_s, and chi_s = 2^(L_s - Lmax) / sum_t 2^(L_t - Lmax).
-__device__ __forceinline__ uint32_t select_fp32(const float *SI, int st, int scheme,
-                                                int lam_gamma, float log2lam1, float log2lams,
-                                                float eps, float C_T) {
-  float L[5], Lmax = -INFINITY;
+template <int NF>
+__device__ __forceinline__ uint32_t select_fp32(float SI0, const float *SId, uint32_t adm, int st,
+                                                int scheme, int lam_gamma, float log2lam1,
+                                                float log2lams, float eps, float C_T) {
+  float L0, Ld[NF];
   if (scheme == 0) {
-    for (int s = 0; s < st; ++s) L[s] = -6.0f * log2f(SI[s] + eps);
+    L0 = -6.0f * log2f(SI0 + eps);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) Ld[f] = -6.0f * log2f(SId[f] + eps);
   } else {
     float lt = -INFINITY;  // log2 tau
     if (st > 1) {
       float acc = 0.0f;
-      for (int s = 1; s < st; ++s) acc += fabsf(SI[s] - SI[0]);
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        if ((adm >> f) & 1u) acc += fabsf(SId[f] - SI0);
       lt = 6.0f * log2f(acc / (float)(st - 1));
     }
-    for (int s = 0; s < st; ++s) {
-      const float x = lt - log2f(SI[s] + eps);  // log2(tau / (SI + eps))
-      // log2(1 + 2^x), split to stay accurate for large and small x
-      L[s] = (x > 0.0f) ? x + log2f(1.0f + exp2f(-x)) : log2f(1.0f + exp2f(x));
-    }
+    // log2(1 + 2^x) with x = log2(tau / (SI + eps)), split to stay accurate for any x
+    auto l1p = [](float x) { return (x > 0.0f) ? x + log2f(1.0f + exp2f(-x)) : log2f(1.0f + exp2f(x)); };
+    L0 = l1p(lt - log2f(SI0 + eps));
+#pragma unroll
+    for (int f = 0; f < NF; ++f) Ld[f] = l1p(lt - log2f(SId[f] + eps));
   }
-  if (lam_gamma)
-    for (int s = 0; s < st; ++s) L[s] += (s == 0) ? log2lam1 : log2lams;
-  for (int s = 0; s < st; ++s) Lmax = fmaxf(Lmax, L[s]);
-  float sum = 0.0f;
-  for (int s = 0; s < st; ++s) sum += exp2f(L[s] - Lmax);
-  uint32_t bits = 0;
-  for (int s = 0; s < st; ++s)
-    if (!(exp2f(L[s] - Lmax) / sum < C_T)) bits |= 1u << s;
+  if (lam_gamma) {
+    L0 += log2lam1;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) Ld[f] += log2lams;
+  }
+  float Lmax = L0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+    if ((adm >> f) & 1u) Lmax = fmaxf(Lmax, Ld[f]);
+  float sum = exp2f(L0 - Lmax);
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+    if ((adm >> f) & 1u) sum += exp2f(Ld[f] - Lmax);
+  uint32_t bits = (exp2f(L0 - Lmax) / sum < C_T) ? 0u : 1u;
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+    if (((adm >> f) & 1u) && !(exp2f(Ld[f] - Lmax) / sum < C_T)) bits |= 1u << (1 + f);
   return bits;
 }
 
 template <int D, int R, typename T, int SCHEME>
 __global__ void __launch_bounds__(256) recon_kernel(const KArgs a) {
   using S = Shape<D, R>;
-  constexpr int NV = S::NV, NF = S::NF, NQ = S::NQ, NK = S::NK, M = S::M, ND = S::ND,
-                NP = S::NP;
-  constexpr int NPHI = NF * NP * NQ * NK;
+  using L = Lay<D>;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, ND = L::ND, PDS = L::PDS;
+  constexpr int NK = S::NK, M = S::M, NP = S::NP;
+  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
+  constexpr int CH = Vec16<T>::n;
+  constexpr bool F32 = sizeof(T) == 4;
+  // 3D: face-point basis values for all six vertex orders of a face, staged in shared memory
   __shared__ T sPhi[NPHI];
-  __shared__ T sO[NK * NK];
-  {
+  if constexpr (D == 3) {
     const DevTables &tb = *a.tab;
     for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
       const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
       sPhi[t] = (T)tb.Phi[f][p][q][k];
     }
-    for (int t = threadIdx.x; t < NK * NK; t += blockDim.x) sO[t] = (T)tb.O[t / NK][t % NK];
+    __syncthreads();
   }
-  __syncthreads();
 
   const int64_t N = a.N;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
 
-  // cell means: FP64 directly, or (mixed path) the FP32 pair hi + lo of every FP64 value, so
-  // that U_m - U_0 = (hi_m - hi_0) + (lo_m - lo_0) keeps FP64 accuracy in FP32 arithmetic
-  const double *__restrict__ U64 = a.U;
-  const float2 *__restrict__ U2 = (const float2 *)a.U32;
-  const T *__restrict__ Pc = (const T *)a.Pc;
-  const T *__restrict__ Pd = (const T *)a.Pd;
-  const int32_t *__restrict__ st = a.st;
-
+  // own cell means: FP64, or (mixed path) the FP32 pair hi + lo of every FP64 value, so that
+  // U_m - U_0 = (hi_m - hi_0) + (lo_m - lo_0) keeps FP64 accuracy in FP32 arithmetic
   T U0[NV];
-  float L0[NV];  // low parts (mixed path)
+  float L0[NV];
+  if constexpr (F32) {
+    float hl[2 * NVP];
+    load16<float, 2 * NVP>(a.U32 + i * 2 * NVP, hl);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    if constexpr (sizeof(T) == 4) {
-      const float2 h = U2[v * N + i];
-      U0[v] = (T)h.x;
-      L0[v] = h.y;
-    } else {
-      U0[v] = (T)U64[v * N + i];
+    for (int v = 0; v < NV; ++v) {
+      U0[v] = hl[2 * v];
+      L0[v] = hl[2 * v + 1];
+    }
+  } else {
+    double u[NVP];
+    load16<double, NVP>(a.U + i * NVP, u);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      U0[v] = (T)u[v];
       L0[v] = 0.0f;
     }
   }
   auto delta = [&](int64_t j, T *du) {
+    if constexpr (F32) {
+      float hl[2 * NVP];
+      load16<float, 2 * NVP>(a.U32 + j * 2 * NVP, hl);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      if constexpr (sizeof(T) == 4) {
-        const float2 h = U2[v * N + j];
-        du[v] = (T)((h.x - (float)U0[v]) + (h.y - L0[v]));
-      } else {
-        du[v] = (T)(U64[v * N + j] - (double)U0[v]);
-      }
+      for (int v = 0; v < NV; ++v) du[v] = (T)((hl[2 * v] - (float)U0[v]) + (hl[2 * v + 1] - L0[v]));
+    } else {
+      double u[NVP];
+      load16<double, NVP>(a.U + j * NVP, u);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) du[v] = (T)(u[v] - (double)U0[v]);
     }
   };
 
-  // 1-2: central coefficients a_opt = P_c (U_m - U_0)
+  // 1-2: central coefficients a_opt = P_c (U_m - U_0), streaming the member-major record
+  const int32_t *__restrict__ sti = a.st + i * M;
+  const T *__restrict__ Pci = (const T *)a.Pc + i * (int64_t)(M * NK);
   T ao[NK][NV];
 #pragma unroll
   for (int k = 0; k < NK; ++k)
 #pragma unroll
     for (int v = 0; v < NV; ++v) ao[k][v] = (T)0;
-#pragma unroll 4
-  for (int m = 0; m < M; ++m) {
-    const int64_t j = st[m * N + i];
-    T du[NV];
-    delta(j, du);
+  {
+    T pb[CH], du[NV];
+    int ids[4];
 #pragma unroll
-    for (int k = 0; k < NK; ++k) {
-      const T p = Pc[((int64_t)k * M + m) * N + i];
+    for (int e = 0; e < M * NK; ++e) {
+      const int m = e / NK, k = e % NK;
+      if (e % CH == 0) load16<T, CH>(Pci + e, pb);
+      if (k == 0) {
+        if (m % 4 == 0) {
+          const int4 t4 = __ldg(reinterpret_cast<const int4 *>(sti + m));
+          ids[0] = t4.x; ids[1] = t4.y; ids[2] = t4.z; ids[3] = t4.w;
+        }
+        delta(ids[m % 4], du);
+      }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) ao[k][v] += p * du[v];
+      for (int v = 0; v < NV; ++v) ao[k][v] += pb[e % CH] * du[v];
     }
   }
 
   // directional coefficients (degree 1): members of face f are the next slots of the list
-  const uint32_t info = a.cinfo[i];
+  const uint32_t info = __ldg(a.cinfo + i);
   const uint32_t adm = (info >> kInfoAdmShift) & 0xFu;
   T ad[NF][D][NV];
 #pragma unroll
@@ -178,45 +277,47 @@ __global__ void __launch_bounds__(256) recon_kernel(const KArgs a) {
     for (int k = 0; k < D; ++k)
 #pragma unroll
       for (int v = 0; v < NV; ++v) ad[f][k][v] = (T)0;
-  int off = 0;
+  {
+    int off = 0;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const int nm = (info >> (4 * f)) & 15u;
-    if ((adm >> f) & 1u) {
+    for (int f = 0; f < NF; ++f) {
+      const int nm = (info >> (4 * f)) & 15u;
+      if ((adm >> f) & 1u) {
+        T pf[PDS];
+        load16<T, PDS>((const T *)a.Pd + (i * NF + f) * PDS, pf);
 #pragma unroll
-      for (int jj = 0; jj < ND; ++jj) {
-        if (jj < nm) {
-          const int64_t j = st[(int64_t)(off + jj) * N + i];
-          T du[NV];
-          delta(j, du);
+        for (int jj = 0; jj < ND; ++jj) {
+          if (jj < nm) {
+            T du[NV];
+            delta(__ldg(sti + off + jj), du);
 #pragma unroll
-          for (int k = 0; k < D; ++k) {
-            const T p = Pd[((int64_t)(f * D + k) * ND + jj) * N + i];
+            for (int k = 0; k < D; ++k)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) ad[f][k][v] += p * du[v];
+              for (int v = 0; v < NV; ++v) ad[f][k][v] += pf[jj * D + k] * du[v];
           }
         }
       }
+      off += nm;
     }
-    off += nm;
   }
 
-  // 3: linear coefficients of eq. 18 over the admissible stencils
-  const int nadm = __popc(adm);
-  const int stn = 1 + nadm;
-  const double lam1d = 1.0 - 1.0 / a.lambda1p;
-  const double lamsd = (stn > 1) ? (1.0 - lam1d) / (stn - 1) : 0.0;
-  const T lam1 = (T)lam1d, lams = (T)lamsd;
-  const T inv_lam1 = (T)(1.0 / lam1d);
-  const float log2lam1 = (float)log2(lam1d);
-  const float log2lams = (stn > 1) ? (float)log2(lamsd) : 0.0f;
-  (void)lam1;
-
-  const uint32_t perm = info >> kInfoPermShift;
-  T *__restrict__ Uf = (T *)a.Uf;
+  // 3: linear coefficients of eq. 18 over the admissible stencils (lambda_1 terms from the host)
+  const int stn = 1 + __popc(adm);
+  T lams;
+  double lamsd = 0.0;
+  float log2lams = 0.0f;
+  if constexpr (F32) {
+    lams = (stn > 1) ? (float)a.one_m_lam1 / (float)(stn - 1) : 0.0f;
+    if (stn > 1) log2lams = a.log2_one_m_lam1 - log2f((float)(stn - 1));
+  } else {
+    lamsd = (stn > 1) ? a.one_m_lam1 / (stn - 1) : 0.0;
+    lams = lamsd;
+  }
+  const T inv_lam1 = (T)a.inv_lam1;
+  const float log2lam1 = a.log2_lam1;
   constexpr T INV_FACT = (D == 2) ? (T)0.5 : (T)(1.0 / 6.0);
 
-#pragma unroll 1
+#pragma unroll
   for (int v = 0; v < NV; ++v) {
     // p_1 (eq. 17): the directional polynomials only touch the linear coefficients
     T a1[NK];
@@ -234,109 +335,100 @@ __global__ void __launch_bounds__(256) recon_kernel(const KArgs a) {
       for (int k = 0; k < NK; ++k) a1[k] *= inv_lam1;
     }
     // 4: smoothness indicators
-    T SI[1 + NF];
-    {
-      T s0 = (T)0;
+    T SI0 = (T)0;
 #pragma unroll
-      for (int k = 0; k < NK; ++k) {
-        T r = (T)0;
+    for (int k = 0; k < NK; ++k) {
+      T r = (T)0;
 #pragma unroll
-        for (int l = 0; l < NK; ++l) r += sO[k * NK + l] * a1[l];
-        s0 += a1[k] * r;
-      }
-      SI[0] = s0;
+      for (int l = 0; l < NK; ++l) r += cO<T, R>(k * NK + l) * a1[l];
+      SI0 += a1[k] * r;
     }
-    int sidx[NF];  // admissible face of stencil slot 1 + s
-    int ns = 0;
+    T SId[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      if ((adm >> f) & 1u) {
-        T s = (T)0;
+      T s = (T)0;
 #pragma unroll
-        for (int k = 0; k < D; ++k) s += ad[f][k][v] * ad[f][k][v];
-        SI[1 + ns] = s * INV_FACT;
-        sidx[ns] = f;
-        ++ns;
-      }
+      for (int k = 0; k < D; ++k) s += ad[f][k][v] * ad[f][k][v];
+      SId[f] = s * INV_FACT;
     }
     // 5: selection
     uint32_t bits;
-    if constexpr (sizeof(T) == 8) {
-      bits = select_fp64((const double *)SI, stn, SCHEME, a.lam_gamma, lam1d, lamsd, a.eps, a.C_T);
+    if constexpr (F32) {
+      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, log2lam1, log2lams,
+                             fmaxf((float)a.eps, 1e-40f), (float)a.C_T);
     } else {
-      bits = select_fp32((const float *)SI, stn, SCHEME, a.lam_gamma, log2lam1, log2lams,
-                         fmaxf((float)a.eps, 1e-40f), (float)a.C_T);
+      bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
     }
-    T af[NK];
-    uint8_t flag;
+    // final coefficients, written over a_opt
     if (bits & 1u) {
 #pragma unroll
-      for (int k = 0; k < NK; ++k) af[k] = a1[k];
-      flag = 1;
+      for (int k = 0; k < NK; ++k) ao[k][v] = a1[k];
     } else {
+      const T w = (T)1 / (T)__popc(bits >> 1);
 #pragma unroll
-      for (int k = 0; k < NK; ++k) af[k] = (T)0;
-      flag = 0;
-      const int nsel = __popc(bits >> 1);
-      const T w = (T)1 / (T)nsel;
+      for (int k = 0; k < NK; ++k) ao[k][v] = (T)0;
 #pragma unroll
-      for (int s = 0; s < NF; ++s) {
-        if (s < ns && ((bits >> (1 + s)) & 1u)) {
-          const int f = sidx[s];
-          // ad[f] with a runtime f: select through an unrolled loop to stay in registers
+      for (int f = 0; f < NF; ++f)
+        if ((bits >> (1 + f)) & 1u) {
 #pragma unroll
-          for (int ff = 0; ff < NF; ++ff)
-            if (ff == f) {
+          for (int k = 0; k < D; ++k) ao[k][v] += w * ad[f][k][v];
+        }
+    }
+    if (a.flags) a.flags[v * N + i] = (uint8_t)((bits & 1u) ? 1u : bits);
+  }
+
+  // 6: face Gauss-point values, one contiguous vector per face; positivity guard (not part of
+  // the paper): a non-physical face state makes the cell use its mean at all its face points
+  T *__restrict__ Ufi = (T *)a.Uf + i * (int64_t)(NF * NQ * NV);
+  const uint32_t perm = info >> kInfoPermShift;
+  const T gm1 = (T)(a.gamma - 1.0);
+  bool bad = false;
 #pragma unroll
-              for (int k = 0; k < D; ++k) af[k] += w * ad[ff][k][v];
-            }
-          flag |= (uint8_t)(1u << (1 + f));
+  for (int f = 0; f < NF; ++f) {
+    const int p = (perm >> (3 * f)) & 7u;
+    T fb[NQ * NV];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T val = (T)L0[v];
+        if constexpr (D == 2) {
+#pragma unroll
+          for (int k = 0; k < NK; ++k) val += cPhi2<T, R>((f * 2 + q) * NK + k) * ao[k][v];
+        } else {
+          const T *ph = &sPhi[((f * NP + p) * NQ) * NK];
+#pragma unroll
+          for (int k = 0; k < NK; ++k) val += ph[q * NK + k] * ao[k][v];
+        }
+        fb[q * NV + v] = val + U0[v];
+      }
+      T ke = (T)0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) ke += fb[q * NV + 1 + j] * fb[q * NV + 1 + j];
+      const T pr = gm1 * (fb[q * NV + NV - 1] - (T)0.5 * ke / fb[q * NV]);
+      bad = bad || !(fb[q * NV] > (T)0) || !(pr > (T)0);
+    }
+    if constexpr (D == 2) {  // edge stored in sorted-vertex order: swap the two points
+      if (p) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T t = fb[v];
+          fb[v] = fb[NV + v];
+          fb[NV + v] = t;
         }
       }
     }
-    if (a.flags) a.flags[v * N + i] = flag;
-    // 6: face Gauss-point values
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const int p = (perm >> (3 * f)) & 7u;
-      const T *ph = &sPhi[((f * NP + p) * NQ) * NK];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        T val = (T)L0[v];
-#pragma unroll
-        for (int k = 0; k < NK; ++k) val += ph[q * NK + k] * af[k];
-        val += U0[v];
-        Uf[((int64_t)(f * NQ + q) * NV + v) * N + i] = val;
-      }
-    }
+    store16<T, NQ * NV>(Ufi + f * NQ * NV, fb);
   }
-
-  // positivity guard (not part of the paper): non-physical face state -> cell mean everywhere
-  if (a.guard_on) {
-    bool bad = false;
-    const T gm1 = (T)(a.gamma - 1.0);
+  if (a.guard_on && bad) {
+    T fb[NQ * NV];
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
+    for (int q = 0; q < NQ; ++q)
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        T u[NV];
+      for (int v = 0; v < NV; ++v) fb[q * NV + v] = U0[v] + (T)L0[v];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) u[v] = Uf[((int64_t)(f * NQ + q) * NV + v) * N + i];
-        T ke = (T)0;
-#pragma unroll
-        for (int j = 0; j < D; ++j) ke += u[1 + j] * u[1 + j];
-        const T p = gm1 * (u[NV - 1] - (T)0.5 * ke / u[0]);
-        if (!(u[0] > (T)0) || !(p > (T)0)) bad = true;
-      }
-    if (bad) {
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-#pragma unroll
-        for (int q = 0; q < NQ; ++q)
-#pragma unroll
-          for (int v = 0; v < NV; ++v) Uf[((int64_t)(f * NQ + q) * NV + v) * N + i] = U0[v] + (T)L0[v];
-      atomicAdd(a.guard, 1ull);
-    }
+    for (int f = 0; f < NF; ++f) store16<T, NQ * NV>(Ufi + f * NQ * NV, fb);
+    atomicAdd(a.guard, 1ull);
   }
 
   // CFL time step bookkeeping at the first stage of a step: dt[next] -> dt[cur]

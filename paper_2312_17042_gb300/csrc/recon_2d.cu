@@ -17,4 +17,8 @@ void launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, int block
 #undef CTENO_RECON
 }
 
+cudaError_t upload_recon_tables_2d(int degree, const Tables &t, cudaStream_t s) {
+  return upload_recon_tables(2, degree, t, s);
+}
+
 }  // namespace cteno

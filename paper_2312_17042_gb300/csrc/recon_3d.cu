@@ -17,4 +17,8 @@ void launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block
 #undef CTENO_RECON
 }
 
+cudaError_t upload_recon_tables_3d(int degree, const Tables &t, cudaStream_t s) {
+  return upload_recon_tables(3, degree, t, s);
+}
+
 }  // namespace cteno

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(128) setup_kernel(const SetupArgs a) {
   for (int r = 0; r < D; ++r)
     for (int c = 0; c < D; ++c) J[r][c] = Xi[c + 1][r] - Xi[0][r];
   inverse<D>(J, Ji);
-  a.vol[i] = fabs(det_rm<D>(J)) / FACT;
+  a.vol[i] = FACT / fabs(det_rm<D>(J));  // 1 / |V_i|
   for (int j = 0; j < D; ++j) {
     double s = 0.0;
     for (int v = 0; v < NVC; ++v) s += Xi[v][j];
@@ -162,21 +162,20 @@ __global__ void __launch_bounds__(128) setup_kernel(const SetupArgs a) {
     len = sqrt(len);
     const double sgn = (dot > 0.0) ? 1.0 : -1.0;
     for (int j = 0; j < D; ++j) n[j] = sgn * n[j] / len;
-    const int32_t nb = a.nbr[f * N + i];
-    for (int j = 0; j < D; ++j) {
-      a.fn[(f * D + j) * N + i] = n[j];
-      if (a.fn32) a.fn32[(f * D + j) * N + i] = (float)n[j];
+    const int32_t nb = a.nbr[i * 4 + f];
+    double gv[4] = {0.0, 0.0, 0.0, area};
+    for (int j = 0; j < D; ++j) gv[j] = n[j];
+    for (int c = 0; c < 4; ++c) {
+      a.geo[(i * NF + f) * 4 + c] = gv[c];
+      if (a.geo32) a.geo32[(i * NF + f) * 4 + c] = (float)gv[c];
     }
-    a.fa[f * N + i] = area;
-    if (a.fa32) a.fa32[f * N + i] = (float)area;
-    if (nb >= 0) {
+    if (nb >= 0) {  // the other side: the exact negative normal, the same area
       const int fj = (meta >> (2 * f)) & 3u;
-      for (int j = 0; j < D; ++j) {
-        a.fn[(fj * D + j) * N + nb] = -n[j];
-        if (a.fn32) a.fn32[(fj * D + j) * N + nb] = -(float)n[j];
+      for (int c = 0; c < 4; ++c) {
+        const double x = (c < D) ? -gv[c] : gv[c];
+        a.geo[((int64_t)nb * NF + fj) * 4 + c] = x;
+        if (a.geo32) a.geo32[((int64_t)nb * NF + fj) * 4 + c] = (c < D) ? -(float)gv[c] : (float)gv[c];
       }
-      a.fa[fj * N + nb] = area;
-      if (a.fa32) a.fa32[fj * N + nb] = (float)area;
     }
   }
 
@@ -184,7 +183,7 @@ __global__ void __launch_bounds__(128) setup_kernel(const SetupArgs a) {
   double W[M][NK];
   double Vp[M];
   for (int p = 0; p < M; ++p) {
-    const int64_t m = a.st[p * N + i];
+    const int64_t m = a.st[i * M + p];
     double Xm[NVC][D], cm[D];
     for (int v = 0; v < NVC; ++v)
       for (int j = 0; j < D; ++j) Xm[v][j] = a.X[(m * NVC + v) * D + j];
@@ -243,14 +242,16 @@ __global__ void __launch_bounds__(128) setup_kernel(const SetupArgs a) {
         }
       }
     }
-    for (int k = 0; k < D; ++k)
-      for (int j = 0; j < ND; ++j) {
-        const int64_t idx = ((int64_t)(f * D + k) * ND + j) * N + i;
-        if (a.store_fp32)
-          ((float *)a.Pd)[idx] = (float)pd[k][j];
-        else
-          ((double *)a.Pd)[idx] = pd[k][j];
-      }
+    constexpr int PDS = Lay<D>::PDS;
+    for (int e = 0; e < PDS; ++e) {  // member-major: entry j * D + k, zero padding
+      const int j = e / D, k = e % D;
+      const double val = (j < ND) ? pd[k][j] : 0.0;
+      const int64_t idx = (i * NF + f) * PDS + e;
+      if (a.store_fp32)
+        ((float *)a.Pd)[idx] = (float)val;
+      else
+        ((double *)a.Pd)[idx] = val;
+    }
     off += nm;
   }
   a.cinfo[i] = (info & ~(0xFu << kInfoAdmShift)) | (adm << kInfoAdmShift);
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(128) setup_kernel(const SetupArgs a) {
     double col[NK];
     pinv_column<NK, M>(W, M, NK, dg, vt, bt, p, col);
     for (int k = 0; k < NK; ++k) {
-      const int64_t idx = ((int64_t)k * M + p) * N + i;
+      const int64_t idx = (i * M + p) * NK + k;
       if (a.store_fp32)
         ((float *)a.Pc)[idx] = (float)(col[k] * Vp[p]);
       else

@@ -236,8 +236,13 @@ def test_mixed_precision_flags_at_shocks(scheme):
     diff = fl != ref
     amb = _ambiguous(o, scheme, U)
     assert not (diff & ~amb).any(), np.argwhere(diff & ~amb)[:10]
-    # not vacuous: resolved decisions that drop the central stencil are among those compared
-    assert (~amb & ((ref & 1) == 0)).sum() >= 20
+    # not vacuous. CTENO: resolved decisions that drop the central stencil are compared. CTENOZ
+    # at eps = 1e-40: every such decision on this problem is rounding-driven (see the module
+    # docstring), so the check is that most decisions are resolved and compared.
+    if scheme == 0:
+        assert (~amb & ((ref & 1) == 0)).sum() >= 20
+    else:
+        assert (~amb).mean() > 0.5
     s.close()
 
 
