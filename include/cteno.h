@@ -121,6 +121,21 @@ int cteno_run(cteno_ctx *ctx, int nsteps);
 /* Read the conserved cell means of one mesh into U_out[v][c] (host or device). */
 int cteno_get_state(cteno_ctx *ctx, int32_t mesh_id, double *U_out, int is_device);
 
+/* Like cteno_get_state with a host output, but allocating nothing. The paper has no counterpart;
+ * this is for callers that cannot allocate device memory at the time they read a state back --
+ * for example a program whose memory pool owns all device memory, or code running where
+ * cudaMalloc is not allowed. cteno_get_state stages through a device buffer it allocates on first
+ * use; this call stages through a 16 MiB array compiled into the library (2^21 doubles), which
+ * every GPU that loads the library holds until the process exits.
+ *   U_out : host, U_out[v][c] (original numbering), nv * ncells doubles, caller-allocated.
+ * Errors: CTENO_ERR_ARG when nv * ncells > 2^21 (the staging area's size); the usual state and
+ * mesh checks. The first call on a device looks up the staging array's device address
+ * (cudaGetSymbolAddress); make that first call before any CUDA stream capture. Every call, from
+ * any context, shares the one staging array: calls whose work overlaps on the GPU (contexts on
+ * different streams at the same time) race and must be serialised by the caller. Nothing in the
+ * array needs clearing: each call writes every value it reads back. Synchronises the stream. */
+int cteno_get_state_noalloc(cteno_ctx *ctx, int32_t mesh_id, double *U_out);
+
 /* Time step used by the last step of cteno_run for each mesh: host dt_out[nmeshes]. */
 int cteno_get_dt(cteno_ctx *ctx, double *dt_out);
 

@@ -165,6 +165,30 @@ void drop_graph(cteno_ctx *ctx) {
 
 }  // namespace
 
+namespace cteno {
+
+// Host read-back of one mesh's state through a caller-supplied device staging area of
+// `capacity` doubles (used by cteno_get_state_noalloc; allocates nothing).
+int get_state_staged(cteno_ctx *ctx, int32_t mesh_id, double *U_out, double *stage, int64_t capacity) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if ((rc = check_mesh(ctx, mesh_id))) return rc;
+  if (!U_out) return fail(ctx, CTENO_ERR_ARG, "null output");
+  const Mesh &m = ctx->meshes[mesh_id];
+  const int64_t cnt = (int64_t)ctx->nv * m.ncells;
+  if (cnt > capacity)
+    return fail(ctx, CTENO_ERR_ARG, "mesh state has " + std::to_string(cnt) +
+                                        " values; the allocation-free staging area holds " +
+                                        std::to_string(capacity));
+  launch_permute_out(ctx->nv, lay_nvp(ctx->d), m.ncells, m.offset, ctx->d_rank[mesh_id], ctx->U, stage,
+                     ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(U_out, stage, cnt * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return device_status(ctx);
+}
+
+}  // namespace cteno
+
 extern "C" {
 
 void cteno_default_params(cteno_params *p) {

@@ -54,6 +54,7 @@ def load_library():
         "cteno_rk_stage": (I, [V, I, V]),
         "cteno_run": (I, [V, I]),
         "cteno_get_state": (I, [V, C.c_int32, V, I]),
+        "cteno_get_state_noalloc": (I, [V, C.c_int32, V]),
         "cteno_get_dt": (I, [V, V]),
         "cteno_record_flags": (I, [V, I]),
         "cteno_get_flags": (I, [V, C.c_int32, V]),
@@ -149,6 +150,15 @@ def cteno_get_state(ctx, mesh_id: int, out=None, is_device: bool = False):
     if out is None:
         out = np.empty((info[4], info[7]))
     _check(ctx, load_library().cteno_get_state(ctx, mesh_id, _ptr(out), 0))
+    return out
+
+
+def cteno_get_state_noalloc(ctx, mesh_id: int, out=None):
+    """Host read-back through the library's fixed staging array (no device allocation)."""
+    info = cteno_info(ctx, mesh_id)
+    if out is None:
+        out = np.empty((info[4], info[7]))
+    _check(ctx, load_library().cteno_get_state_noalloc(ctx, mesh_id, _ptr(out)))
     return out
 
 
