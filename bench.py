@@ -11,6 +11,10 @@ with CTENO at degree 2; `variants` gives every scheme / degree / precision combi
 workload. L2 (129 MB) is flushed between timed steps by a 256 MB write outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload shock_tube_2d|density_wave_3d_64|blast_3d_96|batch_2d] [--profile]
+
+The default workload is the shock tube; the others are the 3D and batched configurations, measured
+with the same line format (--profile runs only warm-up + steps of the headline variant, for ncu).
 
 Under torchrun each rank advances its own replica of the workload (the path does not shard
 within a mesh: replicas only); value = cells x stages of all ranks / max over ranks of the time.
@@ -34,10 +38,48 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mcell-RK-stage/s (deg 2/3, 2D tri & 3D tet), FP32-mixed vs FP64 on one GB300"
 UNIT = "Mcell-RK-stage/s"
-NX, NY, CFL = 512, 128, 0.4
-HEADLINE = dict(scheme=0, degree=2, precision=1)
 SCHEMES = {0: "CTENO", 1: "CTENOZ"}
 PRECISIONS = {0: "fp64", 1: "mixed"}
+
+
+class Case:
+    """A workload: meshes + initial states + the scheme it is defined with."""
+
+    def __init__(self, name, description, meshes, states, dim, scheme, degree, cfl, variants):
+        self.name, self.description = name, description
+        self.meshes, self.states, self.dim = meshes, states, dim
+        self.scheme, self.degree, self.cfl = scheme, degree, cfl
+        self.variants = variants          # (scheme, degree) pairs timed in both precisions
+        self.ncells = sum(m.ncells for m in meshes)
+
+
+def make_case(name, n=0):
+    import workloads as W
+    if name == "shock_tube_2d":
+        wl = W.shock_tube_2d(512, 128)
+        return Case(name, "2D shock tube [0,1]x[0,0.25], 512x128 squares -> 131072 triangles, jitter 0.1h, "
+                    "Sod states, transmissive, CFL 0.4", [wl.mesh], [wl.U0], 2, 0, 2, 0.4,
+                    [(0, 2), (0, 3), (1, 2), (1, 3)])
+    if name == "density_wave_3d_64":
+        n = n or 64
+        wl = W.density_wave_3d(n)
+        return Case(name, f"3D periodic unit cube, {n}^3 cubes x 6 tetrahedra -> {wl.mesh.ncells} cells, "
+                    "jitter 0.08h, density wave, CFL 0.5", [wl.mesh], [wl.U0], 3, 0, 2, 0.5, [(0, 2)])
+    if name == "blast_3d_96":
+        n = n or 96
+        wl = W.blast_3d(n)
+        return Case(name, f"3D unit cube, {n}^3 cubes x 6 tetrahedra -> {wl.mesh.ncells} cells, jitter 0.08h, "
+                    "blast p=10 in r<0.2, transmissive, CFL 0.3", [wl.mesh], [wl.U0], 3, 0, 3, 0.3, [(0, 3)])
+    if name == "batch_2d":
+        wls = W.quadrants_batch(64, seed=0)
+        return Case(name, f"64 independent triangle meshes, side log-uniform in [16,256] -> "
+                    f"{sum(w.mesh.ncells for w in wls)} cells, four-quadrant Riemann states, CFL 0.4, "
+                    "one launch per kernel for all meshes", [w.mesh for w in wls], [w.U0 for w in wls],
+                    2, 1, 2, 0.4, [(1, 2)])
+    raise ValueError(name)
+
+
+HEADLINE = dict(precision=1)
 
 
 def variant_name(scheme, degree, precision):
@@ -53,6 +95,15 @@ def parse():
     ap.add_argument("--variant-steps", type=int, default=60)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="shock_tube_2d",
+                    choices=["shock_tube_2d", "density_wave_3d_64", "blast_3d_96", "batch_2d"])
+    ap.add_argument("--n", type=int, default=0,
+                    help="override the mesh size of a 3D workload (cubes per side), e.g. for ncu")
+    ap.add_argument("--launch", default="",
+                    help="R,F launch values (cteno_set_launch convention) instead of autotuning")
+    ap.add_argument("--profile", action="store_true",
+                    help="only run the headline variant (warm-up + steps, no timing extras): a short "
+                         "command for ncu")
     return ap.parse_args()
 
 
@@ -175,9 +226,12 @@ def ncu_traffic(variant):
     return d.get("bytes_per_launch", {}).get(variant)
 
 
-def make_solver(native, mesh, scheme, degree, precision, stream):
-    return native.Solver([mesh], 2, degree=degree, scheme=scheme, precision=precision, stream=stream,
-                         cfl=CFL)
+def make_solver(native, case, scheme, degree, precision, stream):
+    s = native.Solver(case.meshes, case.dim, degree=degree, scheme=scheme, precision=precision,
+                      stream=stream, cfl=case.cfl)
+    for k, U in enumerate(case.states):
+        s.set_state(U, k)
+    return s
 
 
 def time_steps(native, s, steps, warmup, flush, torch, kernel_times=False):
@@ -203,22 +257,32 @@ def time_steps(native, s, steps, warmup, flush, torch, kernel_times=False):
 def run_ours(args, rank, world, local):
     import torch
 
-    import workloads as W
     from paper_2312_17042_gb300 import build as B, native
 
     B.build()
     torch.cuda.set_device(local)
     dist = Dist(world, "nccl")
     stream = torch.cuda.current_stream().cuda_stream
-    wl = W.shock_tube_2d(NX, NY)
-    ncells = wl.mesh.ncells
+    case = make_case(args.workload, args.n)
+    ncells = case.ncells
+    nv = case.dim + 2
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     # headline ---------------------------------------------------------------------------------
-    h = HEADLINE
-    s = make_solver(native, wl.mesh, h["scheme"], h["degree"], h["precision"], stream)
-    s.set_state(wl.U0)
-    blocks = native.cteno_autotune(s.ctx)
+    h = dict(scheme=case.scheme, degree=case.degree, precision=HEADLINE["precision"])
+    s = make_solver(native, case, h["scheme"], h["degree"], h["precision"], stream)
+    if args.launch:
+        blocks = tuple(int(x) for x in args.launch.split(","))
+        native.cteno_set_launch(s.ctx, *blocks)
+    else:
+        blocks = native.cteno_autotune(s.ctx)
+    if args.profile:
+        time_steps(native, s, args.steps, args.warmup, flush, torch)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.workload, "blocks": blocks, "guard": s.sync()}))
+        s.close()
+        dist.close()
+        return
     native.cteno_set_timing(s.ctx, True)
     stats = native.cteno_kernel_stats(s.ctx)
     clocks = ClockSampler(local)
@@ -236,91 +300,90 @@ def run_ours(args, rank, world, local):
     flux_ms_launch = float(kms[:, 1].mean()) / 3.0
     peaks, peak_kind = measured_peaks()
     achieved = stats[0] / (recon_ms_launch * 1e-3) / 1e9
-    hv = variant_name(**h)
-    roofline = {"kernel": "recon_kernel<2,2,float,CTENO>", "bound": "hbm", "achieved": round(achieved, 1),
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "traffic": ncu_traffic(hv), "algorithmic_bytes_per_launch": stats[0],
-                "launch_ms": round(recon_ms_launch, 5), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+    hv = f"{args.workload}:" + variant_name(**h)
+    roofline = {"kernel": f"recon_kernel<{case.dim},{h['degree']},float,{SCHEMES[h['scheme']]}>", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(hv),
+                "algorithmic_bytes_per_launch": stats[0], "launch_ms": round(recon_ms_launch, 5),
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                 "flux_kernel": {"achieved_gbs": round(stats[1] / (flux_ms_launch * 1e-3) / 1e9, 1),
                                 "launch_ms": round(flux_ms_launch, 5),
                                 "algorithmic_bytes_per_launch": stats[1]}}
     native.cteno_set_timing(s.ctx, False)
 
     # end to end through the C ABI with host buffers -------------------------------------------
-    e2e = None
-    if rank == 0 or world > 1:
-        pinned = torch.empty((4, ncells), dtype=torch.float64, pin_memory=True)
-        host = pinned.numpy()
-        host[:] = s.get_state()
-        out = torch.empty((4, ncells), dtype=torch.float64, pin_memory=True).numpy()
-        n_e2e = max(5, min(args.steps, 100))
-        torch.cuda.synchronize()
-        t_total = 0.0
-        for k in range(n_e2e + 2):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            native.cteno_set_state(s.ctx, 0, host)
-            s.run(1)
-            native.cteno_get_state(s.ctx, 0, out)
-            b.record()
-            b.synchronize()
-            if k >= 2:
-                t_total += a.elapsed_time(b)
-        e2e = {"value": round(ncells * 3 * n_e2e / (t_total * 1e-3) / 1e6 * world, 2), "unit": UNIT,
-               "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(out.nbytes),
-               "steps": n_e2e, "api": "cteno_set_state(host) + cteno_run(1) + cteno_get_state(host)"}
+    pinned = [torch.empty((nv, m.ncells), dtype=torch.float64, pin_memory=True).numpy() for m in case.meshes]
+    outs = [torch.empty((nv, m.ncells), dtype=torch.float64, pin_memory=True).numpy() for m in case.meshes]
+    for k in range(len(case.meshes)):
+        pinned[k][:] = s.get_state(k)
+    n_e2e = max(5, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t_total = 0.0
+    for it in range(n_e2e + 2):
+        flush.zero_()
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k in range(len(case.meshes)):
+            native.cteno_set_state(s.ctx, k, pinned[k])
+        s.run(1)
+        for k in range(len(case.meshes)):
+            native.cteno_get_state(s.ctx, k, outs[k])
+        b_.record()
+        b_.synchronize()
+        if it >= 2:
+            t_total += a.elapsed_time(b_)
+    t_total = dist.max(t_total, device="cuda")
+    e2e = {"value": round(world * ncells * 3 * n_e2e / (t_total * 1e-3) / 1e6, 2), "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(p.nbytes for p in pinned)),
+           "d2h_bytes_per_step": int(sum(o.nbytes for o in outs)), "steps": n_e2e,
+           "api": "cteno_set_state(host) + cteno_run(1) + cteno_get_state(host), pinned buffers"}
     s.close()
 
-    # other variants -----------------------------------------------------------------------------
+    # variants: every timed (scheme, degree) of the workload in both precisions -------------------
     variants = {}
+    alu = None
     if not args.no_variants:
         alu = alu_peak(native)
-        for scheme in (0, 1):
-            for degree in (2, 3):
-                for precision in (1, 0):
-                    name = variant_name(scheme, degree, precision)
-                    sv = make_solver(native, wl.mesh, scheme, degree, precision, stream)
-                    sv.set_state(wl.U0)
-                    native.cteno_autotune(sv.ctx)
-                    native.cteno_set_timing(sv.ctx, True)
-                    st = native.cteno_kernel_stats(sv.ctx)
-                    vms, vk = time_steps(native, sv, args.variant_steps, 3, flush, torch, kernel_times=True)
-                    tot = dist.max(sum(vms), device="cuda")
-                    r_ms = float(vk[:, 0].mean()) / 3
-                    entry = {"value": round(world * ncells * 3 * args.variant_steps / (tot * 1e-3) / 1e6, 2),
-                             "ms_per_step": round(tot / args.variant_steps, 4),
-                             "recon_ms_per_launch": round(r_ms, 5),
-                             "flux_ms_per_launch": round(float(vk[:, 1].mean()) / 3, 5)}
-                    if precision == 1:
-                        entry["recon_gbs"] = round(st[0] / (r_ms * 1e-3) / 1e9, 1)
-                        entry["recon_hbm_frac"] = round(entry["recon_gbs"] / peaks["hbm_gbs"], 4)
-                    else:
-                        tfl = st[2] / (r_ms * 1e-3) / 1e12
-                        entry["recon_fp64_tflops"] = round(tfl, 3)
-                        if alu.get("fp64_tflops"):
-                            entry["recon_fp64_alu_frac"] = round(tfl / alu["fp64_tflops"], 4)
-                    variants[name] = entry
-                    sv.close()
-        for scheme in (0, 1):
-            for degree in (2, 3):
-                m, f = variants[variant_name(scheme, degree, 1)], variants[variant_name(scheme, degree, 0)]
-                m["speedup_vs_fp64"] = round(m["value"] / f["value"], 2)
+        for scheme, degree in case.variants:
+            for precision in (1, 0):
+                name = variant_name(scheme, degree, precision)
+                sv = make_solver(native, case, scheme, degree, precision, stream)
+                native.cteno_autotune(sv.ctx)
+                native.cteno_set_timing(sv.ctx, True)
+                st = native.cteno_kernel_stats(sv.ctx)
+                vms, vk = time_steps(native, sv, args.variant_steps, 3, flush, torch, kernel_times=True)
+                tot = dist.max(sum(vms), device="cuda")
+                r_ms = float(vk[:, 0].mean()) / 3
+                entry = {"value": round(world * ncells * 3 * args.variant_steps / (tot * 1e-3) / 1e6, 2),
+                         "ms_per_step": round(tot / args.variant_steps, 4),
+                         "recon_ms_per_launch": round(r_ms, 5),
+                         "flux_ms_per_launch": round(float(vk[:, 1].mean()) / 3, 5)}
+                if precision == 1:
+                    entry["recon_gbs"] = round(st[0] / (r_ms * 1e-3) / 1e9, 1)
+                    entry["recon_hbm_frac"] = round(entry["recon_gbs"] / peaks["hbm_gbs"], 4)
+                else:
+                    tfl = st[2] / (r_ms * 1e-3) / 1e12
+                    entry["recon_fp64_tflops"] = round(tfl, 3)
+                    entry["recon_fp64_alu_frac"] = round(tfl / alu["fp64_tflops"], 4)
+                variants[name] = entry
+                sv.close()
+        for scheme, degree in case.variants:
+            m, f = variants[variant_name(scheme, degree, 1)], variants[variant_name(scheme, degree, 0)]
+            m["speedup_vs_fp64"] = round(m["value"] / f["value"], 2)
 
     # CPU baseline: the oracle on the host cores ---------------------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_timing(wl, HEADLINE, steps=2)
+        cpu = oracle_timing(case, h)
 
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (reconstruction, flux) + f64 (accumulation)",
-        "data": "synthetic (seeded jittered triangle mesh, Sod initial data)",
-        "config": {"workload": f"2D shock tube [0,1]x[0,0.25], {NX}x{NY} squares -> {ncells} triangles, "
-                               "jitter 0.1h, transmissive, CFL 0.4",
-                   "scheme": SCHEMES[h["scheme"]], "degree": h["degree"], "precision": "mixed",
-                   "cells": ncells, "l2": "flushed before every timed step (256 MB write, untimed)",
+        "data": "synthetic (seeded jittered simplex meshes, analytic initial data)",
+        "config": {"workload": case.description, "scheme": SCHEMES[h["scheme"]], "degree": h["degree"],
+                   "precision": "mixed", "cells": ncells,
+                   "l2": "flushed before every timed step (256 MB write, untimed)",
                    "parallelism": f"replicas x{world}", "recon_block": blocks[0], "flux_block": blocks[1],
                    "positivity_guard_cells": int(guard)},
         "roofline": roofline,
@@ -329,27 +392,36 @@ def run_ours(args, rank, world, local):
         "gpu_launches": 6 * args.steps,
         "clocks": clk,
         "variants": variants,
-        "alu_peak_measured": alu if not args.no_variants else None,
+        "alu_peak_measured": alu,
     }
     dist.close()
     if rank == 0:
         print(json.dumps(result))
 
 
-def oracle_timing(wl, h, steps):
+def oracle_timing(case, h, budget_s=20.0):
+    """The oracle, as it stands, on the host cores: SSP-RK3 steps of the full first mesh of the
+    workload (a smaller mesh of the same construction when that mesh is large), set-up excluded."""
+    import workloads as W
     from oracle import Oracle, num_threads
+    mesh, U0, note = case.meshes[0], case.states[0], "the full first mesh"
+    if mesh.ncells > 400000:   # 3D workloads: same construction at n = 16
+        sub = W.density_wave_3d(16) if case.name.startswith("density") else W.blast_3d(16)
+        mesh, U0, note = sub.mesh, sub.U0, f"the same construction at n=16 ({sub.mesh.ncells} cells)"
     t0 = time.perf_counter()
-    o = Oracle(wl.mesh, degree=h["degree"], scheme=h["scheme"], cfl=CFL)
+    o = Oracle(mesh, degree=h["degree"], scheme=h["scheme"], cfl=case.cfl)
     setup = time.perf_counter() - t0
-    o.set_state(wl.U0)
-    t0 = time.perf_counter()
-    for _ in range(steps):
+    o.set_state(U0)
+    steps, t = 0, 0.0
+    while steps < 2 or (t < budget_s / 4 and steps < 20):
+        t0 = time.perf_counter()
         o.step(0.0)
-    t = time.perf_counter() - t0
-    return {"value": round(wl.mesh.ncells * 3 * steps / t / 1e6, 4), "unit": UNIT, "cores": num_threads(),
+        t += time.perf_counter() - t0
+        steps += 1
+    return {"value": round(mesh.ncells * 3 * steps / t / 1e6, 4), "unit": UNIT, "cores": num_threads(),
             "kind": "oracle",
-            "sample": f"{steps} SSP-RK3 steps of the full {wl.mesh.ncells}-cell mesh, "
-                      f"{SCHEMES[h['scheme']]} degree {h['degree']}, FP64; set-up ({setup:.1f} s) excluded"}
+            "sample": f"{steps} SSP-RK3 steps of {note}, {SCHEMES[h['scheme']]} degree {h['degree']}, FP64; "
+                      f"set-up ({setup:.1f} s) excluded"}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -358,14 +430,13 @@ def oracle_timing(wl, h, steps):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    import workloads as W
     from oracle import Oracle, num_threads
-    wl = W.shock_tube_2d(NX, NY)
-    h = HEADLINE
-    o = Oracle(wl.mesh, degree=h["degree"], scheme=h["scheme"], cfl=CFL)
-    o.set_state(wl.U0)
-    # each step is one SSP-RK3 step of the whole mesh; the number of timed steps is capped so the
-    # run stays within about a minute
+    case = make_case(args.workload, args.n)
+    mesh, U0 = case.meshes[0], case.states[0]
+    o = Oracle(mesh, degree=case.degree, scheme=case.scheme, cfl=case.cfl)
+    o.set_state(U0)
+    # each step is one SSP-RK3 step of the whole (first) mesh; the number of timed steps is capped
+    # so the run stays within about a minute
     t0 = time.perf_counter()
     o.step(0.0)
     per = time.perf_counter() - t0
@@ -377,15 +448,14 @@ def run_reference(args, rank, world):
     for _ in range(steps):
         o.step(0.0)
     t = time.perf_counter() - t0
-    value = wl.mesh.ncells * 3 * steps / t / 1e6
+    value = mesh.ncells * 3 * steps / t / 1e6
     sample = (f"{steps} SSP-RK3 steps (of {args.steps} requested, capped to ~1 min) of the full "
-              f"{wl.mesh.ncells}-cell mesh, {SCHEMES[h['scheme']]} degree {h['degree']}, FP64")
+              f"{mesh.ncells}-cell mesh, {SCHEMES[case.scheme]} degree {case.degree}, FP64")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": warm, "ms_per_step": round(t / steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"2D shock tube, {NX}x{NY} squares -> {wl.mesh.ncells} triangles",
-                   "scheme": SCHEMES[h["scheme"]], "degree": h["degree"]},
+        "config": {"workload": case.description, "scheme": SCHEMES[case.scheme], "degree": case.degree},
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": num_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

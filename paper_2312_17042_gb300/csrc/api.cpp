@@ -618,8 +618,16 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count) {
 
 int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
   if (!ctx) return CTENO_ERR_ARG;
-  auto ok = [](int b) { return b == 0 || (b >= 32 && b <= 256 && b % 32 == 0); };
-  if (!ok(recon_block) || !ok(flux_block)) return fail(ctx, CTENO_ERR_ARG, "block size must be a multiple of 32 in [32, 256]");
+  // positive: block size of the uncapped kernel; negative: block size of the register-capped
+  // variant (mixed path only, at most 128 threads)
+  auto ok = [&](int b, bool recon) {
+    if (b == 0) return true;
+    if (recon && b >= kLaneSchedule) return b - kLaneSchedule >= 32 && b - kLaneSchedule <= 256 && b % 32 == 0;
+    if (b < 0) return ctx->fp32 && -b >= 32 && -b <= 128 && (-b) % 32 == 0;
+    return b >= 32 && b <= 256 && b % 32 == 0;
+  };
+  if (!ok(recon_block, true) || !ok(flux_block, false))
+    return fail(ctx, CTENO_ERR_ARG, "block size must be a multiple of 32 in [32, 256] (capped: [32, 128], mixed path)");
   if (recon_block) ctx->recon_block = recon_block;
   if (flux_block) ctx->flux_block = flux_block;
   drop_graph(ctx);
@@ -653,12 +661,21 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int cand[] = {64, 128, 256};
+  // candidates: uncapped kernels at 64/128/256 threads; on the mixed path also the
+  // register-capped variants (8 blocks per SM) at 64/128 threads (negative values)
+  std::vector<int> cand = {64, 128, 256};
+  if (ctx->fp32) {
+    cand.push_back(-64);
+    cand.push_back(-128);
+  }
+  // reconstruction only: the variable-per-lane schedule
+  std::vector<int> rcand = cand;
+  for (int b : {128, 256}) rcand.push_back(kLaneSchedule + b);
   const int reps = 5;
   float best_r = 1e30f, best_f = 1e30f;
   int br = ctx->recon_block, bf = ctx->flux_block;
   const KArgs a = make_args(ctx, 1, 0);  // stage 1: reads U^n, writes U only
-  for (int b : cand) {  // the reconstruction writes only face states: no restore needed
+  for (int b : rcand) {  // the reconstruction writes only face states: no restore needed
     launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, b, ctx->stream);
     CK(cudaEventRecord(e0, ctx->stream));
     for (int r = 0; r < reps; ++r) launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, b, ctx->stream);

@@ -117,6 +117,11 @@ struct SetupArgs {
   int *err;
 };
 
+// Launch-value convention of the reconstruction kernel: b in [32, 256] one thread per cell;
+// -b the register-capped thread-per-cell variant; kLaneSchedule + b the variable-per-lane
+// schedule with b threads per block.
+constexpr int kLaneSchedule = 1024;
+
 void launch_setup(int dim, int degree, const SetupArgs &a, cudaStream_t s);
 // Upload the (d, r) smoothness matrix and face-point basis values to the constant banks of the
 // reconstruction kernels.

@@ -122,8 +122,8 @@ __device__ __forceinline__ double local_dt(const KArgs &a, int64_t i, const doub
   return 1.0 / ((double)s * a.vol[i]);
 }
 
-template <int D, typename T>
-__global__ void __launch_bounds__(256) flux_kernel(const KArgs a) {
+template <int D, typename T, int MINB>
+__global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel(const KArgs a) {
   using L = Lay<D>;
   constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, FB = NQ * NV;
   constexpr bool F32 = sizeof(T) == 4;
@@ -147,42 +147,53 @@ __global__ void __launch_bounds__(256) flux_kernel(const KArgs a) {
   double acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  // faces in groups of FG: all loads of a group are issued before its arithmetic
+  constexpr int FG = (D == 2) ? NF : 2;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const int64_t j = nbv[f];
-    const int fj = (meta >> (2 * f)) & 3u;
-    const bool own = (meta >> (kMetaOwnerShift + f)) & 1u;
-    T gf[4];
-    load16<T, 4>(G + (i * NF + f) * 4, gf);
-    T n[D];
+  for (int f0 = 0; f0 < NF; f0 += FG) {
+    T gf[FG][4], uI[FG][FB], uO[FG][FB];
 #pragma unroll
-    for (int k = 0; k < D; ++k) n[k] = own ? gf[k] : -gf[k];
-    const T area = gf[3];
-    T uI[FB], uO[FB], Ff[NV];
-    load16<T, FB>(Uf + (i * NF + f) * FB, uI);
-    if (j >= 0) {
-      load16<T, FB>(Uf + (j * NF + fj) * FB, uO);
-    } else {  // transmissive boundary: the cell mean outside
+    for (int ff = 0; ff < FG; ++ff) {
+      const int f = f0 + ff;
+      if (f >= NF) break;
+      const int64_t j = nbv[f];
+      const int fj = (meta >> (2 * f)) & 3u;
+      load16<T, 4>(G + (i * NF + f) * 4, gf[ff]);
+      load16<T, FB>(Uf + (i * NF + f) * FB, uI[ff]);
+      if (j >= 0) {
+        load16<T, FB>(Uf + (j * NF + fj) * FB, uO[ff]);
+      } else {  // transmissive boundary: the cell mean outside
 #pragma unroll
-      for (int q = 0; q < NQ; ++q)
+        for (int q = 0; q < NQ; ++q)
 #pragma unroll
-        for (int v = 0; v < NV; ++v) uO[q * NV + v] = (T)u64[v];
-    }
-    // face flux |A| sum_q w_q F_q in the path's type: both cells of the face evaluate it with
-    // the same operands in the same order, so the two values are identical
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      T F[NV];
-      if (own) hllc<D, T>(uI + q * NV, uO + q * NV, n, g, F);
-      else hllc<D, T>(uO + q * NV, uI + q * NV, n, g, F);
-      const T w = (T)a.fw[q];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) Ff[v] = (q == 0) ? w * F[v] : Ff[v] + w * F[v];
+          for (int v = 0; v < NV; ++v) uO[ff][q * NV + v] = (T)u64[v];
+      }
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const double fv = (double)(area * Ff[v]);
-      acc[v] += own ? fv : -fv;  // FP64 accumulation over the faces (conservation)
+    for (int ff = 0; ff < FG; ++ff) {
+      const int f = f0 + ff;
+      if (f >= NF) break;
+      const bool own = (meta >> (kMetaOwnerShift + f)) & 1u;
+      T n[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) n[k] = own ? gf[ff][k] : -gf[ff][k];
+      // face flux |A| sum_q w_q F_q in the path's type: both cells of the face evaluate it with
+      // the same operands in the same order, so the two values are identical
+      T Ff[NV];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        T F[NV];
+        if (own) hllc<D, T>(uI[ff] + q * NV, uO[ff] + q * NV, n, g, F);
+        else hllc<D, T>(uO[ff] + q * NV, uI[ff] + q * NV, n, g, F);
+        const T w = (T)a.fw[q];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Ff[v] = (q == 0) ? w * F[v] : Ff[v] + w * F[v];
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double fv = (double)(gf[ff][3] * Ff[v]);
+        acc[v] += own ? fv : -fv;  // FP64 accumulation over the faces (conservation)
+      }
     }
   }
   // residual and SSP-RK3 (Shu-Osher) stage update in FP64
@@ -276,11 +287,19 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 }  // namespace
 
 void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s) {
+  const bool capped = block < 0;  // register-capped variant (FP32 only)
+  if (capped) block = -block;
   const unsigned grid = grid_for(a.N, block);
-  if (dim == 2 && fp32) flux_kernel<2, float><<<grid, block, 0, s>>>(a);
-  if (dim == 2 && !fp32) flux_kernel<2, double><<<grid, block, 0, s>>>(a);
-  if (dim == 3 && fp32) flux_kernel<3, float><<<grid, block, 0, s>>>(a);
-  if (dim == 3 && !fp32) flux_kernel<3, double><<<grid, block, 0, s>>>(a);
+  if (dim == 2 && fp32) {
+    if (capped) flux_kernel<2, float, 8><<<grid, block, 0, s>>>(a);
+    else flux_kernel<2, float, 0><<<grid, block, 0, s>>>(a);
+  }
+  if (dim == 3 && fp32) {
+    if (capped) flux_kernel<3, float, 8><<<grid, block, 0, s>>>(a);
+    else flux_kernel<3, float, 0><<<grid, block, 0, s>>>(a);
+  }
+  if (dim == 2 && !fp32) flux_kernel<2, double, 0><<<grid, block, 0, s>>>(a);
+  if (dim == 3 && !fp32) flux_kernel<3, double, 0><<<grid, block, 0, s>>>(a);
 }
 
 void launch_dt(int dim, const KArgs &a, cudaStream_t s) {

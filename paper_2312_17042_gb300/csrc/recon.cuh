@@ -181,8 +181,10 @@ __device__ __forceinline__ uint32_t select_fp32(float SI0, const float *SId, uin
   return bits;
 }
 
-template <int D, int R, typename T, int SCHEME>
-__global__ void __launch_bounds__(256) recon_kernel(const KArgs a) {
+// MINB > 0: register-capped variant (at most 128 threads per block, MINB blocks per SM), which the
+// autotuner weighs against the uncapped one (occupancy and wave count against spills).
+template <int D, int R, typename T, int SCHEME, int MINB>
+__global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kernel(const KArgs a) {
   using S = Shape<D, R>;
   using L = Lay<D>;
   constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, ND = L::ND, PDS = L::PDS;
@@ -436,6 +438,243 @@ __global__ void __launch_bounds__(256) recon_kernel(const KArgs a) {
     a.dt[i] = a.dt[a.nmesh + i];
     a.dt[a.nmesh + i] = 1e300;
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Variable-per-lane schedule: a group of NV consecutive lanes reconstructs one cell, lane v the
+// conserved variable v. The steps above are independent across variables up to the positivity
+// guard, so each lane keeps only its own coefficients (K-1 central + d(d+1) directional), all
+// lanes of a group read the same pseudo-inverse chunk (one broadcast request) and the gathers of a
+// neighbour's record are split over the group. A warp holds floor(32 / NV) cells; spare lanes
+// and lanes past the last cell work on a clamped cell and store nothing.
+// ---------------------------------------------------------------------------------------------
+template <int D, int R, typename T, int SCHEME>
+__global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, ND = L::ND, PDS = L::PDS;
+  constexpr int NK = S::NK, M = S::M, NP = S::NP;
+  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
+  constexpr int CH = Vec16<T>::n;
+  constexpr int CPW = 32 / NV;  // cells per warp
+  constexpr bool F32 = sizeof(T) == 4;
+  __shared__ T sPhi[NPHI];
+  if constexpr (D == 3) {
+    const DevTables &tb = *a.tab;
+    for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
+      const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
+      sPhi[t] = (T)tb.Phi[f][p][q][k];
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / NV;                // cell slot in the warp (CPW = spare lanes)
+  const int v = lane - grp * NV;            // this lane's variable
+  const int base = grp * NV;                // first lane of the group
+  const int64_t N = a.N;
+  const int64_t cell = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * CPW + grp;
+  const bool active = grp < CPW && cell < N;
+  const int64_t i = active ? cell : N - 1;  // spare lanes shadow a valid cell
+
+  // own mean of variable v: FP64, or the FP32 pair (hi, lo)
+  T U0;
+  float L0;
+  if constexpr (F32) {
+    const float2 h = __ldg(reinterpret_cast<const float2 *>(a.U32) + i * NVP + v);
+    U0 = h.x;
+    L0 = h.y;
+  } else {
+    U0 = (T)__ldg(a.U + i * NVP + v);
+    L0 = 0.0f;
+  }
+  auto delta = [&](int64_t j) -> T {
+    if constexpr (F32) {
+      const float2 h = __ldg(reinterpret_cast<const float2 *>(a.U32) + j * NVP + v);
+      return (h.x - (float)U0) + (h.y - L0);
+    } else {
+      return (T)(__ldg(a.U + j * NVP + v) - (double)U0);
+    }
+  };
+
+  // central coefficients of variable v
+  const int32_t *__restrict__ sti = a.st + i * M;
+  const T *__restrict__ Pci = (const T *)a.Pc + i * (int64_t)(M * NK);
+  T ao[NK];
+#pragma unroll
+  for (int k = 0; k < NK; ++k) ao[k] = (T)0;
+  {
+    T pb[CH], du = (T)0;
+    int ids[4];
+#pragma unroll
+    for (int e = 0; e < M * NK; ++e) {
+      const int m = e / NK, k = e % NK;
+      if (e % CH == 0) load16<T, CH>(Pci + e, pb);
+      if (k == 0) {
+        if (m % 4 == 0) {
+          const int4 t4 = __ldg(reinterpret_cast<const int4 *>(sti + m));
+          ids[0] = t4.x; ids[1] = t4.y; ids[2] = t4.z; ids[3] = t4.w;
+        }
+        du = delta(ids[m % 4]);
+      }
+      ao[k] += pb[e % CH] * du;
+    }
+  }
+  // directional coefficients of variable v
+  const uint32_t info = __ldg(a.cinfo + i);
+  const uint32_t adm = (info >> kInfoAdmShift) & 0xFu;
+  T ad[NF][D];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int k = 0; k < D; ++k) ad[f][k] = (T)0;
+  {
+    int off = 0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int nm = (info >> (4 * f)) & 15u;
+      if ((adm >> f) & 1u) {
+        T pf[PDS];
+        load16<T, PDS>((const T *)a.Pd + (i * NF + f) * PDS, pf);
+#pragma unroll
+        for (int jj = 0; jj < ND; ++jj) {
+          if (jj < nm) {
+            const T du = delta(__ldg(sti + off + jj));
+#pragma unroll
+            for (int k = 0; k < D; ++k) ad[f][k] += pf[jj * D + k] * du;
+          }
+        }
+      }
+      off += nm;
+    }
+  }
+  // p_1, smoothness indicators, selection (eqs. 15-23), final coefficients in ao
+  const int stn = 1 + __popc(adm);
+  T lams;
+  double lamsd = 0.0;
+  float log2lams = 0.0f;
+  if constexpr (F32) {
+    lams = (stn > 1) ? (float)a.one_m_lam1 / (float)(stn - 1) : 0.0f;
+    if (stn > 1) log2lams = a.log2_one_m_lam1 - log2f((float)(stn - 1));
+  } else {
+    lamsd = (stn > 1) ? a.one_m_lam1 / (stn - 1) : 0.0;
+    lams = lamsd;
+  }
+  constexpr T INV_FACT = (D == 2) ? (T)0.5 : (T)(1.0 / 6.0);
+  {
+    T a1[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) a1[k] = ao[k];
+    if (stn > 1) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        T s = (T)0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) s += ad[f][k];
+        a1[k] -= lams * s;
+      }
+      const T inv_lam1 = (T)a.inv_lam1;
+#pragma unroll
+      for (int k = 0; k < NK; ++k) a1[k] *= inv_lam1;
+    }
+    T SI0 = (T)0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      T rr = (T)0;
+#pragma unroll
+      for (int l = 0; l < NK; ++l) rr += cO<T, R>(k * NK + l) * a1[l];
+      SI0 += a1[k] * rr;
+    }
+    T SId[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T s = (T)0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += ad[f][k] * ad[f][k];
+      SId[f] = s * INV_FACT;
+    }
+    uint32_t bits;
+    if constexpr (F32) {
+      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.log2_lam1, log2lams,
+                             fmaxf((float)a.eps, 1e-40f), (float)a.C_T);
+    } else {
+      bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
+    }
+    if (bits & 1u) {
+#pragma unroll
+      for (int k = 0; k < NK; ++k) ao[k] = a1[k];
+    } else {
+      const T w = (T)1 / (T)__popc(bits >> 1);
+#pragma unroll
+      for (int k = 0; k < NK; ++k) ao[k] = (T)0;
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        if ((bits >> (1 + f)) & 1u) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) ao[k] += w * ad[f][k];
+        }
+    }
+    if (a.flags && active) a.flags[v * N + i] = (uint8_t)((bits & 1u) ? 1u : bits);
+  }
+
+  // face values of variable v; the positivity guard gathers rho, momentum and E of each point
+  // from the group's lanes
+  T *__restrict__ Ufi = (T *)a.Uf + i * (int64_t)(NF * NQ * NV);
+  const uint32_t perm = info >> kInfoPermShift;
+  const T gm1 = (T)(a.gamma - 1.0);
+  bool bad = false;
+  T fv[NF][NQ];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int p = (perm >> (3 * f)) & 7u;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      T val = (T)L0;
+      if constexpr (D == 2) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) val += cPhi2<T, R>((f * 2 + q) * NK + k) * ao[k];
+      } else {
+        const T *ph = &sPhi[((f * NP + p) * NQ + q) * NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) val += ph[k] * ao[k];
+      }
+      val += U0;
+      fv[f][q] = val;
+      const T rho = __shfl_sync(0xffffffffu, val, base);
+      const T E = __shfl_sync(0xffffffffu, val, base + NV - 1);
+      T ke = (T)0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const T m = __shfl_sync(0xffffffffu, val, base + 1 + j);
+        ke += m * m;
+      }
+      const T pr = gm1 * (E - (T)0.5 * ke / rho);
+      bad = bad || !(rho > (T)0) || !(pr > (T)0);
+    }
+  }
+  if (a.guard_on && bad) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) fv[f][q] = U0 + (T)L0;
+    if (active && v == 0) atomicAdd(a.guard, 1ull);
+  }
+  if (active) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int p = (perm >> (3 * f)) & 7u;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        // 2D: an edge is stored in sorted-vertex order, the swapped orientation reverses its points
+        const int qq = (D == 2 && p) ? (NQ - 1 - q) : q;
+        Ufi[(f * NQ + qq) * NV + v] = fv[f][q];
+      }
+    }
+  }
+  if (a.dt_swap && blockIdx.x == 0)
+    for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {
+      a.dt[t] = a.dt[a.nmesh + t];
+      a.dt[a.nmesh + t] = 1e300;
+    }
 }
 
 }  // namespace cteno
