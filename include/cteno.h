@@ -170,14 +170,15 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
 
 /* Launch configuration: block sizes of the reconstruction and flux kernels (0 = keep). A negative
  * value -b selects, on the mixed path, the register-capped variant of the kernel (8 resident
- * blocks per SM) with b threads per block, b in {32, 64, 96, 128}. For the reconstruction kernel,
- * 1024 + b selects the variable-per-lane schedule (one lane per conserved variable, a group of
- * d+2 lanes per cell) with b threads per block, b a multiple of 32 in [32, 256]. */
+ * blocks per SM) with b threads per block, b in {32, 64, 96, 128}. 1024 + b selects the lane
+ * schedule with b threads per block (b a multiple of 32 in [32, 256]): for the reconstruction one
+ * lane per conserved variable (d+2 lanes per cell), for the flux one lane per face (d+1 lanes per
+ * cell). */
 int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block);
 
 /* Time the candidate launch configurations (block sizes 64/128/256, on the mixed path the
- * register-capped variants at 64/128, and for the reconstruction the variable-per-lane schedule at
- * 128/256 threads) on the current state and keep the fastest; the state is
+ * register-capped variants at 64/128, and the lane schedules at 128/256 threads) on the current
+ * state and keep the fastest; the state is
  * restored afterwards. best_out[2] (may be NULL) receives the chosen values, in the convention of
  * cteno_set_launch. */
 int cteno_autotune(cteno_ctx *ctx, int32_t *best_out);

@@ -113,7 +113,17 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.one_m_lam1 = 1.0 - a.lam1;
   a.log2_lam1 = (float)std::log2(a.lam1);
   a.log2_one_m_lam1 = (float)std::log2(a.one_m_lam1);
-  for (int q = 0; q < kMaxNQ; ++q) a.fw[q] = ctx->tab.fw[q];
+  for (int q = 0; q < kMaxNQ; ++q) {
+    a.fw[q] = ctx->tab.fw[q];
+    a.fw32[q] = (float)ctx->tab.fw[q];
+  }
+  a.gamma32 = (float)ctx->p.gamma;
+  a.gm1_32 = (float)(ctx->p.gamma - 1.0);
+  a.eps32 = std::max((float)ctx->p.eps, 1e-40f);
+  a.C_T32 = (float)ctx->p.C_T;
+  a.inv_lam1_32 = (float)a.inv_lam1;
+  a.one_m_lam1_32 = (float)a.one_m_lam1;
+  a.cfl32 = (float)ctx->p.cfl;
   a.stage = stage;
   a.dt_swap = dt_swap;
   return a;
@@ -620,9 +630,9 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
   if (!ctx) return CTENO_ERR_ARG;
   // positive: block size of the uncapped kernel; negative: block size of the register-capped
   // variant (mixed path only, at most 128 threads)
-  auto ok = [&](int b, bool recon) {
+  auto ok = [&](int b, bool) {
     if (b == 0) return true;
-    if (recon && b >= kLaneSchedule) return b - kLaneSchedule >= 32 && b - kLaneSchedule <= 256 && b % 32 == 0;
+    if (b >= kLaneSchedule) return b - kLaneSchedule >= 32 && b - kLaneSchedule <= 256 && b % 32 == 0;
     if (b < 0) return ctx->fp32 && -b >= 32 && -b <= 128 && (-b) % 32 == 0;
     return b >= 32 && b <= 256 && b % 32 == 0;
   };
@@ -668,9 +678,9 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
     cand.push_back(-64);
     cand.push_back(-128);
   }
-  // reconstruction only: the variable-per-lane schedule
-  std::vector<int> rcand = cand;
-  for (int b : {128, 256}) rcand.push_back(kLaneSchedule + b);
+  // the lane schedules (variable per lane for the reconstruction, face per lane for the flux)
+  for (int b : {128, 256}) cand.push_back(kLaneSchedule + b);
+  const std::vector<int> &rcand = cand;
   const int reps = 5;
   float best_r = 1e30f, best_f = 1e30f;
   int br = ctx->recon_block, bf = ctx->flux_block;

@@ -95,6 +95,9 @@ struct KArgs {
   // lam1 = 1 - 1/lambda_1', 1/lam1, 1 - lam1 (lambda_s = (1 - lam1) / (s_t - 1)) and base-2 logs
   double lam1, inv_lam1, one_m_lam1;
   float log2_lam1, log2_one_m_lam1;
+  // FP32 copies for the mixed path (no per-thread conversions)
+  float gamma32, gm1_32, eps32, C_T32, inv_lam1_32, one_m_lam1_32, cfl32;
+  float fw32[kMaxNQ];
   double fw[kMaxNQ];        // face quadrature weights
   int stage;                // 0, 1, 2
   int dt_swap;              // stage 0 of a CFL step: move dt[next] to dt[cur] first

@@ -95,20 +95,25 @@ __device__ __forceinline__ void atomic_min_pos(double *addr, double v) {
 }
 
 // Local CFL step of one cell: |V_i| / sum_f |A_f| (|u_i . n_f| + c_i), in the path's arithmetic
-// type (FP64 geometry for the FP64 path, the FP32 copy for the mixed path).
+// type (FP64 geometry for the FP64 path; FP32 values and geometry for the mixed path, where the
+// step only sets the time-step size).
 template <int D, typename T>
 __device__ __forceinline__ double local_dt(const KArgs &a, int64_t i, const double *u64) {
   constexpr int NF = D + 1;
-  const T *G = (sizeof(T) == 4) ? (const T *)a.geo32 : (const T *)a.geo;
-  const T ir = (T)1 / (T)u64[0];
+  constexpr bool F32 = sizeof(T) == 4;
+  const T *G = F32 ? (const T *)a.geo32 : (const T *)a.geo;
+  T g, uu[D + 2];
+  if constexpr (F32) g = a.gamma32; else g = a.gamma;
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) uu[v] = (T)u64[v];
+  const T ir = (T)1 / uu[0];
   T ke = 0, u[D];
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    u[j] = (T)u64[1 + j] * ir;
-    ke += (T)u64[1 + j] * u[j];
+    u[j] = uu[1 + j] * ir;
+    ke += uu[1 + j] * u[j];
   }
-  const T g = (T)a.gamma;
-  const T p = (g - (T)1) * ((T)u64[D + 1] - (T)0.5 * ke);
+  const T p = (g - (T)1) * (uu[D + 1] - (T)0.5 * ke);
   const T c = sqrt(g * p * ir);
   T s = 0;
 #pragma unroll
@@ -119,7 +124,15 @@ __device__ __forceinline__ double local_dt(const KArgs &a, int64_t i, const doub
     for (int j = 0; j < D; ++j) un += u[j] * gf[j];
     s += gf[3] * (fabs(un) + c);
   }
-  return 1.0 / ((double)s * a.vol[i]);
+  if constexpr (F32) return (double)(1.0f / (s * (float)a.vol[i]));
+  else return 1.0 / (s * a.vol[i]);
+}
+
+// Error-free sum of two FP32 values (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
 }
 
 template <int D, typename T, int MINB>
@@ -132,7 +145,8 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
   if (i >= N) return;
   const T *__restrict__ Uf = (const T *)a.Uf;
   const T *__restrict__ G = F32 ? (const T *)a.geo32 : (const T *)a.geo;
-  const T g = (T)a.gamma;
+  T g;
+  if constexpr (F32) g = a.gamma32; else g = a.gamma;
   const uint32_t meta = __ldg(a.fmeta + i);
   const int4 nb4 = __ldg(reinterpret_cast<const int4 *>(a.nbr) + i);
   const int nbv[4] = {nb4.x, nb4.y, nb4.z, nb4.w};
@@ -145,8 +159,13 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
     u64[2 * c + 1] = x.y;
   }
   double acc[NV];
+  float acc_hi[NV], acc_lo[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  for (int v = 0; v < NV; ++v) {
+    acc[v] = 0.0;
+    acc_hi[v] = 0.0f;
+    acc_lo[v] = 0.0f;
+  }
   // faces in groups of FG: all loads of a group are issued before its arithmetic
   constexpr int FG = (D == 2) ? NF : 2;
 #pragma unroll
@@ -185,21 +204,34 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
         T F[NV];
         if (own) hllc<D, T>(uI[ff] + q * NV, uO[ff] + q * NV, n, g, F);
         else hllc<D, T>(uO[ff] + q * NV, uI[ff] + q * NV, n, g, F);
-        const T w = (T)a.fw[q];
+        T w;
+    if constexpr (F32) w = a.fw32[q]; else w = a.fw[q];
 #pragma unroll
         for (int v = 0; v < NV; ++v) Ff[v] = (q == 0) ? w * F[v] : Ff[v] + w * F[v];
       }
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const double fv = (double)(gf[ff][3] * Ff[v]);
-        acc[v] += own ? fv : -fv;  // FP64 accumulation over the faces (conservation)
+        const T x = gf[ff][3] * Ff[v];
+        const T c = own ? x : -x;  // the exact negative of the other cell's value
+        if constexpr (F32) {
+          // exact FP32 accumulation over the faces: running (hi, lo) by TwoSum
+          float s, e;
+          two_sum(acc_hi[v], c, s, e);
+          acc_hi[v] = s;
+          acc_lo[v] += e;
+        } else {
+          acc[v] += c;  // FP64 accumulation over the faces
+        }
       }
     }
   }
+  if constexpr (F32) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = (double)acc_hi[v] + (double)acc_lo[v];
+  }
   // residual and SSP-RK3 (Shu-Osher) stage update in FP64
   const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
-  const double dt = a.dt[mesh];
-  const double ivol = a.vol[i];
+  const double dtv = a.dt[mesh] * a.vol[i];  // dt / |V_i|
   double un[NVP], res[NVP];
   if (a.stage != 0) {
 #pragma unroll
@@ -216,7 +248,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
       res[v] = 0.0;
       continue;
     }
-    const double upd = u64[v] - dt * acc[v] * ivol;
+    const double upd = u64[v] - dtv * acc[v];
     if (a.stage == 0) res[v] = upd;
     else if (a.stage == 1) res[v] = 0.75 * un[v] + 0.25 * upd;
     else res[v] = (1.0 / 3.0) * un[v] + (2.0 / 3.0) * upd;
@@ -239,6 +271,14 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
   if (!finite) atomicOr(a.err, kErrNonFinite);
   if (a.stage == 2 && finite) atomic_min_pos(&a.dt[a.nmesh + mesh], a.cfl * local_dt<D, T>(a, i, res));
 }
+
+}  // namespace
+}  // namespace cteno
+
+#include "flux_lanes.cuh"
+
+namespace cteno {
+namespace {
 
 template <int D, typename T>
 __global__ void dt_kernel(const KArgs a) {
@@ -287,6 +327,16 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 }  // namespace
 
 void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s) {
+  if (block >= kLaneSchedule) {  // face-per-lane schedule, block - kLaneSchedule threads
+    const int threads = block - kLaneSchedule, cpw = 32 / (dim + 1);
+    const int64_t cells_per_block = (int64_t)(threads / 32) * cpw;
+    const unsigned grid = (unsigned)((a.N + cells_per_block - 1) / cells_per_block);
+    if (dim == 2 && fp32) flux_lanes_kernel<2, float><<<grid, threads, 0, s>>>(a);
+    if (dim == 2 && !fp32) flux_lanes_kernel<2, double><<<grid, threads, 0, s>>>(a);
+    if (dim == 3 && fp32) flux_lanes_kernel<3, float><<<grid, threads, 0, s>>>(a);
+    if (dim == 3 && !fp32) flux_lanes_kernel<3, double><<<grid, threads, 0, s>>>(a);
+    return;
+  }
   const bool capped = block < 0;  // register-capped variant (FP32 only)
   if (capped) block = -block;
   const unsigned grid = grid_for(a.N, block);

@@ -1,0 +1,128 @@
+// flux_lanes.cuh -- face-per-lane schedule of the flux / update kernel (included by flux.cu after
+// the HLLC, local time-step and mesh-lookup helpers).
+//
+// A group of NF = d+1 consecutive lanes updates one cell, lane f computing the HLLC flux through
+// face f at its Gauss points. The face fluxes are exchanged by shuffles and summed in FP64 in face
+// order (bitwise the same sums as the thread-per-cell kernel, so the update stays exactly
+// conservative); the RK update of variable v is done by lane v mod NF.
+#pragma once
+
+namespace cteno {
+namespace {
+
+template <int D, typename T>
+__global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
+  using L = Lay<D>;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, FB = NQ * NV;
+  constexpr int CPW = 32 / NF;
+  constexpr bool F32 = sizeof(T) == 4;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / NF;
+  const int f = lane - grp * NF;  // this lane's face (spare lanes: a face index < NF as well)
+  const int base = grp * NF;
+  const int64_t N = a.N;
+  const int64_t cell = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * CPW + grp;
+  const bool active = grp < CPW && cell < N;
+  const int64_t i = active ? cell : N - 1;  // spare lanes shadow a valid cell, store nothing
+  const T *__restrict__ Uf = (const T *)a.Uf;
+  const T *__restrict__ G = F32 ? (const T *)a.geo32 : (const T *)a.geo;
+  T g;
+  if constexpr (F32) g = a.gamma32; else g = a.gamma;
+  const uint32_t meta = __ldg(a.fmeta + i);
+  const int64_t j = __ldg(a.nbr + i * 4 + f);
+  const int fj = (meta >> (2 * f)) & 3u;
+  const bool own = (meta >> (kMetaOwnerShift + f)) & 1u;
+  T gf[4], uI[FB], uO[FB];
+  load16<T, 4>(G + (i * NF + f) * 4, gf);
+  load16<T, FB>(Uf + (i * NF + f) * FB, uI);
+  if (j >= 0) {
+    load16<T, FB>(Uf + (j * NF + fj) * FB, uO);
+  } else {  // transmissive boundary: the cell mean outside
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T m = (T)a.U[i * NVP + v];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) uO[q * NV + v] = m;
+    }
+  }
+  T n[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) n[k] = own ? gf[k] : -gf[k];
+  T Ff[NV];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    T F[NV];
+    if (own) hllc<D, T>(uI + q * NV, uO + q * NV, n, g, F);
+    else hllc<D, T>(uO + q * NV, uI + q * NV, n, g, F);
+    T w;
+    if constexpr (F32) w = a.fw32[q]; else w = a.fw[q];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ff[v] = (q == 0) ? w * F[v] : Ff[v] + w * F[v];
+  }
+  T contrib[NV];  // this face's |A| F, signed for this cell
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const T x = gf[3] * Ff[v];
+    contrib[v] = own ? x : -x;
+  }
+  // residual of the variables this lane updates: FP64 sum over the faces in face order
+  const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
+  const double dtv = a.dt[mesh] * a.vol[i];  // dt / |V_i|
+  double res[NVP];
+  bool finite = true;
+#pragma unroll
+  for (int v = 0; v < NVP; ++v) res[v] = 0.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double acc = 0.0;
+    if constexpr (F32) {  // exact FP32 accumulation over the faces, as in the per-cell kernel
+      float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+      for (int ff = 0; ff < NF; ++ff) {
+        float s, e;
+        two_sum(hi, __shfl_sync(0xffffffffu, contrib[v], base + ff), s, e);
+        hi = s;
+        lo += e;
+      }
+      acc = (double)hi + (double)lo;
+    } else {
+#pragma unroll
+      for (int ff = 0; ff < NF; ++ff) acc += (double)__shfl_sync(0xffffffffu, contrib[v], base + ff);
+    }
+    if (v % NF == f) {
+      const double u = a.U[i * NVP + v];
+      const double upd = u - dtv * acc;
+      double r;
+      if (a.stage == 0) r = upd;
+      else if (a.stage == 1) r = 0.75 * a.Un[i * NVP + v] + 0.25 * upd;
+      else r = (1.0 / 3.0) * a.Un[i * NVP + v] + (2.0 / 3.0) * upd;
+      res[v] = r;
+      finite = finite && isfinite(r);
+      if (active) {
+        if (a.stage == 0) a.Un[i * NVP + v] = u;
+        a.U[i * NVP + v] = r;
+        if (a.U32) {
+          const float hi = (float)r;
+          reinterpret_cast<float2 *>(a.U32)[i * NVP + v] = make_float2(hi, (float)(r - (double)hi));
+        }
+      }
+    }
+  }
+  if (!finite && active) atomicOr(a.err, kErrNonFinite);
+  if (a.stage == 2) {  // CFL step of the next step: lane 0 of the group collects the new state
+    double full[NVP];
+#pragma unroll
+    for (int v = 0; v < NVP; ++v) full[v] = 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) full[v] = __shfl_sync(0xffffffffu, res[v], base + (v % NF));
+    if (active && f == 0) {
+      bool fin = true;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) fin = fin && isfinite(full[v]);
+      if (fin) atomic_min_pos(&a.dt[a.nmesh + mesh], a.cfl * local_dt<D, T>(a, i, full));
+    }
+  }
+}
+
+}  // namespace
+}  // namespace cteno

@@ -309,13 +309,14 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
   double lamsd = 0.0;
   float log2lams = 0.0f;
   if constexpr (F32) {
-    lams = (stn > 1) ? (float)a.one_m_lam1 / (float)(stn - 1) : 0.0f;
+    lams = (stn > 1) ? a.one_m_lam1_32 / (float)(stn - 1) : 0.0f;
     if (stn > 1) log2lams = a.log2_one_m_lam1 - log2f((float)(stn - 1));
   } else {
     lamsd = (stn > 1) ? a.one_m_lam1 / (stn - 1) : 0.0;
     lams = lamsd;
   }
-  const T inv_lam1 = (T)a.inv_lam1;
+  T inv_lam1;
+  if constexpr (F32) inv_lam1 = a.inv_lam1_32; else inv_lam1 = a.inv_lam1;
   const float log2lam1 = a.log2_lam1;
   constexpr T INV_FACT = (D == 2) ? (T)0.5 : (T)(1.0 / 6.0);
 
@@ -356,8 +357,8 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
     // 5: selection
     uint32_t bits;
     if constexpr (F32) {
-      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, log2lam1, log2lams,
-                             fmaxf((float)a.eps, 1e-40f), (float)a.C_T);
+      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, log2lam1, log2lams, a.eps32,
+                             a.C_T32);
     } else {
       bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
     }
@@ -383,7 +384,8 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
   // the paper): a non-physical face state makes the cell use its mean at all its face points
   T *__restrict__ Ufi = (T *)a.Uf + i * (int64_t)(NF * NQ * NV);
   const uint32_t perm = info >> kInfoPermShift;
-  const T gm1 = (T)(a.gamma - 1.0);
+  T gm1;
+  if constexpr (F32) gm1 = a.gm1_32; else gm1 = a.gamma - 1.0;
   bool bad = false;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
@@ -553,7 +555,7 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
   double lamsd = 0.0;
   float log2lams = 0.0f;
   if constexpr (F32) {
-    lams = (stn > 1) ? (float)a.one_m_lam1 / (float)(stn - 1) : 0.0f;
+    lams = (stn > 1) ? a.one_m_lam1_32 / (float)(stn - 1) : 0.0f;
     if (stn > 1) log2lams = a.log2_one_m_lam1 - log2f((float)(stn - 1));
   } else {
     lamsd = (stn > 1) ? a.one_m_lam1 / (stn - 1) : 0.0;
@@ -572,7 +574,8 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
         for (int f = 0; f < NF; ++f) s += ad[f][k];
         a1[k] -= lams * s;
       }
-      const T inv_lam1 = (T)a.inv_lam1;
+      T inv_lam1;
+      if constexpr (F32) inv_lam1 = a.inv_lam1_32; else inv_lam1 = a.inv_lam1;
 #pragma unroll
       for (int k = 0; k < NK; ++k) a1[k] *= inv_lam1;
     }
@@ -594,8 +597,8 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
     }
     uint32_t bits;
     if constexpr (F32) {
-      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.log2_lam1, log2lams,
-                             fmaxf((float)a.eps, 1e-40f), (float)a.C_T);
+      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.log2_lam1, log2lams, a.eps32,
+                             a.C_T32);
     } else {
       bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
     }
@@ -620,7 +623,8 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
   // from the group's lanes
   T *__restrict__ Ufi = (T *)a.Uf + i * (int64_t)(NF * NQ * NV);
   const uint32_t perm = info >> kInfoPermShift;
-  const T gm1 = (T)(a.gamma - 1.0);
+  T gm1;
+  if constexpr (F32) gm1 = a.gm1_32; else gm1 = a.gamma - 1.0;
   bool bad = false;
   T fv[NF][NQ];
 #pragma unroll

@@ -55,7 +55,7 @@ CASES = [
 
 
 # launch schedules the autotuner can choose: thread per cell (128), variable-per-lane (1024 + 256)
-SCHEDULES = [(128, 128), (1024 + 256, 64)]
+SCHEDULES = [(128, 128), (1024 + 256, 1024 + 128)]
 
 
 @pytest.mark.parametrize("launch", SCHEDULES, ids=["cell-thread", "var-lanes"])
@@ -189,7 +189,7 @@ def test_batched_meshes_match_independent_oracles():
     s.close()
 
 
-@pytest.mark.parametrize("launch", [(128, 128), (-128, -128), (1024 + 128, 64), (1024 + 256, 256)],
+@pytest.mark.parametrize("launch", [(128, 128), (-128, -128), (1024 + 128, 1024 + 256), (1024 + 256, 256)],
                          ids=["cell-thread", "capped", "var-lanes-128", "var-lanes-256"])
 def test_mixed_schedules_agree(launch):
     """Every launch schedule of the mixed path gives the same face states and update on a 2D and a
