@@ -94,6 +94,26 @@ __device__ __forceinline__ void atomic_min_pos(double *addr, double v) {
   atomicMin((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
 }
 
+// Minimum of the lanes' positive values v into dt[slot] with one atomic per warp when all lanes
+// of the warp target the same slot (cells of a mesh are contiguous, so a warp straddles at most a
+// mesh boundary), else one per lane. Lanes with nothing to contribute pass +inf (1e300). Must be
+// called by all 32 lanes of the warp.
+__device__ __forceinline__ void warp_min_to(double *dt, int slot, double v) {
+  const int first = __shfl_sync(0xffffffffu, slot, 0), last = __shfl_sync(0xffffffffu, slot, 31);
+  if (first == last) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long x = __shfl_xor_sync(0xffffffffu, b, o);
+      b = (x < b) ? x : b;
+    }
+    if ((threadIdx.x & 31) == 0 && b < (unsigned long long)__double_as_longlong(1e300))
+      atomicMin((unsigned long long *)&dt[slot], b);
+  } else if (v < 1e300) {
+    atomic_min_pos(&dt[slot], v);
+  }
+}
+
 // Local CFL step of one cell: |V_i| / sum_f |A_f| (|u_i . n_f| + c_i), in the path's arithmetic
 // type (FP64 geometry for the FP64 path; FP32 values and geometry for the mixed path, where the
 // step only sets the time-step size).
@@ -141,8 +161,11 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
   constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, FB = NQ * NV;
   constexpr bool F32 = sizeof(T) == 4;
   const int64_t N = a.N;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // threads past the last cell shadow it and store nothing, so that every lane of the warp
+  // reaches the time-step reduction
+  const bool active = cell < N;
+  const int64_t i = active ? cell : N - 1;
   const T *__restrict__ Uf = (const T *)a.Uf;
   const T *__restrict__ G = F32 ? (const T *)a.geo32 : (const T *)a.geo;
   T g;
@@ -254,13 +277,15 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
     else res[v] = (1.0 / 3.0) * un[v] + (2.0 / 3.0) * upd;
     finite = finite && isfinite(res[v]);
   }
+  if (active) {
 #pragma unroll
-  for (int c = 0; c < NVP / 2; ++c) {
-    reinterpret_cast<double2 *>(a.U + i * NVP)[c] = make_double2(res[2 * c], res[2 * c + 1]);
-    if (a.stage == 0)
-      reinterpret_cast<double2 *>(a.Un + i * NVP)[c] = make_double2(u64[2 * c], u64[2 * c + 1]);
+    for (int c = 0; c < NVP / 2; ++c) {
+      reinterpret_cast<double2 *>(a.U + i * NVP)[c] = make_double2(res[2 * c], res[2 * c + 1]);
+      if (a.stage == 0)
+        reinterpret_cast<double2 *>(a.Un + i * NVP)[c] = make_double2(u64[2 * c], u64[2 * c + 1]);
+    }
   }
-  if (a.U32) {
+  if (a.U32 && active) {
 #pragma unroll
     for (int c = 0; c < NVP / 2; ++c) {
       const float h0 = (float)res[2 * c], h1 = (float)res[2 * c + 1];
@@ -268,8 +293,9 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
           make_float4(h0, (float)(res[2 * c] - (double)h0), h1, (float)(res[2 * c + 1] - (double)h1));
     }
   }
-  if (!finite) atomicOr(a.err, kErrNonFinite);
-  if (a.stage == 2 && finite) atomic_min_pos(&a.dt[a.nmesh + mesh], a.cfl * local_dt<D, T>(a, i, res));
+  if (!finite && active) atomicOr(a.err, kErrNonFinite);
+  if (a.stage == 2)
+    warp_min_to(a.dt, a.nmesh + mesh, (finite && active) ? a.cfl * local_dt<D, T>(a, i, res) : 1e300);
 }
 
 }  // namespace
@@ -283,13 +309,14 @@ namespace {
 template <int D, typename T>
 __global__ void dt_kernel(const KArgs a) {
   constexpr int NVP = Lay<D>::NVP;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.N) return;
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = cell < a.N;
+  const int64_t i = active ? cell : a.N - 1;  // every lane reaches the reduction
   double u[NVP];
 #pragma unroll
   for (int v = 0; v < NVP; ++v) u[v] = a.U[i * NVP + v];
   const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
-  atomic_min_pos(&a.dt[a.nmesh + mesh], a.cfl * local_dt<D, T>(a, i, u));
+  warp_min_to(a.dt, a.nmesh + mesh, active ? a.cfl * local_dt<D, T>(a, i, u) : 1e300);
 }
 
 __global__ void dt_reset_kernel(double *dt, int nmesh) {

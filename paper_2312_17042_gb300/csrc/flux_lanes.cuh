@@ -115,12 +115,10 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
     for (int v = 0; v < NVP; ++v) full[v] = 0.0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) full[v] = __shfl_sync(0xffffffffu, res[v], base + (v % NF));
-    if (active && f == 0) {
-      bool fin = true;
+    bool fin = active && f == 0;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) fin = fin && isfinite(full[v]);
-      if (fin) atomic_min_pos(&a.dt[a.nmesh + mesh], a.cfl * local_dt<D, T>(a, i, full));
-    }
+    for (int v = 0; v < NV; ++v) fin = fin && isfinite(full[v]);
+    warp_min_to(a.dt, a.nmesh + mesh, fin ? a.cfl * local_dt<D, T>(a, i, full) : 1e300);
   }
 }
 
