@@ -213,6 +213,20 @@ def alu_peak(native):
     return {"fp64_tflops": round(f64, 3), "fp32_tflops": round(f32, 2)}
 
 
+def recon_kernel_name(dim, degree, scheme, launch):
+    """Name of the mixed-path reconstruction kernel a launch value selects."""
+    args = f"{dim},{degree},float,{SCHEMES[scheme]}"
+    if launch >= 3072:
+        return f"recon_staged_kernel<{args},lanes> x{launch - 3072}"
+    if launch >= 2048:
+        return f"recon_staged_kernel<{args},cells> x{launch - 2048}"
+    if launch >= 1024:
+        return f"recon_lanes_kernel<{args}> x{launch - 1024}"
+    if launch < 0:
+        return f"recon_kernel<{args},capped> x{-launch}"
+    return f"recon_kernel<{args}> x{launch}"
+
+
 def ncu_traffic(variant):
     """DRAM bytes per reconstruction launch from the committed ncu capture, if the kernel source
     has not changed since."""
@@ -301,7 +315,7 @@ def run_ours(args, rank, world, local):
     peaks, peak_kind = measured_peaks()
     achieved = stats[0] / (recon_ms_launch * 1e-3) / 1e9
     hv = f"{args.workload}:" + variant_name(**h)
-    roofline = {"kernel": f"recon_kernel<{case.dim},{h['degree']},float,{SCHEMES[h['scheme']]}>", "bound": "hbm",
+    roofline = {"kernel": recon_kernel_name(case.dim, h["degree"], h["scheme"], blocks[0]), "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(hv),
                 "algorithmic_bytes_per_launch": stats[0], "launch_ms": round(recon_ms_launch, 5),

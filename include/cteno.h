@@ -173,11 +173,17 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
  * blocks per SM) with b threads per block, b in {32, 64, 96, 128}. 1024 + b selects the lane
  * schedule with b threads per block (b a multiple of 32 in [32, 256]): for the reconstruction one
  * lane per conserved variable (d+2 lanes per cell), for the flux one lane per face (d+1 lanes per
- * cell). */
+ * cell). Reconstruction on the mixed path only: 2048 + b / 3072 + b select the thread-per-cell /
+ * lane schedule as a persistent kernel that copies each tile's operator records (b cells, or
+ * floor(32/(d+2)) cells per warp) into shared memory with bulk copies, two tiles in flight; refused
+ * (CTENO_ERR_ARG) when the two stages need more than 200 KiB of shared memory. If a bounded wait for
+ * such a copy ever gives up (after 1 s), the kernel stops and the next synchronising call returns
+ * CTENO_ERR_DEVICE. */
 int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block);
 
 /* Time the candidate launch configurations (block sizes 64/128/256, on the mixed path the
- * register-capped variants at 64/128, and the lane schedules at 128/256 threads) on the current
+ * register-capped variants at 64/128 and the staged reconstruction schedules that fit, and the
+ * lane schedules at 128/256 threads) on the current
  * state and keep the fastest; the state is
  * restored afterwards. best_out[2] (may be NULL) receives the chosen values, in the convention of
  * cteno_set_launch. */

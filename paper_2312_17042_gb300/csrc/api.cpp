@@ -113,6 +113,12 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.one_m_lam1 = 1.0 - a.lam1;
   a.log2_lam1 = (float)std::log2(a.lam1);
   a.log2_one_m_lam1 = (float)std::log2(a.one_m_lam1);
+  for (int k = 0; k <= kMaxNF; ++k) {  // k = st - 1 admissible directional stencils
+    a.lams_d[k] = k ? a.one_m_lam1 / k : 0.0;
+    a.lams_f[k] = (float)a.lams_d[k];
+    a.log2_lams_f[k] = k ? (float)std::log2(a.lams_d[k]) : 0.0f;
+    a.inv_stm1_f[k] = k ? (float)(1.0 / k) : 0.0f;
+  }
   for (int q = 0; q < kMaxNQ; ++q) {
     a.fw[q] = ctx->tab.fw[q];
     a.fw32[q] = (float)ctx->tab.fw[q];
@@ -163,6 +169,7 @@ int device_status(cteno_ctx *ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   if (e & kErrNonFinite) return fail(ctx, CTENO_ERR_DEVICE, "a cell state became non-finite");
   if (e & kErrRank) return fail(ctx, CTENO_ERR_RANK, "a central least-squares matrix is rank deficient");
+  if (e & kErrTimeout) return fail(ctx, CTENO_ERR_DEVICE, "a bounded wait for a bulk copy timed out");
   return CTENO_OK;
 }
 
@@ -630,14 +637,21 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
   if (!ctx) return CTENO_ERR_ARG;
   // positive: block size of the uncapped kernel; negative: block size of the register-capped
   // variant (mixed path only, at most 128 threads)
-  auto ok = [&](int b, bool) {
+  auto ok = [&](int b, bool recon) {
     if (b == 0) return true;
+    if (b >= kStagedCells) {  // staged schedules: reconstruction, mixed path, two stages that fit
+      const int t = b - (b >= kStagedLanes ? kStagedLanes : kStagedCells);
+      return recon && ctx->fp32 && b < kStagedLanes + 1024 && t >= 32 && t <= 256 && t % 32 == 0 &&
+             recon_staged_smem(ctx->d, ctx->p.degree, 1, b) <= kMaxStagedSmem;
+    }
     if (b >= kLaneSchedule) return b - kLaneSchedule >= 32 && b - kLaneSchedule <= 256 && b % 32 == 0;
     if (b < 0) return ctx->fp32 && -b >= 32 && -b <= 128 && (-b) % 32 == 0;
     return b >= 32 && b <= 256 && b % 32 == 0;
   };
   if (!ok(recon_block, true) || !ok(flux_block, false))
-    return fail(ctx, CTENO_ERR_ARG, "block size must be a multiple of 32 in [32, 256] (capped: [32, 128], mixed path)");
+    return fail(ctx, CTENO_ERR_ARG,
+                "block size must be a multiple of 32 in [32, 256] (capped: [32, 128], mixed path; staged: "
+                "mixed-path reconstruction whose two stages fit in shared memory)");
   if (recon_block) ctx->recon_block = recon_block;
   if (flux_block) ctx->flux_block = flux_block;
   drop_graph(ctx);
@@ -680,7 +694,12 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
   }
   // the lane schedules (variable per lane for the reconstruction, face per lane for the flux)
   for (int b : {128, 256}) cand.push_back(kLaneSchedule + b);
-  const std::vector<int> &rcand = cand;
+  std::vector<int> rcand = cand;
+  // the staged schedules (mixed path) whose two stages fit
+  if (ctx->fp32)
+    for (int b : {kStagedCells + 32, kStagedCells + 64, kStagedCells + 128, kStagedLanes + 64,
+                  kStagedLanes + 128, kStagedLanes + 256})
+      if (recon_staged_smem(ctx->d, ctx->p.degree, 1, b) <= kMaxStagedSmem) rcand.push_back(b);
   const int reps = 5;
   float best_r = 1e30f, best_f = 1e30f;
   int br = ctx->recon_block, bf = ctx->flux_block;

@@ -42,6 +42,7 @@ constexpr int kMetaOwnerShift = 8;
 // Error word bits.
 constexpr int kErrNonFinite = 1;
 constexpr int kErrRank = 2;
+constexpr int kErrTimeout = 4;  // a bounded wait on a bulk copy gave up
 
 // Device tables (a copy of Tables with the fields the kernels read).
 struct DevTables {
@@ -95,6 +96,10 @@ struct KArgs {
   // lam1 = 1 - 1/lambda_1', 1/lam1, 1 - lam1 (lambda_s = (1 - lam1) / (s_t - 1)) and base-2 logs
   double lam1, inv_lam1, one_m_lam1;
   float log2_lam1, log2_one_m_lam1;
+  // lambda_s of each directional stencil when st stencils are admissible (index st - 1, 1..d+1):
+  // (1 - lam1) / (st - 1) in FP64, its FP32 copy and base-2 log; CTENOZ mean factor 1 / (st - 1)
+  double lams_d[kMaxNF + 1];
+  float lams_f[kMaxNF + 1], log2_lams_f[kMaxNF + 1], inv_stm1_f[kMaxNF + 1];
   // FP32 copies for the mixed path (no per-thread conversions)
   float gamma32, gm1_32, eps32, C_T32, inv_lam1_32, one_m_lam1_32, cfl32;
   float fw32[kMaxNQ];
@@ -124,6 +129,21 @@ struct SetupArgs {
 // -b the register-capped thread-per-cell variant; kLaneSchedule + b the variable-per-lane
 // schedule with b threads per block.
 constexpr int kLaneSchedule = 1024;
+// kStagedCells + b / kStagedLanes + b: the thread-per-cell / variable-per-lane schedule as a
+// persistent kernel whose operator records are staged in shared memory by bulk copies (mixed path).
+constexpr int kStagedCells = 2048;
+constexpr int kStagedLanes = 3072;
+constexpr int kMaxStagedSmem = 200 * 1024;  // dynamic shared memory of the two stages, at most
+
+// Dynamic shared memory of a staged launch value (two stages of a tile's operator records).
+inline long long recon_staged_smem(int d, int degree, int fp32, int block) {
+  const int nk = (d == 2 ? (degree + 1) * (degree + 2) / 2 : (degree + 1) * (degree + 2) * (degree + 3) / 6) - 1;
+  const int M = 2 * (nk + 1), sT = fp32 ? 4 : 8;
+  const int threads = block >= kStagedLanes ? block - kStagedLanes : block - kStagedCells;
+  const int cells = block >= kStagedLanes ? (threads / 32) * (32 / (d + 2)) : threads;
+  const long long cell_bytes = (long long)M * nk * sT + (long long)(d + 1) * lay_pds(d) * sT + 4LL * M;
+  return 2 * cells * cell_bytes;
+}
 
 void launch_setup(int dim, int degree, const SetupArgs &a, cudaStream_t s);
 // Upload the (d, r) smoothness matrix and face-point basis values to the constant banks of the
@@ -168,16 +188,32 @@ struct Vec16<double> {
 };
 
 // Load / store COUNT (a multiple of 16 / sizeof(T)) consecutive values from / to a 16-byte
-// aligned address. Loads go through the read-only path: use them only on data the kernel does
-// not write.
-template <typename T, int COUNT>
+// aligned address. Global loads (SH = false) go through the read-only path: use them only on data
+// the kernel does not write; SH = true reads a shared-memory copy.
+template <typename T, int COUNT, bool SH = false>
 __device__ __forceinline__ void load16(const T *__restrict__ src, T *dst) {
   using V = Vec16<T>;
   static_assert(COUNT % V::n == 0, "record not a multiple of 16 bytes");
 #pragma unroll
-  for (int c = 0; c < COUNT / V::n; ++c)
-    V::unpack(__ldg(reinterpret_cast<const typename V::type *>(src) + c), dst + c * V::n);
+  for (int c = 0; c < COUNT / V::n; ++c) {
+    if constexpr (SH)
+      V::unpack(reinterpret_cast<const typename V::type *>(src)[c], dst + c * V::n);
+    else
+      V::unpack(__ldg(reinterpret_cast<const typename V::type *>(src) + c), dst + c * V::n);
+  }
 }
+#ifdef __CUDACC__
+template <bool SH>
+__device__ __forceinline__ int4 load_i4(const int32_t *__restrict__ src) {
+  if constexpr (SH) return *reinterpret_cast<const int4 *>(src);
+  else return __ldg(reinterpret_cast<const int4 *>(src));
+}
+template <bool SH>
+__device__ __forceinline__ int32_t load_i1(const int32_t *__restrict__ src) {
+  if constexpr (SH) return *src;
+  else return __ldg(src);
+}
+#endif
 template <typename T, int COUNT>
 __device__ __forceinline__ void store16(T *__restrict__ dstp, const T *src) {
   using V = Vec16<T>;

@@ -12,6 +12,67 @@
 namespace cteno {
 namespace {
 
+// Reciprocal, quotient and square root: IEEE operations on the FP64 path; on the mixed path the
+// GPU's single-instruction approximations (relative error about 2^-23). Both cells of a face run
+// the same instruction sequence on the same operands, so their face values stay bit-identical.
+template <typename T>
+__device__ __forceinline__ T rcp_(T x) {
+  if constexpr (sizeof(T) == 4) {
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  } else {
+    return 1.0 / x;
+  }
+}
+template <typename T>
+__device__ __forceinline__ T div_(T x, T y) {
+  if constexpr (sizeof(T) == 4) return x * rcp_<T>(y);
+  else return x / y;
+}
+template <typename T>
+__device__ __forceinline__ T sqrt_(T x) {
+  if constexpr (sizeof(T) == 4) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  } else {
+    return sqrt(x);
+  }
+}
+
+// Exact FP32 -> FP64 conversion in integer operations (the FP64 pipe of this GPU is narrow);
+// subnormal FP32 values become zero, infinities and NaNs stay non-finite.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e = (b >> 23) & 0xFFu, sign = b & 0x80000000u;
+  const uint32_t hi = (e == 0) ? sign : (sign | ((e == 255u ? 0x7FFu : e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3));
+  const uint32_t lo = (e == 0) ? 0u : (b << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// FP64 -> FP32 pair (hi, lo) in integer operations: hi is x truncated to 24 significant bits and
+// lo the remainder truncated to 24 bits, so |x - hi - lo| < 2^-46 |x| for 2^-126 <= |x| < 2^128.
+// Smaller magnitudes give (+-0, +-0); larger ones and non-finite values an infinity in hi (the
+// update reports non-finite states separately).
+__device__ __forceinline__ float2 f64_split(double x) {
+  const uint32_t H = (uint32_t)__double2hiint(x), L = (uint32_t)__double2loint(x);
+  const uint32_t sign = H & 0x80000000u;
+  const int e = (int)((H >> 20) & 0x7FFu);
+  const int ef = e - 896;  // biased FP32 exponent of hi
+  if (ef <= 0) return make_float2(__uint_as_float(sign), __uint_as_float(sign));
+  if (ef >= 255) return make_float2(__uint_as_float(sign | 0x7F800000u), 0.0f);
+  const uint32_t mhi = ((H & 0xFFFFFu) << 3) | (L >> 29);
+  const float hi = __uint_as_float(sign | ((uint32_t)ef << 23) | mhi);
+  const uint32_t m = L & 0x1FFFFFFFu;  // the remaining 29 bits, unit 2^(e - 1075)
+  if (m == 0u) return make_float2(hi, __uint_as_float(sign));
+  const int p = 31 - __clz((int)m);    // leading bit of m
+  const int el = p + e - 948;          // biased FP32 exponent of lo
+  if (el <= 0) return make_float2(hi, __uint_as_float(sign));
+  const uint32_t ml = ((p >= 23) ? (m >> (p - 23)) : (m << (23 - p))) & 0x7FFFFFu;
+  return make_float2(hi, __uint_as_float(sign | ((uint32_t)el << 23) | ml));
+}
+
 template <int D, typename T>
 __device__ __forceinline__ void physical_flux(const T *u, const T *n, T p, T un, T *F) {
   F[0] = u[0] * un;
@@ -27,7 +88,7 @@ template <int D, typename T>
 __device__ __forceinline__ void hllc(const T *uL, const T *uR, const T *n, T g, T *F) {
   constexpr int NV = D + 2;
   const T rL = uL[0], rR = uR[0];
-  const T iL = (T)1 / rL, iR = (T)1 / rR;
+  const T iL = rcp_<T>(rL), iR = rcp_<T>(rR);
   T vL[D], vR[D], unL = 0, unR = 0, kL = 0, kR = 0;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -40,10 +101,10 @@ __device__ __forceinline__ void hllc(const T *uL, const T *uR, const T *n, T g, 
   }
   const T pL = (g - (T)1) * (uL[NV - 1] - (T)0.5 * kL);
   const T pR = (g - (T)1) * (uR[NV - 1] - (T)0.5 * kR);
-  const T cL = sqrt(g * pL * iL), cR = sqrt(g * pR * iR);
+  const T cL = sqrt_<T>(g * pL * iL), cR = sqrt_<T>(g * pR * iR);
   const T HL = (uL[NV - 1] + pL) * iL, HR = (uR[NV - 1] + pR) * iR;
-  const T Dr = sqrt(rR * iL);
-  const T idn = (T)1 / ((T)1 + Dr);
+  const T Dr = sqrt_<T>(rR * iL);
+  const T idn = rcp_<T>((T)1 + Dr);
   T ut2 = 0, utn = 0;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -52,16 +113,16 @@ __device__ __forceinline__ void hllc(const T *uL, const T *uR, const T *n, T g, 
     utn += ut * n[j];
   }
   const T Ht = (HL + HR * Dr) * idn;
-  const T ct = sqrt((g - (T)1) * (Ht - (T)0.5 * ut2));
+  const T ct = sqrt_<T>((g - (T)1) * (Ht - (T)0.5 * ut2));
   const T SL = fmin(unL - cL, utn - ct);
   const T SR = fmax(unR + cR, utn + ct);
-  const T SM = (rR * unR * (SR - unR) - rL * unL * (SL - unL) + pL - pR) /
-               (rR * (SR - unR) - rL * (SL - unL));
+  const T SM = div_<T>(rR * unR * (SR - unR) - rL * unL * (SL - unL) + pL - pR,
+                       rR * (SR - unR) - rL * (SL - unL));
   if (SL > (T)0) {
     physical_flux<D, T>(uL, n, pL, unL, F);
   } else if (SM > (T)0) {
     const T ps = rL * (unL - SL) * (unL - SM) + pL;
-    const T fct = (T)1 / (SL - SM), a = SL - unL;
+    const T fct = rcp_<T>(SL - SM), a = SL - unL;
     physical_flux<D, T>(uL, n, pL, unL, F);
     F[0] += SL * (rL * a * fct - uL[0]);
 #pragma unroll
@@ -69,7 +130,7 @@ __device__ __forceinline__ void hllc(const T *uL, const T *uR, const T *n, T g, 
     F[NV - 1] += SL * ((a * uL[NV - 1] - pL * unL + ps * SM) * fct - uL[NV - 1]);
   } else if (SR > (T)0) {
     const T ps = rL * (unL - SL) * (unL - SM) + pL;
-    const T fct = (T)1 / (SR - SM), a = SR - unR;
+    const T fct = rcp_<T>(SR - SM), a = SR - unR;
     physical_flux<D, T>(uR, n, pR, unR, F);
     F[0] += SR * (rR * a * fct - uR[0]);
 #pragma unroll
@@ -118,15 +179,13 @@ __device__ __forceinline__ void warp_min_to(double *dt, int slot, double v) {
 // type (FP64 geometry for the FP64 path; FP32 values and geometry for the mixed path, where the
 // step only sets the time-step size).
 template <int D, typename T>
-__device__ __forceinline__ double local_dt(const KArgs &a, int64_t i, const double *u64) {
+__device__ __forceinline__ double local_dt(const KArgs &a, int64_t i, const T *uu) {
   constexpr int NF = D + 1;
   constexpr bool F32 = sizeof(T) == 4;
   const T *G = F32 ? (const T *)a.geo32 : (const T *)a.geo;
-  T g, uu[D + 2];
+  T g;
   if constexpr (F32) g = a.gamma32; else g = a.gamma;
-#pragma unroll
-  for (int v = 0; v < D + 2; ++v) uu[v] = (T)u64[v];
-  const T ir = (T)1 / uu[0];
+  const T ir = rcp_<T>(uu[0]);
   T ke = 0, u[D];
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -134,7 +193,7 @@ __device__ __forceinline__ double local_dt(const KArgs &a, int64_t i, const doub
     ke += uu[1 + j] * u[j];
   }
   const T p = (g - (T)1) * (uu[D + 1] - (T)0.5 * ke);
-  const T c = sqrt(g * p * ir);
+  const T c = sqrt_<T>(g * p * ir);
   T s = 0;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
@@ -144,7 +203,7 @@ __device__ __forceinline__ double local_dt(const KArgs &a, int64_t i, const doub
     for (int j = 0; j < D; ++j) un += u[j] * gf[j];
     s += gf[3] * (fabs(un) + c);
   }
-  if constexpr (F32) return (double)(1.0f / (s * (float)a.vol[i]));
+  if constexpr (F32) return (double)rcp_<float>(s * (float)a.vol[i]);
   else return 1.0 / (s * a.vol[i]);
 }
 
@@ -250,7 +309,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
   }
   if constexpr (F32) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = (double)acc_hi[v] + (double)acc_lo[v];
+    for (int v = 0; v < NV; ++v) acc[v] = f32_to_f64(acc_hi[v]) + f32_to_f64(acc_lo[v]);
   }
   // residual and SSP-RK3 (Shu-Osher) stage update in FP64
   const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
@@ -285,17 +344,27 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
         reinterpret_cast<double2 *>(a.Un + i * NVP)[c] = make_double2(u64[2 * c], u64[2 * c + 1]);
     }
   }
-  if (a.U32 && active) {
+  T ust[NVP];  // the new state in the path's type, for the CFL step
+  if constexpr (F32) {  // FP32 (hi, lo) shadow of the new state
+    float4 hl[NVP / 2];
 #pragma unroll
     for (int c = 0; c < NVP / 2; ++c) {
-      const float h0 = (float)res[2 * c], h1 = (float)res[2 * c + 1];
-      reinterpret_cast<float4 *>(a.U32 + i * 2 * NVP)[c] =
-          make_float4(h0, (float)(res[2 * c] - (double)h0), h1, (float)(res[2 * c + 1] - (double)h1));
+      const float2 s0 = f64_split(res[2 * c]), s1 = f64_split(res[2 * c + 1]);
+      hl[c] = make_float4(s0.x, s0.y, s1.x, s1.y);
+      ust[2 * c] = s0.x;
+      ust[2 * c + 1] = s1.x;
     }
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < NVP / 2; ++c) reinterpret_cast<float4 *>(a.U32 + i * 2 * NVP)[c] = hl[c];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NVP; ++v) ust[v] = res[v];
   }
   if (!finite && active) atomicOr(a.err, kErrNonFinite);
   if (a.stage == 2)
-    warp_min_to(a.dt, a.nmesh + mesh, (finite && active) ? a.cfl * local_dt<D, T>(a, i, res) : 1e300);
+    warp_min_to(a.dt, a.nmesh + mesh, (finite && active) ? a.cfl * local_dt<D, T>(a, i, ust) : 1e300);
 }
 
 }  // namespace
@@ -315,8 +384,11 @@ __global__ void dt_kernel(const KArgs a) {
   double u[NVP];
 #pragma unroll
   for (int v = 0; v < NVP; ++v) u[v] = a.U[i * NVP + v];
+  T uu[NVP];
+#pragma unroll
+  for (int v = 0; v < NVP; ++v) uu[v] = (T)u[v];
   const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
-  warp_min_to(a.dt, a.nmesh + mesh, active ? a.cfl * local_dt<D, T>(a, i, u) : 1e300);
+  warp_min_to(a.dt, a.nmesh + mesh, active ? a.cfl * local_dt<D, T>(a, i, uu) : 1e300);
 }
 
 __global__ void dt_reset_kernel(double *dt, int nmesh) {
@@ -333,10 +405,10 @@ __global__ void permute_in_kernel(int nv, int nvp, int64_t n, int64_t off, const
   for (int v = 0; v < nvp; ++v) {
     const double x = (v < nv) ? src[v * n + c] : 0.0;
     U[g * nvp + v] = x;
-    if (U32) {
-      const float hi = (float)x;
-      U32[(g * nvp + v) * 2] = hi;
-      U32[(g * nvp + v) * 2 + 1] = (float)(x - (double)hi);
+    if (U32) {  // the same (hi, lo) split as the stage update
+      const float2 s = f64_split(x);
+      U32[(g * nvp + v) * 2] = s.x;
+      U32[(g * nvp + v) * 2 + 1] = s.y;
     }
   }
 }

@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     double acc = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     if constexpr (F32) {  // exact FP32 accumulation over the faces, as in the per-cell kernel
-      float hi = 0.0f, lo = 0.0f;
 #pragma unroll
       for (int ff = 0; ff < NF; ++ff) {
         float s, e;
@@ -84,12 +84,12 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
         hi = s;
         lo += e;
       }
-      acc = (double)hi + (double)lo;
     } else {
 #pragma unroll
       for (int ff = 0; ff < NF; ++ff) acc += (double)__shfl_sync(0xffffffffu, contrib[v], base + ff);
     }
-    if (v % NF == f) {
+    if (v % NF == f) {  // FP64 work only in the lane that updates variable v
+      if constexpr (F32) acc = f32_to_f64(hi) + f32_to_f64(lo);
       const double u = a.U[i * NVP + v];
       const double upd = u - dtv * acc;
       double r;
@@ -101,10 +101,7 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
       if (active) {
         if (a.stage == 0) a.Un[i * NVP + v] = u;
         a.U[i * NVP + v] = r;
-        if (a.U32) {
-          const float hi = (float)r;
-          reinterpret_cast<float2 *>(a.U32)[i * NVP + v] = make_float2(hi, (float)(r - (double)hi));
-        }
+        if (a.U32) reinterpret_cast<float2 *>(a.U32)[i * NVP + v] = f64_split(r);
       }
     }
   }
@@ -118,7 +115,13 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
     bool fin = active && f == 0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) fin = fin && isfinite(full[v]);
-    warp_min_to(a.dt, a.nmesh + mesh, fin ? a.cfl * local_dt<D, T>(a, i, full) : 1e300);
+    T ft[NVP];
+#pragma unroll
+    for (int v = 0; v < NVP; ++v) {
+      if constexpr (F32) ft[v] = f64_split(full[v]).x;
+      else ft[v] = full[v];
+    }
+    warp_min_to(a.dt, a.nmesh + mesh, fin ? a.cfl * local_dt<D, T>(a, i, ft) : 1e300);
   }
 }
 

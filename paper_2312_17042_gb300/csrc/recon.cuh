@@ -16,8 +16,10 @@
 // stencil means come from neighbouring records (L1/L2 hits after the Morton renumbering).
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 
+#include "bulk.cuh"
 #include "device.h"
 
 namespace cteno {
@@ -135,17 +137,42 @@ __device__ __forceinline__ uint32_t select_fp64(double SI0, const double *SId, u
   return bits;
 }
 
+// Base-2 logarithm and power with the GPU's single-instruction approximations (relative error
+// about 2^-22; subnormal inputs are kept, so eps = 1e-40 stays distinct from zero).
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// tab[k] for k in [0, N] through selects on compile-time offsets (a kernel parameter array is
+// then read from the constant bank without a local copy).
+template <int N, typename X>
+__device__ __forceinline__ X pick(const X *tab, int k) {
+  X r = tab[0];
+#pragma unroll
+  for (int j = 1; j <= N; ++j)
+    if (k == j) r = tab[j];
+  return r;
+}
+
 // The same decision in FP32 without overflow: every gamma_s is carried as its base-2 logarithm
-// L_s, and chi_s = 2^(L_s - Lmax) / sum_t 2^(L_t - Lmax).
+// L_s, and chi_s = 2^(L_s - Lmax) / sum_t 2^(L_t - Lmax); chi_s < C_T is tested as
+// 2^(L_s - Lmax) < C_T sum_t 2^(L_t - Lmax) (no division). inv_stm1 = 1 / (st - 1).
 template <int NF>
 __device__ __forceinline__ uint32_t select_fp32(float SI0, const float *SId, uint32_t adm, int st,
                                                 int scheme, int lam_gamma, float log2lam1,
-                                                float log2lams, float eps, float C_T) {
+                                                float log2lams, float inv_stm1, float eps, float C_T) {
   float L0, Ld[NF];
   if (scheme == 0) {
-    L0 = -6.0f * log2f(SI0 + eps);
+    L0 = -6.0f * lg2_approx(SI0 + eps);
 #pragma unroll
-    for (int f = 0; f < NF; ++f) Ld[f] = -6.0f * log2f(SId[f] + eps);
+    for (int f = 0; f < NF; ++f) Ld[f] = -6.0f * lg2_approx(SId[f] + eps);
   } else {
     float lt = -INFINITY;  // log2 tau
     if (st > 1) {
@@ -153,13 +180,15 @@ __device__ __forceinline__ uint32_t select_fp32(float SI0, const float *SId, uin
 #pragma unroll
       for (int f = 0; f < NF; ++f)
         if ((adm >> f) & 1u) acc += fabsf(SId[f] - SI0);
-      lt = 6.0f * log2f(acc / (float)(st - 1));
+      lt = 6.0f * lg2_approx(acc * inv_stm1);
     }
     // log2(1 + 2^x) with x = log2(tau / (SI + eps)), split to stay accurate for any x
-    auto l1p = [](float x) { return (x > 0.0f) ? x + log2f(1.0f + exp2f(-x)) : log2f(1.0f + exp2f(x)); };
-    L0 = l1p(lt - log2f(SI0 + eps));
+    auto l1p = [](float x) {
+      return (x > 0.0f) ? x + lg2_approx(1.0f + ex2_approx(-x)) : lg2_approx(1.0f + ex2_approx(x));
+    };
+    L0 = l1p(lt - lg2_approx(SI0 + eps));
 #pragma unroll
-    for (int f = 0; f < NF; ++f) Ld[f] = l1p(lt - log2f(SId[f] + eps));
+    for (int f = 0; f < NF; ++f) Ld[f] = l1p(lt - lg2_approx(SId[f] + eps));
   }
   if (lam_gamma) {
     L0 += log2lam1;
@@ -170,43 +199,35 @@ __device__ __forceinline__ uint32_t select_fp32(float SI0, const float *SId, uin
 #pragma unroll
   for (int f = 0; f < NF; ++f)
     if ((adm >> f) & 1u) Lmax = fmaxf(Lmax, Ld[f]);
-  float sum = exp2f(L0 - Lmax);
+  const float e0 = ex2_approx(L0 - Lmax);
+  float ed[NF], sum = e0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    ed[f] = ex2_approx(Ld[f] - Lmax);
+    if ((adm >> f) & 1u) sum += ed[f];
+  }
+  const float cut = C_T * sum;
+  uint32_t bits = (e0 < cut) ? 0u : 1u;
 #pragma unroll
   for (int f = 0; f < NF; ++f)
-    if ((adm >> f) & 1u) sum += exp2f(Ld[f] - Lmax);
-  uint32_t bits = (exp2f(L0 - Lmax) / sum < C_T) ? 0u : 1u;
-#pragma unroll
-  for (int f = 0; f < NF; ++f)
-    if (((adm >> f) & 1u) && !(exp2f(Ld[f] - Lmax) / sum < C_T)) bits |= 1u << (1 + f);
+    if (((adm >> f) & 1u) && !(ed[f] < cut)) bits |= 1u << (1 + f);
   return bits;
 }
 
-// MINB > 0: register-capped variant (at most 128 threads per block, MINB blocks per SM), which the
-// autotuner weighs against the uncapped one (occupancy and wave count against spills).
-template <int D, int R, typename T, int SCHEME, int MINB>
-__global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kernel(const KArgs a) {
+// One cell of the thread-per-cell schedule. Pci, Pdi, sti: the cell's central pseudo-inverse,
+// directional operators and stencil ids, in global memory (SH = false) or in a shared-memory copy
+// (SH = true); sPhi: 3D face-point basis values in shared memory.
+template <int D, int R, typename T, int SCHEME, bool SH>
+__device__ __forceinline__ void recon_cell(const KArgs &a, const int64_t i, const T *__restrict__ Pci,
+                                           const T *__restrict__ Pdi, const int32_t *__restrict__ sti,
+                                           const T *__restrict__ sPhi) {
   using S = Shape<D, R>;
   using L = Lay<D>;
   constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, ND = L::ND, PDS = L::PDS;
   constexpr int NK = S::NK, M = S::M, NP = S::NP;
-  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
   constexpr int CH = Vec16<T>::n;
   constexpr bool F32 = sizeof(T) == 4;
-  // 3D: face-point basis values for all six vertex orders of a face, staged in shared memory
-  __shared__ T sPhi[NPHI];
-  if constexpr (D == 3) {
-    const DevTables &tb = *a.tab;
-    for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
-      const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
-      sPhi[t] = (T)tb.Phi[f][p][q][k];
-    }
-    __syncthreads();
-  }
-
   const int64_t N = a.N;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-
   // own cell means: FP64, or (mixed path) the FP32 pair hi + lo of every FP64 value, so that
   // U_m - U_0 = (hi_m - hi_0) + (lo_m - lo_0) keeps FP64 accuracy in FP32 arithmetic
   T U0[NV];
@@ -243,8 +264,6 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
   };
 
   // 1-2: central coefficients a_opt = P_c (U_m - U_0), streaming the member-major record
-  const int32_t *__restrict__ sti = a.st + i * M;
-  const T *__restrict__ Pci = (const T *)a.Pc + i * (int64_t)(M * NK);
   T ao[NK][NV];
 #pragma unroll
   for (int k = 0; k < NK; ++k)
@@ -256,10 +275,10 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
 #pragma unroll
     for (int e = 0; e < M * NK; ++e) {
       const int m = e / NK, k = e % NK;
-      if (e % CH == 0) load16<T, CH>(Pci + e, pb);
+      if (e % CH == 0) load16<T, CH, SH>(Pci + e, pb);
       if (k == 0) {
         if (m % 4 == 0) {
-          const int4 t4 = __ldg(reinterpret_cast<const int4 *>(sti + m));
+          const int4 t4 = load_i4<SH>(sti + m);
           ids[0] = t4.x; ids[1] = t4.y; ids[2] = t4.z; ids[3] = t4.w;
         }
         delta(ids[m % 4], du);
@@ -286,12 +305,12 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
       const int nm = (info >> (4 * f)) & 15u;
       if ((adm >> f) & 1u) {
         T pf[PDS];
-        load16<T, PDS>((const T *)a.Pd + (i * NF + f) * PDS, pf);
+        load16<T, PDS, SH>(Pdi + f * PDS, pf);
 #pragma unroll
         for (int jj = 0; jj < ND; ++jj) {
           if (jj < nm) {
             T du[NV];
-            delta(__ldg(sti + off + jj), du);
+            delta(load_i1<SH>(sti + off + jj), du);
 #pragma unroll
             for (int k = 0; k < D; ++k)
 #pragma unroll
@@ -307,12 +326,13 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
   const int stn = 1 + __popc(adm);
   T lams;
   double lamsd = 0.0;
-  float log2lams = 0.0f;
+  float log2lams = 0.0f, inv_stm1 = 0.0f;
   if constexpr (F32) {
-    lams = (stn > 1) ? a.one_m_lam1_32 / (float)(stn - 1) : 0.0f;
-    if (stn > 1) log2lams = a.log2_one_m_lam1 - log2f((float)(stn - 1));
+    lams = pick<NF>(a.lams_f, stn - 1);
+    log2lams = pick<NF>(a.log2_lams_f, stn - 1);
+    inv_stm1 = pick<NF>(a.inv_stm1_f, stn - 1);
   } else {
-    lamsd = (stn > 1) ? a.one_m_lam1 / (stn - 1) : 0.0;
+    lamsd = pick<NF>(a.lams_d, stn - 1);
     lams = lamsd;
   }
   T inv_lam1;
@@ -357,7 +377,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
     // 5: selection
     uint32_t bits;
     if constexpr (F32) {
-      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, log2lam1, log2lams, a.eps32,
+      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, log2lam1, log2lams, inv_stm1, a.eps32,
                              a.C_T32);
     } else {
       bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
@@ -409,8 +429,12 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
       T ke = (T)0;
 #pragma unroll
       for (int j = 0; j < D; ++j) ke += fb[q * NV + 1 + j] * fb[q * NV + 1 + j];
-      const T pr = gm1 * (fb[q * NV + NV - 1] - (T)0.5 * ke / fb[q * NV]);
-      bad = bad || !(fb[q * NV] > (T)0) || !(pr > (T)0);
+      if constexpr (F32) {  // rho > 0 and p > 0, the latter as rho E - |m|^2 / 2 > 0 (no division)
+        bad = bad || !(fb[q * NV] > 0.0f) || !(fb[q * NV] * fb[q * NV + NV - 1] - 0.5f * ke > 0.0f);
+      } else {
+        const T pr = gm1 * (fb[q * NV + NV - 1] - (T)0.5 * ke / fb[q * NV]);
+        bad = bad || !(fb[q * NV] > (T)0) || !(pr > (T)0);
+      }
     }
     if constexpr (D == 2) {  // edge stored in sorted-vertex order: swap the two points
       if (p) {
@@ -435,6 +459,35 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
     atomicAdd(a.guard, 1ull);
   }
 
+}
+
+// MINB > 0: register-capped variant (at most 128 threads per block, MINB blocks per SM), which the
+// autotuner weighs against the uncapped one (occupancy and wave count against spills).
+template <int D, int R, typename T, int SCHEME, int MINB>
+__global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kernel(const KArgs a) {
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  constexpr int NF = L::NF, NQ = L::NQ, PDS = L::PDS;
+  constexpr int NK = S::NK, M = S::M, NP = S::NP;
+  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
+  // 3D: face-point basis values for all six vertex orders of a face, staged in shared memory
+  __shared__ T sPhi[NPHI];
+  if constexpr (D == 3) {
+    const DevTables &tb = *a.tab;
+    for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
+      const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
+      sPhi[t] = (T)tb.Phi[f][p][q][k];
+    }
+    __syncthreads();
+  }
+
+  const int64_t N = a.N;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+
+  recon_cell<D, R, T, SCHEME, false>(a, i, (const T *)a.Pc + i * (int64_t)(M * NK),
+                                     (const T *)a.Pd + i * (int64_t)(NF * PDS), a.st + i * M, sPhi);
+
   // CFL time step bookkeeping at the first stage of a step: dt[next] -> dt[cur]
   if (a.dt_swap && i < a.nmesh) {
     a.dt[i] = a.dt[a.nmesh + i];
@@ -450,34 +503,22 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
 // neighbour's record are split over the group. A warp holds floor(32 / NV) cells; spare lanes
 // and lanes past the last cell work on a clamped cell and store nothing.
 // ---------------------------------------------------------------------------------------------
-template <int D, int R, typename T, int SCHEME>
-__global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
+// One cell of the variable-per-lane schedule, seen from lane v of its group (first lane base);
+// every lane of the warp calls it (inactive lanes with a clamped valid cell i) because the
+// positivity guard exchanges values with shuffles. Operator pointers as for recon_cell.
+template <int D, int R, typename T, int SCHEME, bool SH>
+__device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, const bool active, const int v,
+                                           const int base, const T *__restrict__ Pci,
+                                           const T *__restrict__ Pdi, const int32_t *__restrict__ sti,
+                                           const T *__restrict__ sPhi) {
   using S = Shape<D, R>;
   using L = Lay<D>;
-  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, ND = L::ND, PDS = L::PDS;
+  constexpr int NVP = L::NVP, NF = L::NF, NQ = L::NQ, ND = L::ND, PDS = L::PDS;
+  constexpr int NV = L::NV;
   constexpr int NK = S::NK, M = S::M, NP = S::NP;
-  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
   constexpr int CH = Vec16<T>::n;
-  constexpr int CPW = 32 / NV;  // cells per warp
   constexpr bool F32 = sizeof(T) == 4;
-  __shared__ T sPhi[NPHI];
-  if constexpr (D == 3) {
-    const DevTables &tb = *a.tab;
-    for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
-      const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
-      sPhi[t] = (T)tb.Phi[f][p][q][k];
-    }
-    __syncthreads();
-  }
-  const int lane = threadIdx.x & 31;
-  const int grp = lane / NV;                // cell slot in the warp (CPW = spare lanes)
-  const int v = lane - grp * NV;            // this lane's variable
-  const int base = grp * NV;                // first lane of the group
   const int64_t N = a.N;
-  const int64_t cell = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * CPW + grp;
-  const bool active = grp < CPW && cell < N;
-  const int64_t i = active ? cell : N - 1;  // spare lanes shadow a valid cell
-
   // own mean of variable v: FP64, or the FP32 pair (hi, lo)
   T U0;
   float L0;
@@ -499,8 +540,6 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
   };
 
   // central coefficients of variable v
-  const int32_t *__restrict__ sti = a.st + i * M;
-  const T *__restrict__ Pci = (const T *)a.Pc + i * (int64_t)(M * NK);
   T ao[NK];
 #pragma unroll
   for (int k = 0; k < NK; ++k) ao[k] = (T)0;
@@ -510,10 +549,10 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
 #pragma unroll
     for (int e = 0; e < M * NK; ++e) {
       const int m = e / NK, k = e % NK;
-      if (e % CH == 0) load16<T, CH>(Pci + e, pb);
+      if (e % CH == 0) load16<T, CH, SH>(Pci + e, pb);
       if (k == 0) {
         if (m % 4 == 0) {
-          const int4 t4 = __ldg(reinterpret_cast<const int4 *>(sti + m));
+          const int4 t4 = load_i4<SH>(sti + m);
           ids[0] = t4.x; ids[1] = t4.y; ids[2] = t4.z; ids[3] = t4.w;
         }
         du = delta(ids[m % 4]);
@@ -536,11 +575,11 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
       const int nm = (info >> (4 * f)) & 15u;
       if ((adm >> f) & 1u) {
         T pf[PDS];
-        load16<T, PDS>((const T *)a.Pd + (i * NF + f) * PDS, pf);
+        load16<T, PDS, SH>(Pdi + f * PDS, pf);
 #pragma unroll
         for (int jj = 0; jj < ND; ++jj) {
           if (jj < nm) {
-            const T du = delta(__ldg(sti + off + jj));
+            const T du = delta(load_i1<SH>(sti + off + jj));
 #pragma unroll
             for (int k = 0; k < D; ++k) ad[f][k] += pf[jj * D + k] * du;
           }
@@ -553,12 +592,13 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
   const int stn = 1 + __popc(adm);
   T lams;
   double lamsd = 0.0;
-  float log2lams = 0.0f;
+  float log2lams = 0.0f, inv_stm1 = 0.0f;
   if constexpr (F32) {
-    lams = (stn > 1) ? a.one_m_lam1_32 / (float)(stn - 1) : 0.0f;
-    if (stn > 1) log2lams = a.log2_one_m_lam1 - log2f((float)(stn - 1));
+    lams = pick<NF>(a.lams_f, stn - 1);
+    log2lams = pick<NF>(a.log2_lams_f, stn - 1);
+    inv_stm1 = pick<NF>(a.inv_stm1_f, stn - 1);
   } else {
-    lamsd = (stn > 1) ? a.one_m_lam1 / (stn - 1) : 0.0;
+    lamsd = pick<NF>(a.lams_d, stn - 1);
     lams = lamsd;
   }
   constexpr T INV_FACT = (D == 2) ? (T)0.5 : (T)(1.0 / 6.0);
@@ -597,7 +637,7 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
     }
     uint32_t bits;
     if constexpr (F32) {
-      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.log2_lam1, log2lams, a.eps32,
+      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.log2_lam1, log2lams, inv_stm1, a.eps32,
                              a.C_T32);
     } else {
       bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
@@ -651,8 +691,12 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
         const T m = __shfl_sync(0xffffffffu, val, base + 1 + j);
         ke += m * m;
       }
-      const T pr = gm1 * (E - (T)0.5 * ke / rho);
-      bad = bad || !(rho > (T)0) || !(pr > (T)0);
+      if constexpr (F32) {  // rho > 0 and p > 0, the latter as rho E - |m|^2 / 2 > 0 (no division)
+        bad = bad || !(rho > 0.0f) || !(rho * E - 0.5f * ke > 0.0f);
+      } else {
+        const T pr = gm1 * (E - (T)0.5 * ke / rho);
+        bad = bad || !(rho > (T)0) || !(pr > (T)0);
+      }
     }
   }
   if (a.guard_on && bad) {
@@ -674,11 +718,175 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
       }
     }
   }
+}
+
+template <int D, int R, typename T, int SCHEME>
+__global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  constexpr int NV = L::NV, NF = L::NF, NQ = L::NQ, PDS = L::PDS;
+  constexpr int NK = S::NK, M = S::M, NP = S::NP;
+  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
+  constexpr int CPW = 32 / NV;  // cells per warp
+  __shared__ T sPhi[NPHI];
+  if constexpr (D == 3) {
+    const DevTables &tb = *a.tab;
+    for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
+      const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
+      sPhi[t] = (T)tb.Phi[f][p][q][k];
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / NV;                // cell slot in the warp (CPW = spare lanes)
+  const int v = lane - grp * NV;            // this lane's variable
+  const int base = grp * NV;                // first lane of the group
+  const int64_t N = a.N;
+  const int64_t cell = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * CPW + grp;
+  const bool active = grp < CPW && cell < N;
+  const int64_t i = active ? cell : N - 1;  // spare lanes shadow a valid cell
+
+  recon_lane<D, R, T, SCHEME, false>(a, i, active, v, base, (const T *)a.Pc + i * (int64_t)(M * NK),
+                                     (const T *)a.Pd + i * (int64_t)(NF * PDS), a.st + i * M, sPhi);
   if (a.dt_swap && blockIdx.x == 0)
     for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {
       a.dt[t] = a.dt[a.nmesh + t];
       a.dt[a.nmesh + t] = 1e300;
     }
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Staged schedules: a persistent grid walks tiles of C consecutive cells, C the cells of one block
+// of the thread-per-cell or variable-per-lane schedule. The operator records of a tile (central
+// pseudo-inverses, directional operators, stencil ids) are three contiguous spans of the
+// cell-major layout; one thread fetches them with three bulk copies into one of two shared-memory
+// stages while the block computes on the other, so each SM keeps a whole tile of the dominant
+// stream in flight instead of what its warps' outstanding loads cover.
+// ---------------------------------------------------------------------------------------------
+template <int D, int R, typename T>
+struct StagedRecord {  // bytes per cell of each stream
+  static constexpr int PC = Shape<D, R>::M * Shape<D, R>::NK * (int)sizeof(T);
+  static constexpr int PD = Lay<D>::NF * Lay<D>::PDS * (int)sizeof(T);
+  static constexpr int ST = Shape<D, R>::M * 4;
+  static constexpr int CELL = PC + PD + ST;
+  static_assert(PC % 16 == 0 && PD % 16 == 0 && ST % 16 == 0, "bulk copies need 16-byte spans");
+};
+constexpr uint64_t kStageWaitNs = 1000000000ull;  // 1 s: far above any tile's copy time
+
+template <int D, int R, typename T, int SCHEME, bool LANES>
+__global__ void __launch_bounds__(256) recon_staged_kernel(const KArgs a) {
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  using B = StagedRecord<D, R, T>;
+  constexpr int NV = L::NV, NF = L::NF, NQ = L::NQ, PDS = L::PDS;
+  constexpr int NK = S::NK, M = S::M, NP = S::NP;
+  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
+  constexpr int CPW = 32 / NV;
+  __shared__ T sPhi[NPHI];
+  __shared__ __align__(8) uint64_t bar[2];
+  extern __shared__ __align__(128) unsigned char stage_mem[];
+
+  const int C = LANES ? (int)(blockDim.x >> 5) * CPW : (int)blockDim.x;
+  const int64_t N = a.N;
+  const int64_t tiles = (N + C - 1) / C;
+  unsigned char *const stage0 = stage_mem, *const stage1 = stage_mem + (size_t)C * B::CELL;
+  auto sPc = [&](int s) { return reinterpret_cast<T *>(s ? stage1 : stage0); };
+  auto sPd = [&](int s) { return reinterpret_cast<T *>((s ? stage1 : stage0) + (size_t)C * B::PC); };
+  auto sSt = [&](int s) {
+    return reinterpret_cast<int32_t *>((s ? stage1 : stage0) + (size_t)C * (B::PC + B::PD));
+  };
+  // thread 0 only: fetch the records of `tile` into stage s
+  auto issue = [&](int64_t tile, int s) {
+    const int64_t c0 = tile * C;
+    const uint32_t n = (uint32_t)min((int64_t)C, N - c0);
+    mbar_arrive_expect_tx(&bar[s], n * (uint32_t)B::CELL);
+    bulk_copy_g2s(sPc(s), (const unsigned char *)a.Pc + c0 * B::PC, n * B::PC, &bar[s]);
+    bulk_copy_g2s(sPd(s), (const unsigned char *)a.Pd + c0 * B::PD, n * B::PD, &bar[s]);
+    bulk_copy_g2s(sSt(s), (const unsigned char *)a.st + c0 * B::ST, n * B::ST, &bar[s]);
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  if constexpr (D == 3) {
+    const DevTables &tb = *a.tab;
+    for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
+      const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
+      sPhi[t] = (T)tb.Phi[f][p][q][k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if ((int64_t)blockIdx.x < tiles) issue(blockIdx.x, 0);
+    if ((int64_t)blockIdx.x + gridDim.x < tiles) issue((int64_t)blockIdx.x + gridDim.x, 1);
+  }
+  // CFL time step bookkeeping at the first stage of a step: dt[next] -> dt[cur]
+  if (a.dt_swap && blockIdx.x == 0)
+    for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {
+      a.dt[t] = a.dt[a.nmesh + t];
+      a.dt[a.nmesh + t] = 1e300;
+    }
+
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+    const int s = it & 1;
+    const uint32_t parity = (it >> 1) & 1;
+    const bool ok = mbar_wait(&bar[s], parity, kStageWaitNs);
+    if (__syncthreads_or(!ok)) {  // the whole block stops; its copies in flight are awaited
+      if (threadIdx.x == 0) {
+        atomicOr(a.err, kErrTimeout);
+        mbar_wait(&bar[s], parity, kStageWaitNs);
+        if (tile + gridDim.x < tiles) mbar_wait(&bar[s ^ 1], ((it + 1) >> 1) & 1, kStageWaitNs);
+      }
+      return;
+    }
+    const int64_t c0 = tile * C;
+    const int nvalid = (int)min((int64_t)C, N - c0);
+    if constexpr (LANES) {
+      const int lane = threadIdx.x & 31, grp = lane / NV;
+      const int slot = (int)(threadIdx.x >> 5) * CPW + grp;
+      const bool active = grp < CPW && slot < nvalid;
+      const int ls = active ? slot : nvalid - 1;  // spare lanes shadow a valid cell of the tile
+      recon_lane<D, R, T, SCHEME, true>(a, c0 + ls, active, lane - grp * NV, grp * NV,
+                                        sPc(s) + ls * (M * NK), sPd(s) + ls * (NF * PDS),
+                                        sSt(s) + ls * M, sPhi);
+    } else {
+      const int slot = threadIdx.x;
+      if (slot < nvalid)
+        recon_cell<D, R, T, SCHEME, true>(a, c0 + slot, sPc(s) + slot * (M * NK),
+                                          sPd(s) + slot * (NF * PDS), sSt(s) + slot * M, sPhi);
+    }
+    __syncthreads();  // every thread is done with stage s
+    if (threadIdx.x == 0 && tile + 2 * (int64_t)gridDim.x < tiles) {
+      fence_proxy_async_shared();
+      issue(tile + 2 * (int64_t)gridDim.x, s);
+    }
+  }
+}
+
+// Host side: persistent launch of the staged kernel, grid = (co-resident blocks per SM) x SMs.
+template <int D, int R, typename T, int SCHEME, bool LANES>
+void launch_recon_staged(const KArgs &a, int threads, cudaStream_t s) {
+  const int C = LANES ? (threads / 32) * (32 / (D + 2)) : threads;
+  const size_t smem = (size_t)2 * C * StagedRecord<D, R, T>::CELL;
+  auto kern = recon_staged_kernel<D, R, T, SCHEME, LANES>;
+  static int resident[9] = {};  // per threads / 32
+  static int sms = 0;
+  int &nb = resident[threads / 32];
+  if (!nb) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStagedSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+    if (nb < 1) nb = 1;  // a launch that cannot fit fails loudly below
+  }
+  const int64_t tiles = (a.N + C - 1) / C;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)nb * sms);
+  kern<<<grid, threads, smem, s>>>(a);
 }
 
 }  // namespace cteno

@@ -4,6 +4,20 @@
 namespace cteno {
 
 void launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s) {
+  if (block >= kStagedCells) {  // staged persistent schedules (mixed path; the launch value is
+                                // validated by the caller)
+    const bool lanes = block >= kStagedLanes;
+    const int threads = block - (lanes ? kStagedLanes : kStagedCells);
+    if (!fp32) return;
+#define CTENO_STAGED(R, SC) \
+  (lanes ? launch_recon_staged<3, R, float, SC, true>(a, threads, s) : launch_recon_staged<3, R, float, SC, false>(a, threads, s))
+    if (degree == 2 && scheme == 0) CTENO_STAGED(2, 0);
+    if (degree == 2 && scheme == 1) CTENO_STAGED(2, 1);
+    if (degree == 3 && scheme == 0) CTENO_STAGED(3, 0);
+    if (degree == 3 && scheme == 1) CTENO_STAGED(3, 1);
+#undef CTENO_STAGED
+    return;
+  }
   if (block >= kLaneSchedule) {  // variable-per-lane schedule, block - kLaneSchedule threads
     const int threads = block - kLaneSchedule, cpw = 32 / (3 + 2);
     const int64_t cells_per_block = (int64_t)(threads / 32) * cpw;

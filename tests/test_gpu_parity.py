@@ -189,17 +189,40 @@ def test_batched_meshes_match_independent_oracles():
     s.close()
 
 
-@pytest.mark.parametrize("launch", [(128, 128), (-128, -128), (1024 + 128, 1024 + 256), (1024 + 256, 256)],
-                         ids=["cell-thread", "capped", "var-lanes-128", "var-lanes-256"])
+def _staged_smem(d, degree, launch):
+    """Shared memory of a staged launch value: two stages of a tile's operator records (FP32)."""
+    nk = ((degree + 1) * (degree + 2) // 2 if d == 2 else (degree + 1) * (degree + 2) * (degree + 3) // 6) - 1
+    M = 2 * (nk + 1)
+    lanes = launch >= 3072
+    threads = launch - (3072 if lanes else 2048)
+    cells = (threads // 32) * (32 // (d + 2)) if lanes else threads
+    return 2 * cells * (4 * M * nk + 4 * (d + 1) * (8 if d == 2 else 20) + 4 * M)
+
+
+STAGED_SMEM_MAX = 200 * 1024
+
+
+@pytest.mark.parametrize("launch", [(128, 128), (-128, -128), (1024 + 128, 1024 + 256), (1024 + 256, 256),
+                                    (2048 + 32, 128), (2048 + 64, -128), (3072 + 64, 1024 + 128),
+                                    (3072 + 128, 256), (3072 + 256, 128)],
+                         ids=["cell-thread", "capped", "var-lanes-128", "var-lanes-256", "staged-cells-32",
+                              "staged-cells-64", "staged-lanes-64", "staged-lanes-128", "staged-lanes-256"])
 def test_mixed_schedules_agree(launch):
     """Every launch schedule of the mixed path gives the same face states and update on a 2D and a
-    3D mesh (the arithmetic per variable is the same in each schedule)."""
+    3D mesh (the arithmetic per variable is the same in each schedule). A staged schedule whose two
+    stages do not fit in shared memory is refused."""
     native = _native()
-    for wl, d, deg in ((W.shock_tube_2d(40, 12), 2, 3), (W.blast_3d(6), 3, 3)):
+    for wl, d, deg in ((W.shock_tube_2d(40, 12), 2, 3), (W.blast_3d(6), 3, 3), (W.blast_3d(5), 3, 2),
+                       (W.shock_tube_2d(37, 11), 2, 2)):
+        s = _solver(native, [wl.mesh], d, degree=deg, precision=1)
+        if launch[0] >= 2048 and _staged_smem(d, deg, launch[0]) > STAGED_SMEM_MAX:
+            with pytest.raises(native.CtenoError):
+                native.cteno_set_launch(s.ctx, *launch)
+            s.close()
+            continue
         ref = _solver(native, [wl.mesh], d, degree=deg, precision=1)
         ref.set_state(wl.U0)
         ref.stage(0, 1e-4)
-        s = _solver(native, [wl.mesh], d, degree=deg, precision=1)
         native.cteno_set_launch(s.ctx, *launch)
         s.set_state(wl.U0)
         s.stage(0, 1e-4)
@@ -336,6 +359,37 @@ def test_full_size_shock_tube_sampled_residual():
         s.close()
 
 
+@pytest.mark.parametrize("launch", [None, (2048 + 64, 0), (3072 + 128, 0)],
+                         ids=["autotuned", "staged-cells-64", "staged-lanes-128"])
+def test_full_size_shock_tube_mixed_sampled_residual(launch):
+    """The benchmark's workload and precision: 512x128 shock tube, mixed path, CTENO degree 2, in
+    the autotuned launch configuration (and with each staged schedule forced). One stage against
+    the FP64 oracle's residual at sampled cells; FP32 reconstruction with (hi, lo) differences
+    keeps the residual within 1e-5 of its scale."""
+    native = _native()
+    from oracle import Oracle
+    wl = W.shock_tube_2d(512, 128)
+    s = _solver(native, [wl.mesh], 2, degree=2, scheme=0, precision=1, cfl=0.4)
+    s.set_state(wl.U0)
+    if launch is None:
+        native.cteno_autotune(s.ctx)
+    else:
+        native.cteno_set_launch(s.ctx, *launch)
+    dt = 1e-4
+    s.stage(0, dt)
+    R_gpu = (s.get_state() - wl.U0) / dt
+    o = Oracle(wl.mesh, setup=False, degree=2, scheme=0)
+    o.set_state(wl.U0)
+    cen = W.cell_centroids(wl.mesh)
+    rng = np.random.default_rng(7)
+    near = np.where(np.abs(cen[:, 0] - 0.5) < 0.01)[0]
+    ids = np.concatenate([rng.choice(near, 40, replace=False), rng.choice(wl.mesh.ncells, 40, replace=False)])
+    R_orc = o.residual_cells(ids)
+    scale = np.abs(R_orc).max(axis=0) + 1e-300
+    assert (np.abs(R_gpu[:, ids].T - R_orc) / scale).max() < 1e-5
+    s.close()
+
+
 def test_rejects_bad_calls_without_faulting():
     native = _native()
     wl = W.density_wave_2d(8)
@@ -346,6 +400,10 @@ def test_rejects_bad_calls_without_faulting():
         native.cteno_rk_stage(s.ctx, 5, [1e-3])          # no such stage
     with pytest.raises(native.CtenoError):
         native.cteno_set_launch(s.ctx, 100, 0)           # not a multiple of 32
+    with pytest.raises(native.CtenoError):
+        native.cteno_set_launch(s.ctx, 2048 + 64, 0)     # staged schedules: mixed path only
+    with pytest.raises(native.CtenoError):
+        native.cteno_set_launch(s.ctx, 128, 3072 + 64)   # and reconstruction only
     s.set_state(wl.U0)
     s.run(1)
     assert s.sync() == 0
