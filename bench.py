@@ -216,6 +216,8 @@ def alu_peak(native):
 def recon_kernel_name(dim, degree, scheme, launch):
     """Name of the mixed-path reconstruction kernel a launch value selects."""
     args = f"{dim},{degree},float,{SCHEMES[scheme]}"
+    if launch == 4096:
+        return f"recon_halo_kernel<{args}> x128"
     if launch >= 3072:
         return f"recon_staged_kernel<{args},lanes> x{launch - 3072}"
     if launch >= 2048:

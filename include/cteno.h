@@ -178,11 +178,14 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
  * floor(32/(d+2)) cells per warp) into shared memory with bulk copies, two tiles in flight; refused
  * (CTENO_ERR_ARG) when the two stages need more than 200 KiB of shared memory. If a bounded wait for
  * such a copy ever gives up (after 1 s), the kernel stops and the next synchronising call returns
- * CTENO_ERR_DEVICE. */
+ * CTENO_ERR_DEVICE. 4096 (mixed path) selects that lane schedule with 4 warps whose tiles also copy
+ * the states of their distinct stencil members into shared memory (lists built by cteno_lsq_build);
+ * refused like the staged values when it does not fit. */
 int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block);
 
 /* Time the candidate launch configurations (block sizes 64/128/256, on the mixed path the
- * register-capped variants at 64/128 and the staged reconstruction schedules that fit, and the
+ * register-capped variants at 64/128 and the staged and gather-staged reconstruction schedules
+ * that fit, and the
  * lane schedules at 128/256 threads) on the current
  * state and keep the fastest; the state is
  * restored afterwards. best_out[2] (may be NULL) receives the chosen values, in the convention of

@@ -31,6 +31,9 @@ struct cteno_ctx {
   double *U = nullptr, *Un = nullptr;
   float *U32 = nullptr;
   int32_t *st = nullptr, *nbr = nullptr;
+  int32_t *hl = nullptr;             // gather staging: per-tile distinct member lists (mixed path)
+  uint16_t *lidx = nullptr;          //   and per-cell local indices into them
+  int hrec = 0, hms = 0;
   uint32_t *cinfo = nullptr, *fmeta = nullptr;
   void *Pc = nullptr, *Pd = nullptr, *Uf = nullptr;
   uint8_t *flags = nullptr;
@@ -87,6 +90,11 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.Un = ctx->Un;
   a.U32 = ctx->U32;
   a.st = ctx->st;
+  a.hl = ctx->hl;
+  a.lidx = ctx->lidx;
+  a.htile = halo_tile(ctx->d);
+  a.hrec = ctx->hrec;
+  a.hms = ctx->hms;
   a.cinfo = ctx->cinfo;
   a.Pc = ctx->Pc;
   a.Pd = ctx->Pd;
@@ -286,6 +294,55 @@ int cteno_stencil_build(cteno_ctx *ctx) {
   return CTENO_OK;
 }
 
+namespace {
+// Gather staging lists for tiles of halo_tile(d) consecutive device cells: the distinct stencil
+// members of the tile's cells and the cells themselves, ascending, in a record of hrec int32 words
+// [count, 0, 0, 0, ids..., 0 padding]; per cell halo_ms(M) uint16 local indices (its stencil in
+// device order, then itself). Tiles may span mesh boundaries (ids are device ids).
+int build_gather_tiles(cteno_ctx *ctx, const std::vector<int32_t> &hst) {
+  const int64_t N = ctx->N;
+  const int M = ctx->M, C = halo_tile(ctx->d), MS = halo_ms(M);
+  const int64_t ntiles = (N + C - 1) / C;
+  std::vector<std::vector<int32_t>> lists(ntiles);
+  std::vector<uint16_t> li((size_t)ntiles * C * MS, 0);
+  int hmax = 0;
+#pragma omp parallel for reduction(max : hmax) schedule(static)
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const int64_t c0 = t * C, c1 = std::min<int64_t>(N, c0 + C);
+    std::vector<int32_t> &L = lists[t];
+    for (int64_t g = c0; g < c1; ++g) {
+      for (int p = 0; p < M; ++p) L.push_back(hst[(size_t)g * M + p]);
+      L.push_back((int32_t)g);
+    }
+    std::sort(L.begin(), L.end());
+    L.erase(std::unique(L.begin(), L.end()), L.end());
+    auto local = [&](int32_t id) { return (uint16_t)(std::lower_bound(L.begin(), L.end(), id) - L.begin()); };
+    for (int64_t g = c0; g < c1; ++g) {
+      uint16_t *row = &li[(size_t)g * MS];
+      for (int p = 0; p < M; ++p) row[p] = local(hst[(size_t)g * M + p]);
+      row[M] = local((int32_t)g);
+    }
+    hmax = std::max(hmax, (int)L.size());
+  }
+  if (hmax > 65535) return CTENO_OK;  // not representable: the schedule stays unavailable
+  const int hrec = 4 + (hmax + 3) / 4 * 4;
+  std::vector<int32_t> hh((size_t)ntiles * hrec, 0);
+  for (int64_t t = 0; t < ntiles; ++t) {
+    int32_t *rec = &hh[(size_t)t * hrec];
+    rec[0] = (int32_t)lists[t].size();
+    std::copy(lists[t].begin(), lists[t].end(), rec + 4);
+  }
+  CK(dalloc(ctx, &ctx->hl, hh.size() * sizeof(int32_t)));
+  CK(dalloc(ctx, &ctx->lidx, li.size() * sizeof(uint16_t)));
+  CK(cudaMemcpyAsync(ctx->hl, hh.data(), hh.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->lidx, li.data(), li.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));  // the host arrays go out of scope
+  ctx->hrec = hrec;
+  ctx->hms = MS;
+  return CTENO_OK;
+}
+}  // namespace
+
 int cteno_lsq_build(cteno_ctx *ctx) {
   if (!ctx) return CTENO_ERR_ARG;
   if (!ctx->stencils) return fail(ctx, CTENO_ERR_STATE, "cteno_stencil_build has not run");
@@ -405,6 +462,10 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   CK(cudaMemcpyAsync(ctx->d_mesh_off, hoff.data(), sizeof(int64_t) * (nmesh + 1), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(dX, hX.data(), hX.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->st, hst.data(), hst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->fp32) {
+    const int rc = build_gather_tiles(ctx, hst);
+    if (rc) return rc;
+  }
   CK(cudaMemcpyAsync(ctx->nbr, hnbr.data(), hnbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->cinfo, hinfo.data(), hinfo.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->fmeta, hmeta.data(), hmeta.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
@@ -639,6 +700,8 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
   // variant (mixed path only, at most 128 threads)
   auto ok = [&](int b, bool recon) {
     if (b == 0) return true;
+    if (b == kHaloLanes)  // gather-staged schedule: reconstruction, mixed path, lists built, fits
+      return recon && ctx->fp32 && ctx->hl && recon_halo_smem(ctx->d, ctx->p.degree, ctx->hrec) <= kMaxStagedSmem;
     if (b >= kStagedCells) {  // staged schedules: reconstruction, mixed path, two stages that fit
       const int t = b - (b >= kStagedLanes ? kStagedLanes : kStagedCells);
       return recon && ctx->fp32 && b < kStagedLanes + 1024 && t >= 32 && t <= 256 && t % 32 == 0 &&
@@ -700,6 +763,8 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
     for (int b : {kStagedCells + 32, kStagedCells + 64, kStagedCells + 128, kStagedLanes + 64,
                   kStagedLanes + 128, kStagedLanes + 256})
       if (recon_staged_smem(ctx->d, ctx->p.degree, 1, b) <= kMaxStagedSmem) rcand.push_back(b);
+  if (ctx->fp32 && ctx->hl && recon_halo_smem(ctx->d, ctx->p.degree, ctx->hrec) <= kMaxStagedSmem)
+    rcand.push_back(kHaloLanes);
   const int reps = 5;
   float best_r = 1e30f, best_f = 1e30f;
   int br = ctx->recon_block, bf = ctx->flux_block;

@@ -104,6 +104,12 @@ struct KArgs {
   float gamma32, gm1_32, eps32, C_T32, inv_lam1_32, one_m_lam1_32, cfl32;
   float fw32[kMaxNQ];
   double fw[kMaxNQ];        // face quadrature weights
+  // gather staging (mixed path): cells in tiles of htile; per tile a record of hrec int32 words
+  // [count, 0, 0, 0, distinct member ids ascending, padding]; per cell hms uint16 local indices
+  // into its tile's list (stencil members in device order, then the cell itself)
+  const int32_t *hl;
+  const uint16_t *lidx;
+  int htile, hrec, hms;
   int stage;                // 0, 1, 2
   int dt_swap;              // stage 0 of a CFL step: move dt[next] to dt[cur] first
 };
@@ -134,6 +140,20 @@ constexpr int kLaneSchedule = 1024;
 constexpr int kStagedCells = 2048;
 constexpr int kStagedLanes = 3072;
 constexpr int kMaxStagedSmem = 200 * 1024;  // dynamic shared memory of the two stages, at most
+// kHaloLanes: the staged lane schedule (4 warps) that also stages each tile's distinct stencil
+// members' states in shared memory (mixed path).
+constexpr int kHaloLanes = 4096;
+constexpr int kHaloWarps = 4;
+inline int halo_tile(int d) { return kHaloWarps * (32 / (d + 2)); }
+inline int halo_ms(int M) { return (M + 1 + 7) / 8 * 8; }
+// Dynamic shared memory of the gather-staged launch for a tile record of hrec words.
+inline long long recon_halo_smem(int d, int degree, int hrec) {
+  const int nk = (d == 2 ? (degree + 1) * (degree + 2) / 2 : (degree + 1) * (degree + 2) * (degree + 3) / 6) - 1;
+  const int M = 2 * (nk + 1), C = halo_tile(d);
+  const long long rec = (long long)M * nk * 4 + (long long)(d + 1) * lay_pds(d) * 4 + 2LL * halo_ms(M);
+  const long long hs = 8LL * lay_nvp(d);  // one FP32 (hi, lo) state record
+  return 2 * (C * rec + 4LL * hrec + (long long)(hrec - 4) * hs);
+}
 
 // Dynamic shared memory of a staged launch value (two stages of a tile's operator records).
 inline long long recon_staged_smem(int d, int degree, int fp32, int block) {

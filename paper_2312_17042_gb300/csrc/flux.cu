@@ -118,27 +118,26 @@ __device__ __forceinline__ void hllc(const T *uL, const T *uR, const T *n, T g, 
   const T SR = fmax(unR + cR, utn + ct);
   const T SM = div_<T>(rR * unR * (SR - unR) - rL * unL * (SL - unL) + pL - pR,
                        rR * (SR - unR) - rL * (SL - unL));
-  if (SL > (T)0) {
-    physical_flux<D, T>(uL, n, pL, unL, F);
-  } else if (SM > (T)0) {
-    const T ps = rL * (unL - SL) * (unL - SM) + pL;
-    const T fct = rcp_<T>(SL - SM), a = SL - unL;
-    physical_flux<D, T>(uL, n, pL, unL, F);
-    F[0] += SL * (rL * a * fct - uL[0]);
+  // The four cases, tested in the order SL > 0 (left state), SM > 0 (left star state), SR > 0
+  // (right star state), else (right state), evaluated without branches (neighbouring faces of a
+  // warp take different cases): the operands of side k are selected, the star correction is
+  // dropped in the two supersonic cases. Each case's arithmetic is the same as written out alone.
+  const bool left = (SL > (T)0) || (SM > (T)0);
+  const bool sup = (SL > (T)0) || (!(SM > (T)0) && !(SR > (T)0));
+  T uk[NV];
 #pragma unroll
-    for (int j = 0; j < D; ++j) F[1 + j] += SL * ((a * uL[1 + j] + (ps - pL) * n[j]) * fct - uL[1 + j]);
-    F[NV - 1] += SL * ((a * uL[NV - 1] - pL * unL + ps * SM) * fct - uL[NV - 1]);
-  } else if (SR > (T)0) {
-    const T ps = rL * (unL - SL) * (unL - SM) + pL;
-    const T fct = rcp_<T>(SR - SM), a = SR - unR;
-    physical_flux<D, T>(uR, n, pR, unR, F);
-    F[0] += SR * (rR * a * fct - uR[0]);
+  for (int v = 0; v < NV; ++v) uk[v] = left ? uL[v] : uR[v];
+  const T pk = left ? pL : pR, unk = left ? unL : unR, Sk = left ? SL : SR, rk = uk[0];
+  physical_flux<D, T>(uk, n, pk, unk, F);
+  const T ps = rL * (unL - SL) * (unL - SM) + pL;
+  const T fct = rcp_<T>(Sk - SM), a = Sk - unk;
+  T G[NV];
+  G[0] = F[0] + Sk * (rk * a * fct - uk[0]);
 #pragma unroll
-    for (int j = 0; j < D; ++j) F[1 + j] += SR * ((a * uR[1 + j] + (ps - pR) * n[j]) * fct - uR[1 + j]);
-    F[NV - 1] += SR * ((a * uR[NV - 1] - pR * unR + ps * SM) * fct - uR[NV - 1]);
-  } else {
-    physical_flux<D, T>(uR, n, pR, unR, F);
-  }
+  for (int j = 0; j < D; ++j) G[1 + j] = F[1 + j] + Sk * ((a * uk[1 + j] + (ps - pk) * n[j]) * fct - uk[1 + j]);
+  G[NV - 1] = F[NV - 1] + Sk * ((a * uk[NV - 1] - pk * unk + ps * SM) * fct - uk[NV - 1]);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = sup ? F[v] : G[v];
 }
 
 __device__ __forceinline__ int mesh_of(const KArgs &a, int64_t i) {

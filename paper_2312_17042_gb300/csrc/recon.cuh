@@ -505,12 +505,17 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
 // ---------------------------------------------------------------------------------------------
 // One cell of the variable-per-lane schedule, seen from lane v of its group (first lane base);
 // every lane of the warp calls it (inactive lanes with a clamped valid cell i) because the
-// positivity guard exchanges values with shuffles. Operator pointers as for recon_cell.
-template <int D, int R, typename T, int SCHEME, bool SH>
+// positivity guard exchanges values with shuffles. Operator pointers as for recon_cell. HALO:
+// sti holds the cell's uint16 local indices (members, then the cell itself) into `halo`, the
+// shared-memory FP32 (hi, lo) records of its tile's distinct stencil members.
+template <int D, int R, typename T, int SCHEME, bool SH, bool HALO = false>
 __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, const bool active, const int v,
                                            const int base, const T *__restrict__ Pci,
-                                           const T *__restrict__ Pdi, const int32_t *__restrict__ sti,
-                                           const T *__restrict__ sPhi) {
+                                           const T *__restrict__ Pdi, const void *__restrict__ sti_,
+                                           const T *__restrict__ sPhi, const float *__restrict__ halo = nullptr) {
+  static_assert(!HALO || (SH && sizeof(T) == 4), "gather staging: shared-memory records, mixed path");
+  const int32_t *__restrict__ sti = reinterpret_cast<const int32_t *>(sti_);
+  const uint16_t *__restrict__ lid = reinterpret_cast<const uint16_t *>(sti_);
   using S = Shape<D, R>;
   using L = Lay<D>;
   constexpr int NVP = L::NVP, NF = L::NF, NQ = L::NQ, ND = L::ND, PDS = L::PDS;
@@ -522,7 +527,11 @@ __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, cons
   // own mean of variable v: FP64, or the FP32 pair (hi, lo)
   T U0;
   float L0;
-  if constexpr (F32) {
+  if constexpr (HALO) {
+    const float2 h = reinterpret_cast<const float2 *>(halo)[(int)lid[M] * NVP + v];
+    U0 = h.x;
+    L0 = h.y;
+  } else if constexpr (F32) {
     const float2 h = __ldg(reinterpret_cast<const float2 *>(a.U32) + i * NVP + v);
     U0 = h.x;
     L0 = h.y;
@@ -531,13 +540,17 @@ __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, cons
     L0 = 0.0f;
   }
   auto delta = [&](int64_t j) -> T {
-    if constexpr (F32) {
+    if constexpr (HALO) {
+      const float2 h = reinterpret_cast<const float2 *>(halo)[(int)j * NVP + v];
+      return (h.x - (float)U0) + (h.y - L0);
+    } else if constexpr (F32) {
       const float2 h = __ldg(reinterpret_cast<const float2 *>(a.U32) + j * NVP + v);
       return (h.x - (float)U0) + (h.y - L0);
     } else {
       return (T)(__ldg(a.U + j * NVP + v) - (double)U0);
     }
   };
+  constexpr int IDV = HALO ? 8 : 4;  // ids per 16-byte load
 
   // central coefficients of variable v
   T ao[NK];
@@ -545,17 +558,27 @@ __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, cons
   for (int k = 0; k < NK; ++k) ao[k] = (T)0;
   {
     T pb[CH], du = (T)0;
-    int ids[4];
+    int ids[IDV];
 #pragma unroll
     for (int e = 0; e < M * NK; ++e) {
       const int m = e / NK, k = e % NK;
       if (e % CH == 0) load16<T, CH, SH>(Pci + e, pb);
       if (k == 0) {
-        if (m % 4 == 0) {
-          const int4 t4 = load_i4<SH>(sti + m);
-          ids[0] = t4.x; ids[1] = t4.y; ids[2] = t4.z; ids[3] = t4.w;
+        if (m % IDV == 0) {
+          if constexpr (HALO) {
+            const uint4 w = *reinterpret_cast<const uint4 *>(lid + m);
+            const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              ids[2 * t] = (int)(ww[t] & 0xFFFFu);
+              ids[2 * t + 1] = (int)(ww[t] >> 16);
+            }
+          } else {
+            const int4 t4 = load_i4<SH>(sti + m);
+            ids[0] = t4.x; ids[1] = t4.y; ids[2] = t4.z; ids[3] = t4.w;
+          }
         }
-        du = delta(ids[m % 4]);
+        du = delta(ids[m % IDV]);
       }
       ao[k] += pb[e % CH] * du;
     }
@@ -579,7 +602,7 @@ __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, cons
 #pragma unroll
         for (int jj = 0; jj < ND; ++jj) {
           if (jj < nm) {
-            const T du = delta(load_i1<SH>(sti + off + jj));
+            const T du = delta(HALO ? (int)lid[off + jj] : load_i1<SH>(sti + off + jj));
 #pragma unroll
             for (int k = 0; k < D; ++k) ad[f][k] += pf[jj * D + k] * du;
           }
@@ -865,6 +888,154 @@ __global__ void __launch_bounds__(256) recon_staged_kernel(const KArgs a) {
       issue(tile + 2 * (int64_t)gridDim.x, s);
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Gather-staged lane schedule (mixed path): as the staged lane schedule with four warps, and in
+// addition the states of each tile's distinct stencil members (listed per tile on the host) are
+// copied into shared memory by all threads with 16-byte asynchronous copies, one tile ahead of
+// the computation; the cells' stencil ids are then 16-bit indices into that list, so every gather
+// of the reconstruction is a shared-memory read and each member state crosses L2 once per tile.
+// ---------------------------------------------------------------------------------------------
+template <int D, int R, int SCHEME>
+__global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs a) {
+  using T = float;
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  using B = StagedRecord<D, R, T>;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, PDS = L::PDS;
+  constexpr int NK = S::NK, M = S::M, NP = S::NP;
+  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
+  constexpr int CPW = 32 / NV, C = kHaloWarps * CPW;
+  constexpr int MS = (M + 1 + 7) / 8 * 8;   // local ids per cell
+  constexpr int HS = NVP * 2 * 4;           // bytes of one member state (FP32 pairs)
+  constexpr int LI = MS * 2;                // bytes of one cell's local ids
+  __shared__ T sPhi[NPHI];
+  __shared__ __align__(8) uint64_t bar[2];
+  extern __shared__ __align__(128) unsigned char stage_mem[];
+
+  const int64_t N = a.N;
+  const int64_t tiles = (N + C - 1) / C;
+  const int HR = a.hrec;  // words of a tile's member record
+  const size_t o_pd = (size_t)C * B::PC, o_li = o_pd + (size_t)C * B::PD, o_hl = o_li + (size_t)C * LI,
+               o_hs = o_hl + (size_t)HR * 4, stage_bytes = o_hs + (size_t)(HR - 4) * HS;
+  auto base = [&](int s) { return stage_mem + (size_t)s * stage_bytes; };
+  auto issue = [&](int64_t tile, int s) {  // thread 0: the tile's records
+    const int64_t c0 = tile * C;
+    const uint32_t n = (uint32_t)min((int64_t)C, N - c0);
+    mbar_arrive_expect_tx(&bar[s], n * (uint32_t)(B::PC + B::PD + LI) + (uint32_t)HR * 4u);
+    bulk_copy_g2s(base(s), (const unsigned char *)a.Pc + c0 * B::PC, n * B::PC, &bar[s]);
+    bulk_copy_g2s(base(s) + o_pd, (const unsigned char *)a.Pd + c0 * B::PD, n * B::PD, &bar[s]);
+    bulk_copy_g2s(base(s) + o_li, (const unsigned char *)a.lidx + c0 * LI, n * LI, &bar[s]);
+    bulk_copy_g2s(base(s) + o_hl, a.hl + tile * HR, (uint32_t)HR * 4u, &bar[s]);
+  };
+  auto gather = [&](int s) {  // all threads: the tile's member states (its records have landed)
+    const int32_t *hl = reinterpret_cast<const int32_t *>(base(s) + o_hl);
+    const int cnt = hl[0];
+    unsigned char *hs = base(s) + o_hs;
+    for (int t = threadIdx.x; t < cnt * (HS / 16); t += blockDim.x) {
+      const int h = t / (HS / 16), c = t - h * (HS / 16);
+      cp_async16(hs + h * HS + c * 16, a.U32 + (int64_t)hl[4 + h] * (2 * NVP) + c * 4);
+    }
+  };
+  // a timed-out wait on phase `parity` of stage s: report it, give that copy (and, with `also`,
+  // the first copy into stage 1) a second bounded wait, let this thread's small copies land
+  auto give_up = [&](int s, uint32_t parity, bool also) {
+    if (threadIdx.x == 0) {
+      atomicOr(a.err, kErrTimeout);
+      mbar_wait(&bar[s], parity, kStageWaitNs);
+      if (also) mbar_wait(&bar[1], 0, kStageWaitNs);
+    }
+    cp_async_wait<0>();
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  if constexpr (D == 3) {
+    const DevTables &tb = *a.tab;
+    for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
+      const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
+      sPhi[t] = (T)tb.Phi[f][p][q][k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if ((int64_t)blockIdx.x < tiles) issue(blockIdx.x, 0);
+    if ((int64_t)blockIdx.x + gridDim.x < tiles) issue((int64_t)blockIdx.x + gridDim.x, 1);
+  }
+  if (a.dt_swap && blockIdx.x == 0)
+    for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {
+      a.dt[t] = a.dt[a.nmesh + t];
+      a.dt[a.nmesh + t] = 1e300;
+    }
+  // member states of the first tile
+  if ((int64_t)blockIdx.x < tiles) {
+    const bool ok = mbar_wait(&bar[0], 0, kStageWaitNs);
+    if (__syncthreads_or(!ok)) {
+      give_up(0, 0, (int64_t)blockIdx.x + gridDim.x < tiles);
+      return;
+    }
+    gather(0);
+  }
+  cp_async_commit();
+
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+    const int s = it & 1;
+    const int64_t next = tile + gridDim.x;
+    // records of the next tile, then its member states (in flight during this tile's work)
+    bool ok = true;
+    if (next < tiles) ok = mbar_wait(&bar[s ^ 1], ((it + 1) >> 1) & 1, kStageWaitNs);
+    if (__syncthreads_or(!ok)) {
+      give_up(s ^ 1, ((it + 1) >> 1) & 1, false);
+      return;
+    }
+    if (next < tiles) gather(s ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();  // this thread's copies of the current tile's states
+    __syncthreads();     // everyone's
+    const int64_t c0 = tile * C;
+    const int nvalid = (int)min((int64_t)C, N - c0);
+    const int lane = threadIdx.x & 31, grp = lane / NV;
+    const int slot = (int)(threadIdx.x >> 5) * CPW + grp;
+    const bool active = grp < CPW && slot < nvalid;
+    const int ls = active ? slot : nvalid - 1;  // spare lanes shadow a valid cell of the tile
+    unsigned char *b = base(s);
+    recon_lane<D, R, T, SCHEME, true, true>(a, c0 + ls, active, lane - grp * NV, grp * NV,
+                                            reinterpret_cast<const T *>(b) + ls * (M * NK),
+                                            reinterpret_cast<const T *>(b + o_pd) + ls * (NF * PDS),
+                                            b + o_li + (size_t)ls * LI, sPhi,
+                                            reinterpret_cast<const float *>(b + o_hs));
+    __syncthreads();  // stage s is free again
+    if (threadIdx.x == 0 && tile + 2 * (int64_t)gridDim.x < tiles) {
+      fence_proxy_async_shared();
+      issue(tile + 2 * (int64_t)gridDim.x, s);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <int D, int R, int SCHEME>
+void launch_recon_halo(const KArgs &a, cudaStream_t s) {
+  const int threads = kHaloWarps * 32, C = halo_tile(D);
+  const size_t smem = (size_t)recon_halo_smem(D, R, a.hrec);
+  auto kern = recon_halo_kernel<D, R, SCHEME>;
+  static int resident = 0, sms = 0, for_hrec = -1;
+  if (for_hrec != a.hrec) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStagedSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, threads, smem);
+    if (resident < 1) resident = 1;  // a launch that cannot fit fails loudly below
+    for_hrec = a.hrec;
+  }
+  const int64_t tiles = (a.N + C - 1) / C;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)resident * sms);
+  kern<<<grid, threads, smem, s>>>(a);
 }
 
 // Host side: persistent launch of the staged kernel, grid = (co-resident blocks per SM) x SMs.

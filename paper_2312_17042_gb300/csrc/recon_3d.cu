@@ -4,6 +4,14 @@
 namespace cteno {
 
 void launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s) {
+  if (block == kHaloLanes) {  // gather-staged lane schedule (mixed path)
+    if (!fp32) return;
+    if (degree == 2 && scheme == 0) launch_recon_halo<3, 2, 0>(a, s);
+    if (degree == 2 && scheme == 1) launch_recon_halo<3, 2, 1>(a, s);
+    if (degree == 3 && scheme == 0) launch_recon_halo<3, 3, 0>(a, s);
+    if (degree == 3 && scheme == 1) launch_recon_halo<3, 3, 1>(a, s);
+    return;
+  }
   if (block >= kStagedCells) {  // staged persistent schedules (mixed path; the launch value is
                                 // validated by the caller)
     const bool lanes = block >= kStagedLanes;
