@@ -117,6 +117,12 @@ def dist_env():
     return rank, world, local
 
 
+def whole_job_value(world: int, cells_per_rank: int, steps: int, max_ms: float) -> float:
+    """Mcell-RK-stage/s of the whole job: every rank advances its own replica of `cells_per_rank`
+    cells through `steps` SSP-RK3 steps (3 stages each); the time is the maximum over ranks."""
+    return world * cells_per_rank * 3 * steps / (max_ms * 1e-3) / 1e6
+
+
 class Dist:
     def __init__(self, world, backend):
         self.world = world
@@ -216,8 +222,8 @@ def alu_peak(native):
 def recon_kernel_name(dim, degree, scheme, launch):
     """Name of the mixed-path reconstruction kernel a launch value selects."""
     args = f"{dim},{degree},float,{SCHEMES[scheme]}"
-    if launch == 4096:
-        return f"recon_halo_kernel<{args}> x128"
+    if launch in (4096, 4097):
+        return f"recon_halo_kernel<{args},{'one-tile' if launch == 4097 else 'persistent'}> x128"
     if launch >= 3072:
         return f"recon_staged_kernel<{args},lanes> x{launch - 3072}"
     if launch >= 2048:
@@ -311,12 +317,12 @@ def run_ours(args, rank, world, local):
     guard = s.sync()
     total_ms = dist.max(sum(ms), device="cuda")
     ms_per_step = total_ms / args.steps
-    value = world * ncells * 3 * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_value(world, ncells, args.steps, total_ms)
     recon_ms_launch = float(kms[:, 0].mean()) / 3.0
     flux_ms_launch = float(kms[:, 1].mean()) / 3.0
     peaks, peak_kind = measured_peaks()
     achieved = stats[0] / (recon_ms_launch * 1e-3) / 1e9
-    hv = f"{args.workload}:" + variant_name(**h)
+    hv = f"{args.workload}:" + variant_name(**h) + f":{blocks[0]}"
     roofline = {"kernel": recon_kernel_name(case.dim, h["degree"], h["scheme"], blocks[0]), "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(hv),
@@ -349,7 +355,7 @@ def run_ours(args, rank, world, local):
         if it >= 2:
             t_total += a.elapsed_time(b_)
     t_total = dist.max(t_total, device="cuda")
-    e2e = {"value": round(world * ncells * 3 * n_e2e / (t_total * 1e-3) / 1e6, 2), "unit": UNIT,
+    e2e = {"value": round(whole_job_value(world, ncells, n_e2e, t_total), 2), "unit": UNIT,
            "h2d_bytes_per_step": int(sum(p.nbytes for p in pinned)),
            "d2h_bytes_per_step": int(sum(o.nbytes for o in outs)), "steps": n_e2e,
            "api": "cteno_set_state(host) + cteno_run(1) + cteno_get_state(host), pinned buffers"}
@@ -370,7 +376,7 @@ def run_ours(args, rank, world, local):
                 vms, vk = time_steps(native, sv, args.variant_steps, 3, flush, torch, kernel_times=True)
                 tot = dist.max(sum(vms), device="cuda")
                 r_ms = float(vk[:, 0].mean()) / 3
-                entry = {"value": round(world * ncells * 3 * args.variant_steps / (tot * 1e-3) / 1e6, 2),
+                entry = {"value": round(whole_job_value(world, ncells, args.variant_steps, tot), 2),
                          "ms_per_step": round(tot / args.variant_steps, 4),
                          "recon_ms_per_launch": round(r_ms, 5),
                          "flux_ms_per_launch": round(float(vk[:, 1].mean()) / 3, 5)}

@@ -180,7 +180,8 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
  * such a copy ever gives up (after 1 s), the kernel stops and the next synchronising call returns
  * CTENO_ERR_DEVICE. 4096 (mixed path) selects that lane schedule with 4 warps whose tiles also copy
  * the states of their distinct stencil members into shared memory (lists built by cteno_lsq_build);
- * refused like the staged values when it does not fit. */
+ * 4097 the same with one tile per block and a single stage (half the shared memory); both refused
+ * like the staged values when they do not fit. */
 int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block);
 
 /* Time the candidate launch configurations (block sizes 64/128/256, on the mixed path the

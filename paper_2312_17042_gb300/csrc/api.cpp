@@ -700,8 +700,9 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
   // variant (mixed path only, at most 128 threads)
   auto ok = [&](int b, bool recon) {
     if (b == 0) return true;
-    if (b == kHaloLanes)  // gather-staged schedule: reconstruction, mixed path, lists built, fits
-      return recon && ctx->fp32 && ctx->hl && recon_halo_smem(ctx->d, ctx->p.degree, ctx->hrec) <= kMaxStagedSmem;
+    if (b == kHaloLanes || b == kHaloLanes + 1)  // gather-staged: reconstruction, mixed, lists built, fits
+      return recon && ctx->fp32 && ctx->hl &&
+             recon_halo_smem(ctx->d, ctx->p.degree, ctx->hrec) / (b == kHaloLanes ? 1 : 2) <= kMaxStagedSmem;
     if (b >= kStagedCells) {  // staged schedules: reconstruction, mixed path, two stages that fit
       const int t = b - (b >= kStagedLanes ? kStagedLanes : kStagedCells);
       return recon && ctx->fp32 && b < kStagedLanes + 1024 && t >= 32 && t <= 256 && t % 32 == 0 &&
@@ -763,8 +764,11 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
     for (int b : {kStagedCells + 32, kStagedCells + 64, kStagedCells + 128, kStagedLanes + 64,
                   kStagedLanes + 128, kStagedLanes + 256})
       if (recon_staged_smem(ctx->d, ctx->p.degree, 1, b) <= kMaxStagedSmem) rcand.push_back(b);
-  if (ctx->fp32 && ctx->hl && recon_halo_smem(ctx->d, ctx->p.degree, ctx->hrec) <= kMaxStagedSmem)
-    rcand.push_back(kHaloLanes);
+  if (ctx->fp32 && ctx->hl) {
+    const long long hs = recon_halo_smem(ctx->d, ctx->p.degree, ctx->hrec);
+    if (hs <= kMaxStagedSmem) rcand.push_back(kHaloLanes);
+    if (hs / 2 <= kMaxStagedSmem) rcand.push_back(kHaloLanes + 1);
+  }
   const int reps = 5;
   float best_r = 1e30f, best_f = 1e30f;
   int br = ctx->recon_block, bf = ctx->flux_block;

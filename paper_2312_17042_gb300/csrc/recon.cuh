@@ -897,7 +897,10 @@ __global__ void __launch_bounds__(256) recon_staged_kernel(const KArgs a) {
 // the computation; the cells' stencil ids are then 16-bit indices into that list, so every gather
 // of the reconstruction is a shared-memory read and each member state crosses L2 once per tile.
 // ---------------------------------------------------------------------------------------------
-template <int D, int R, int SCHEME>
+// ONE: one tile per block and a single stage (grid = tiles): half the shared memory, so twice the
+// resident blocks hide each other's copy latency (small meshes, where a persistent block would
+// see only a few tiles, and 3D degree 3, whose two stages do not fit).
+template <int D, int R, int SCHEME, bool ONE>
 __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs a) {
   using T = float;
   using S = Shape<D, R>;
@@ -949,9 +952,25 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
     cp_async_wait<0>();
   };
 
+  // the reconstruction of the cells of `tile` from stage s (records and member states landed)
+  auto work = [&](int64_t tile, int s) {
+    const int64_t c0 = tile * C;
+    const int nvalid = (int)min((int64_t)C, N - c0);
+    const int lane = threadIdx.x & 31, grp = lane / NV;
+    const int slot = (int)(threadIdx.x >> 5) * CPW + grp;
+    const bool active = grp < CPW && slot < nvalid;
+    const int ls = active ? slot : nvalid - 1;  // spare lanes shadow a valid cell of the tile
+    unsigned char *b = base(s);
+    recon_lane<D, R, T, SCHEME, true, true>(a, c0 + ls, active, lane - grp * NV, grp * NV,
+                                            reinterpret_cast<const T *>(b) + ls * (M * NK),
+                                            reinterpret_cast<const T *>(b + o_pd) + ls * (NF * PDS),
+                                            b + o_li + (size_t)ls * LI, sPhi,
+                                            reinterpret_cast<const float *>(b + o_hs));
+  };
+
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    if (!ONE) mbar_init(&bar[1], 1);
     fence_barrier_init();
   }
   if constexpr (D == 3) {
@@ -964,13 +983,26 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
   __syncthreads();
   if (threadIdx.x == 0) {
     if ((int64_t)blockIdx.x < tiles) issue(blockIdx.x, 0);
-    if ((int64_t)blockIdx.x + gridDim.x < tiles) issue((int64_t)blockIdx.x + gridDim.x, 1);
+    if (!ONE && (int64_t)blockIdx.x + gridDim.x < tiles) issue((int64_t)blockIdx.x + gridDim.x, 1);
   }
   if (a.dt_swap && blockIdx.x == 0)
     for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {
       a.dt[t] = a.dt[a.nmesh + t];
       a.dt[a.nmesh + t] = 1e300;
     }
+  if constexpr (ONE) {  // grid = tiles: this block's tile only
+    const bool ok = mbar_wait(&bar[0], 0, kStageWaitNs);
+    if (__syncthreads_or(!ok)) {
+      give_up(0, 0, false);
+      return;
+    }
+    gather(0);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    work(blockIdx.x, 0);
+    return;
+  }
   // member states of the first tile
   if ((int64_t)blockIdx.x < tiles) {
     const bool ok = mbar_wait(&bar[0], 0, kStageWaitNs);
@@ -997,18 +1029,7 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
     cp_async_commit();
     cp_async_wait<1>();  // this thread's copies of the current tile's states
     __syncthreads();     // everyone's
-    const int64_t c0 = tile * C;
-    const int nvalid = (int)min((int64_t)C, N - c0);
-    const int lane = threadIdx.x & 31, grp = lane / NV;
-    const int slot = (int)(threadIdx.x >> 5) * CPW + grp;
-    const bool active = grp < CPW && slot < nvalid;
-    const int ls = active ? slot : nvalid - 1;  // spare lanes shadow a valid cell of the tile
-    unsigned char *b = base(s);
-    recon_lane<D, R, T, SCHEME, true, true>(a, c0 + ls, active, lane - grp * NV, grp * NV,
-                                            reinterpret_cast<const T *>(b) + ls * (M * NK),
-                                            reinterpret_cast<const T *>(b + o_pd) + ls * (NF * PDS),
-                                            b + o_li + (size_t)ls * LI, sPhi,
-                                            reinterpret_cast<const float *>(b + o_hs));
+    work(tile, s);
     __syncthreads();  // stage s is free again
     if (threadIdx.x == 0 && tile + 2 * (int64_t)gridDim.x < tiles) {
       fence_proxy_async_shared();
@@ -1018,11 +1039,11 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
   cp_async_wait<0>();
 }
 
-template <int D, int R, int SCHEME>
+template <int D, int R, int SCHEME, bool ONE>
 void launch_recon_halo(const KArgs &a, cudaStream_t s) {
   const int threads = kHaloWarps * 32, C = halo_tile(D);
-  const size_t smem = (size_t)recon_halo_smem(D, R, a.hrec);
-  auto kern = recon_halo_kernel<D, R, SCHEME>;
+  const size_t smem = (size_t)recon_halo_smem(D, R, a.hrec) / (ONE ? 2 : 1);
+  auto kern = recon_halo_kernel<D, R, SCHEME, ONE>;
   static int resident = 0, sms = 0, for_hrec = -1;
   if (for_hrec != a.hrec) {
     int dev = 0;
@@ -1034,7 +1055,7 @@ void launch_recon_halo(const KArgs &a, cudaStream_t s) {
     for_hrec = a.hrec;
   }
   const int64_t tiles = (a.N + C - 1) / C;
-  const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)resident * sms);
+  const unsigned grid = ONE ? (unsigned)tiles : (unsigned)std::min<int64_t>(tiles, (int64_t)resident * sms);
   kern<<<grid, threads, smem, s>>>(a);
 }
 

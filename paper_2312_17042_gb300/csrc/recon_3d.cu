@@ -4,12 +4,16 @@
 namespace cteno {
 
 void launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s) {
-  if (block == kHaloLanes) {  // gather-staged lane schedule (mixed path)
+  if (block == kHaloLanes || block == kHaloLanes + 1) {  // gather-staged lane schedule (mixed)
     if (!fp32) return;
-    if (degree == 2 && scheme == 0) launch_recon_halo<3, 2, 0>(a, s);
-    if (degree == 2 && scheme == 1) launch_recon_halo<3, 2, 1>(a, s);
-    if (degree == 3 && scheme == 0) launch_recon_halo<3, 3, 0>(a, s);
-    if (degree == 3 && scheme == 1) launch_recon_halo<3, 3, 1>(a, s);
+    const bool one = block == kHaloLanes + 1;  // one tile per block, single stage
+#define CTENO_HALO(R, SC) \
+  (one ? launch_recon_halo<3, R, SC, true>(a, s) : launch_recon_halo<3, R, SC, false>(a, s))
+    if (degree == 2 && scheme == 0) CTENO_HALO(2, 0);
+    if (degree == 2 && scheme == 1) CTENO_HALO(2, 1);
+    if (degree == 3 && scheme == 0) CTENO_HALO(3, 0);
+    if (degree == 3 && scheme == 1) CTENO_HALO(3, 1);
+#undef CTENO_HALO
     return;
   }
   if (block >= kStagedCells) {  // staged persistent schedules (mixed path; the launch value is

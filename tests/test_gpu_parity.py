@@ -204,10 +204,10 @@ STAGED_SMEM_MAX = 200 * 1024
 
 @pytest.mark.parametrize("launch", [(128, 128), (-128, -128), (1024 + 128, 1024 + 256), (1024 + 256, 256),
                                     (2048 + 32, 128), (2048 + 64, -128), (3072 + 64, 1024 + 128),
-                                    (3072 + 128, 256), (3072 + 256, 128), (4096, 128)],
+                                    (3072 + 128, 256), (3072 + 256, 128), (4096, 128), (4097, -128)],
                          ids=["cell-thread", "capped", "var-lanes-128", "var-lanes-256", "staged-cells-32",
                               "staged-cells-64", "staged-lanes-64", "staged-lanes-128", "staged-lanes-256",
-                              "gather-staged"])
+                              "gather-staged", "gather-staged-one-tile"])
 def test_mixed_schedules_agree(launch):
     """Every launch schedule of the mixed path gives the same face states and update on a 2D and a
     3D mesh (the arithmetic per variable is the same in each schedule). A staged schedule whose two
@@ -368,8 +368,9 @@ def test_full_size_shock_tube_sampled_residual():
         s.close()
 
 
-@pytest.mark.parametrize("launch", [None, (2048 + 64, 0), (3072 + 128, 0), (4096, 0)],
-                         ids=["autotuned", "staged-cells-64", "staged-lanes-128", "gather-staged"])
+@pytest.mark.parametrize("launch", [None, (2048 + 64, 0), (3072 + 128, 0), (4096, 0), (4097, 0)],
+                         ids=["autotuned", "staged-cells-64", "staged-lanes-128", "gather-staged",
+                              "gather-staged-one-tile"])
 def test_full_size_shock_tube_mixed_sampled_residual(launch):
     """The benchmark's workload and precision: 512x128 shock tube, mixed path, CTENO degree 2, in
     the autotuned launch configuration (and with each staged schedule forced). One stage against
