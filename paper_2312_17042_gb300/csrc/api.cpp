@@ -1,5 +1,6 @@
 // api.cpp -- the C ABI of include/cteno.h: context, device memory, set-up and the time loop.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -133,7 +134,7 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   }
   a.gamma32 = (float)ctx->p.gamma;
   a.gm1_32 = (float)(ctx->p.gamma - 1.0);
-  a.eps32 = std::max((float)ctx->p.eps, 1e-40f);
+  a.eps32 = std::max((float)ctx->p.eps, FLT_MIN);  // FP32 eps: at least the smallest normal number
   a.C_T32 = (float)ctx->p.C_T;
   a.inv_lam1_32 = (float)a.inv_lam1;
   a.one_m_lam1_32 = (float)a.one_m_lam1;

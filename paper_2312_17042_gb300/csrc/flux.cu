@@ -13,13 +13,15 @@ namespace cteno {
 namespace {
 
 // Reciprocal, quotient and square root: IEEE operations on the FP64 path; on the mixed path the
-// GPU's single-instruction approximations (relative error about 2^-23). Both cells of a face run
-// the same instruction sequence on the same operands, so their face values stay bit-identical.
+// GPU's single-instruction approximations (relative error about 2^-23, subnormal operands flushed
+// to zero: densities, pressures and wave-speed differences of physical states are normal numbers).
+// Both cells of a face run the same instruction sequence on the same operands, so their face
+// values stay bit-identical.
 template <typename T>
 __device__ __forceinline__ T rcp_(T x) {
   if constexpr (sizeof(T) == 4) {
     float y;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
   } else {
     return 1.0 / x;
@@ -34,7 +36,7 @@ template <typename T>
 __device__ __forceinline__ T sqrt_(T x) {
   if constexpr (sizeof(T) == 4) {
     float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
   } else {
     return sqrt(x);

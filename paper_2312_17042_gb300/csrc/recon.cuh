@@ -138,15 +138,16 @@ __device__ __forceinline__ uint32_t select_fp64(double SI0, const double *SId, u
 }
 
 // Base-2 logarithm and power with the GPU's single-instruction approximations (relative error
-// about 2^-22; subnormal inputs are kept, so eps = 1e-40 stays distinct from zero).
+// about 2^-22, subnormals flushed to zero). The FP32 eps is at least the smallest normal number,
+// so SI + eps is normal; a power below it contributes nothing to a decision against C_T.
 __device__ __forceinline__ float lg2_approx(float x) {
   float y;
-  asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
-  asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
