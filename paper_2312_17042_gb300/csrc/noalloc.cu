@@ -16,7 +16,7 @@ namespace {
 // Staging area: 2^21 doubles (16 MiB). Every GPU that loads the library keeps this array for the
 // life of the process.
 constexpr int64_t kStageValues = int64_t(1) << 21;
-__device__ __align__(256) double g_noalloc_stage[kStageValues];
+static __device__ __align__(256) double g_noalloc_stage[kStageValues];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_lock;
