@@ -223,6 +223,29 @@ __device__ __forceinline__ void load16(const T *__restrict__ src, T *dst) {
   }
 }
 #ifdef __CUDACC__
+// Streamed operator records (read once per cell): 16-byte read-only global loads that do not
+// allocate in L1 (kept for the reused neighbour means) and ask L2 for 256-byte blocks (the next
+// chunks of the same record arrive with the first miss).
+template <typename T, int COUNT>
+__device__ __forceinline__ void load16_stream(const T *__restrict__ src, T *dst) {
+  static_assert(COUNT % (16 / sizeof(T)) == 0, "record not a multiple of 16 bytes");
+#pragma unroll
+  for (int c = 0; c < COUNT * (int)sizeof(T) / 16; ++c) {
+    if constexpr (sizeof(T) == 4) {
+      float4 x;
+      asm("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
+          : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w)
+          : "l"(reinterpret_cast<const float4 *>(src) + c));
+      dst[4 * c] = x.x; dst[4 * c + 1] = x.y; dst[4 * c + 2] = x.z; dst[4 * c + 3] = x.w;
+    } else {
+      double2 x;
+      asm("ld.global.nc.L1::no_allocate.L2::256B.v2.f64 {%0, %1}, [%2];"
+          : "=d"(x.x), "=d"(x.y)
+          : "l"(reinterpret_cast<const double2 *>(src) + c));
+      dst[2 * c] = x.x; dst[2 * c + 1] = x.y;
+    }
+  }
+}
 template <bool SH>
 __device__ __forceinline__ int4 load_i4(const int32_t *__restrict__ src) {
   if constexpr (SH) return *reinterpret_cast<const int4 *>(src);

@@ -276,7 +276,10 @@ __device__ __forceinline__ void recon_cell(const KArgs &a, const int64_t i, cons
 #pragma unroll
     for (int e = 0; e < M * NK; ++e) {
       const int m = e / NK, k = e % NK;
-      if (e % CH == 0) load16<T, CH, SH>(Pci + e, pb);
+      if (e % CH == 0) {
+        if constexpr (SH) load16<T, CH, true>(Pci + e, pb);
+        else load16_stream<T, CH>(Pci + e, pb);
+      }
       if (k == 0) {
         if (m % 4 == 0) {
           const int4 t4 = load_i4<SH>(sti + m);
@@ -306,7 +309,8 @@ __device__ __forceinline__ void recon_cell(const KArgs &a, const int64_t i, cons
       const int nm = (info >> (4 * f)) & 15u;
       if ((adm >> f) & 1u) {
         T pf[PDS];
-        load16<T, PDS, SH>(Pdi + f * PDS, pf);
+        if constexpr (SH) load16<T, PDS, true>(Pdi + f * PDS, pf);
+        else load16_stream<T, PDS>(Pdi + f * PDS, pf);
 #pragma unroll
         for (int jj = 0; jj < ND; ++jj) {
           if (jj < nm) {
@@ -563,7 +567,10 @@ __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, cons
 #pragma unroll
     for (int e = 0; e < M * NK; ++e) {
       const int m = e / NK, k = e % NK;
-      if (e % CH == 0) load16<T, CH, SH>(Pci + e, pb);
+      if (e % CH == 0) {
+        if constexpr (SH) load16<T, CH, true>(Pci + e, pb);
+        else load16_stream<T, CH>(Pci + e, pb);
+      }
       if (k == 0) {
         if (m % IDV == 0) {
           if constexpr (HALO) {
@@ -599,7 +606,8 @@ __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, cons
       const int nm = (info >> (4 * f)) & 15u;
       if ((adm >> f) & 1u) {
         T pf[PDS];
-        load16<T, PDS, SH>(Pdi + f * PDS, pf);
+        if constexpr (SH) load16<T, PDS, true>(Pdi + f * PDS, pf);
+        else load16_stream<T, PDS>(Pdi + f * PDS, pf);
 #pragma unroll
         for (int jj = 0; jj < ND; ++jj) {
           if (jj < nm) {
