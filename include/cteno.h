@@ -106,8 +106,14 @@ int cteno_stencil_build(cteno_ctx *ctx);
 int cteno_lsq_build(cteno_ctx *ctx);
 
 /* Set the conserved cell means of one mesh: U[v][c] (layout above), host or device pointer
- * (is_device = 0 / 1). Also computes the CFL time step of the new state for cteno_run. */
+ * (is_device = 0 / 1). Also computes that mesh's CFL time step of the new state for cteno_run. */
 int cteno_set_state(cteno_ctx *ctx, int32_t mesh_id, const double *U, int is_device);
+
+/* Set the conserved cell means of every mesh at once (one copy and one launch for the batch):
+ * U holds mesh after mesh, in the order the meshes were added, each mesh's block laid out as
+ * for cteno_set_state (nv * ncells values, [v][c] in its own numbering); nv * (total cells)
+ * doubles, host or device. Also computes every mesh's CFL time step. */
+int cteno_set_state_all(cteno_ctx *ctx, const double *U, int is_device);
 
 /* One stage (stage = 0, 1, 2) of the SSP-RK3 step, for every mesh, with the time step dt[mesh]
  * (host array of length nmeshes). Stage 0 stores U^n. */
@@ -120,6 +126,10 @@ int cteno_run(cteno_ctx *ctx, int nsteps);
 
 /* Read the conserved cell means of one mesh into U_out[v][c] (host or device). */
 int cteno_get_state(cteno_ctx *ctx, int32_t mesh_id, double *U_out, int is_device);
+
+/* Read the conserved cell means of every mesh at once into U_out (host or device), laid out as
+ * for cteno_set_state_all. A host read synchronises the stream once for the whole batch. */
+int cteno_get_state_all(cteno_ctx *ctx, double *U_out, int is_device);
 
 /* Like cteno_get_state with a host output, but allocating nothing. The paper has no counterpart;
  * this is for callers that cannot allocate device memory at the time they read a state back --

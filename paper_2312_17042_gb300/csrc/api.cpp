@@ -43,6 +43,7 @@ struct cteno_ctx {
   int *derr = nullptr;
   unsigned long long *guard = nullptr;
   std::vector<int32_t *> d_rank;
+  int32_t *d_grank = nullptr;        // device cell of each concatenated original cell (all meshes)
   double *stage_buf = nullptr;       // staging for host <-> device state copies
   size_t stage_cap = 0;
   double *backup = nullptr;          // autotune state backup
@@ -440,11 +441,16 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   CK(dalloc(ctx, &ctx->derr, sizeof(int)));
   CK(dalloc(ctx, &ctx->guard, sizeof(unsigned long long)));
   ctx->d_rank.resize(nmesh);
+  std::vector<int32_t> hgrank(N);
   for (int k = 0; k < nmesh; ++k) {
-    CK(dalloc(ctx, &ctx->d_rank[k], sizeof(int32_t) * ctx->meshes[k].ncells));
-    CK(cudaMemcpyAsync(ctx->d_rank[k], ctx->meshes[k].rank.data(),
-                       sizeof(int32_t) * ctx->meshes[k].ncells, cudaMemcpyHostToDevice, ctx->stream));
+    const Mesh &mk = ctx->meshes[k];
+    CK(dalloc(ctx, &ctx->d_rank[k], sizeof(int32_t) * mk.ncells));
+    CK(cudaMemcpyAsync(ctx->d_rank[k], mk.rank.data(), sizeof(int32_t) * mk.ncells, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    for (int64_t c = 0; c < mk.ncells; ++c) hgrank[mk.offset + c] = (int32_t)(mk.offset + mk.rank[c]);
   }
+  CK(dalloc(ctx, &ctx->d_grank, sizeof(int32_t) * N));
+  CK(cudaMemcpyAsync(ctx->d_grank, hgrank.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, ctx->stream));
   DevTables dt{};
   dt.nk = tab.nk;
   dt.nq = tab.nq;
@@ -531,9 +537,46 @@ int cteno_set_state(cteno_ctx *ctx, int32_t mesh_id, const double *U, int is_dev
   launch_permute_in(ctx->nv, lay_nvp(ctx->d), m.ncells, m.offset, ctx->d_rank[mesh_id], src, ctx->U,
                     ctx->U32, ctx->stream);
   KArgs a = make_args(ctx, 0, 0);
-  launch_dt(ctx->d, a, ctx->stream);
+  launch_dt_mesh(ctx->d, a, mesh_id, m.offset, m.ncells, ctx->stream);  // this mesh's CFL step only
   CK(cudaGetLastError());
   return CTENO_OK;
+}
+
+int cteno_set_state_all(cteno_ctx *ctx, const double *U, int is_device) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (!U) return fail(ctx, CTENO_ERR_ARG, "null state");
+  const size_t cnt = (size_t)ctx->nv * ctx->N;
+  const double *src = U;
+  if (!is_device) {
+    if ((rc = ensure_stage_buf(ctx, cnt))) return rc;
+    CK(cudaMemcpyAsync(ctx->stage_buf, U, cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    src = ctx->stage_buf;
+  }
+  launch_permute_in_all(ctx->nv, lay_nvp(ctx->d), ctx->N, (int)ctx->meshes.size(), ctx->d_mesh_off,
+                        ctx->d_grank, src, ctx->U, ctx->U32, ctx->stream);
+  launch_dt(ctx->d, make_args(ctx, 0, 0), ctx->stream);
+  CK(cudaGetLastError());
+  return CTENO_OK;
+}
+
+int cteno_get_state_all(cteno_ctx *ctx, double *U_out, int is_device) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (!U_out) return fail(ctx, CTENO_ERR_ARG, "null output");
+  const size_t cnt = (size_t)ctx->nv * ctx->N;
+  const int nmesh = (int)ctx->meshes.size();
+  if (is_device) {
+    launch_permute_out_all(ctx->nv, lay_nvp(ctx->d), ctx->N, nmesh, ctx->d_mesh_off, ctx->d_grank, ctx->U,
+                           U_out, ctx->stream);
+    CK(cudaGetLastError());
+    return CTENO_OK;
+  }
+  if ((rc = ensure_stage_buf(ctx, cnt))) return rc;
+  launch_permute_out_all(ctx->nv, lay_nvp(ctx->d), ctx->N, nmesh, ctx->d_mesh_off, ctx->d_grank, ctx->U,
+                         ctx->stage_buf, ctx->stream);
+  CK(cudaMemcpyAsync(U_out, ctx->stage_buf, cnt * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return device_status(ctx);
 }
 
 int cteno_rk_stage(cteno_ctx *ctx, int stage, const double *dt) {

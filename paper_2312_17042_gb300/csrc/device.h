@@ -180,6 +180,14 @@ inline void launch_recon(int dim, int degree, int fp32, int scheme, const KArgs 
 void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s);
 void launch_dt(int dim, const KArgs &a, cudaStream_t s);
 void launch_dt_reset(const KArgs &a, cudaStream_t s);
+// CFL step of one mesh only (device cells [first, first + count)).
+void launch_dt_mesh(int dim, const KArgs &a, int mesh, int64_t first, int64_t count, cudaStream_t s);
+// All meshes in one launch: host-side order is mesh after mesh, [v][cell] per mesh in the mesh's
+// original numbering; grank[c] is the device cell of concatenated original cell c.
+void launch_permute_in_all(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
+                           const int32_t *grank, const double *src, double *U, float *U32, cudaStream_t s);
+void launch_permute_out_all(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
+                            const int32_t *grank, const double *U, double *dst, cudaStream_t s);
 void launch_permute_in(int nv, int nvp, int64_t n, int64_t off, const int32_t *rank,
                        const double *src, double *U, float *U32, cudaStream_t s);
 void launch_permute_out(int nv, int nvp, int64_t n, int64_t off, const int32_t *rank,

@@ -376,12 +376,13 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
 namespace cteno {
 namespace {
 
+// CFL step of cells [first, first + count) (all cells, or the cells of one mesh).
 template <int D, typename T>
-__global__ void dt_kernel(const KArgs a) {
+__global__ void dt_kernel(const KArgs a, int64_t first, int64_t count) {
   constexpr int NVP = Lay<D>::NVP;
-  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = cell < a.N;
-  const int64_t i = active ? cell : a.N - 1;  // every lane reaches the reduction
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = idx < count;
+  const int64_t i = first + (active ? idx : count - 1);  // every lane reaches the reduction
   double u[NVP];
 #pragma unroll
   for (int v = 0; v < NVP; ++v) u[v] = a.U[i * NVP + v];
@@ -395,6 +396,47 @@ __global__ void dt_kernel(const KArgs a) {
 __global__ void dt_reset_kernel(double *dt, int nmesh) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nmesh) dt[nmesh + i] = 1e300;
+}
+
+__global__ void dt_reset_one_kernel(double *dt, int nmesh, int mesh) { dt[nmesh + mesh] = 1e300; }
+
+// All meshes at once: the source holds mesh after mesh, each mesh's values as [v][cell] in its
+// original numbering; grank maps the concatenated original cell to its device cell.
+__device__ __forceinline__ int mesh_of_offsets(const int64_t *off, int nmesh, int64_t c) {
+  int lo = 0, hi = nmesh - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void permute_in_all_kernel(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
+                                      const int32_t *grank, const double *src, double *U, float *U32) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  const int k = mesh_of_offsets(mesh_off, nmesh, c);
+  const int64_t off = mesh_off[k], n = mesh_off[k + 1] - off, local = c - off;
+  const int64_t g = grank[c];
+  for (int v = 0; v < nvp; ++v) {
+    const double x = (v < nv) ? src[nv * off + v * n + local] : 0.0;
+    U[g * nvp + v] = x;
+    if (U32) {
+      const float2 s = f64_split(x);
+      U32[(g * nvp + v) * 2] = s.x;
+      U32[(g * nvp + v) * 2 + 1] = s.y;
+    }
+  }
+}
+
+__global__ void permute_out_all_kernel(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
+                                       const int32_t *grank, const double *U, double *dst) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  const int k = mesh_of_offsets(mesh_off, nmesh, c);
+  const int64_t off = mesh_off[k], n = mesh_off[k + 1] - off, local = c - off;
+  const int64_t g = grank[c];
+  for (int v = 0; v < nv; ++v) dst[nv * off + v * n + local] = U[g * nvp + v];
 }
 
 // src[v][c] (caller order, mesh of n cells) -> U[off + rank[c]][v] (+ the FP32 pair)
@@ -452,13 +494,35 @@ void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s) {
   if (dim == 3 && !fp32) flux_kernel<3, double, 0><<<grid, block, 0, s>>>(a);
 }
 
+namespace {
+void launch_dt_cells(int dim, const KArgs &a, int64_t first, int64_t count, cudaStream_t s) {
+  const bool f32 = a.geo32 != nullptr;
+  const unsigned g = grid_for(count, 256);
+  if (dim == 2 && f32) dt_kernel<2, float><<<g, 256, 0, s>>>(a, first, count);
+  if (dim == 2 && !f32) dt_kernel<2, double><<<g, 256, 0, s>>>(a, first, count);
+  if (dim == 3 && f32) dt_kernel<3, float><<<g, 256, 0, s>>>(a, first, count);
+  if (dim == 3 && !f32) dt_kernel<3, double><<<g, 256, 0, s>>>(a, first, count);
+}
+}  // namespace
+
 void launch_dt(int dim, const KArgs &a, cudaStream_t s) {
   dt_reset_kernel<<<grid_for(a.nmesh, 64), 64, 0, s>>>(a.dt, a.nmesh);
-  const bool f32 = a.geo32 != nullptr;
-  if (dim == 2 && f32) dt_kernel<2, float><<<grid_for(a.N, 256), 256, 0, s>>>(a);
-  if (dim == 2 && !f32) dt_kernel<2, double><<<grid_for(a.N, 256), 256, 0, s>>>(a);
-  if (dim == 3 && f32) dt_kernel<3, float><<<grid_for(a.N, 256), 256, 0, s>>>(a);
-  if (dim == 3 && !f32) dt_kernel<3, double><<<grid_for(a.N, 256), 256, 0, s>>>(a);
+  launch_dt_cells(dim, a, 0, a.N, s);
+}
+
+void launch_dt_mesh(int dim, const KArgs &a, int mesh, int64_t first, int64_t count, cudaStream_t s) {
+  dt_reset_one_kernel<<<1, 1, 0, s>>>(a.dt, a.nmesh, mesh);
+  launch_dt_cells(dim, a, first, count, s);
+}
+
+void launch_permute_in_all(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
+                           const int32_t *grank, const double *src, double *U, float *U32, cudaStream_t s) {
+  permute_in_all_kernel<<<grid_for(N, 256), 256, 0, s>>>(nv, nvp, N, nmesh, mesh_off, grank, src, U, U32);
+}
+
+void launch_permute_out_all(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
+                            const int32_t *grank, const double *U, double *dst, cudaStream_t s) {
+  permute_out_all_kernel<<<grid_for(N, 256), 256, 0, s>>>(nv, nvp, N, nmesh, mesh_off, grank, U, dst);
 }
 
 void launch_dt_reset(const KArgs &a, cudaStream_t s) {

@@ -55,6 +55,8 @@ def load_library():
         "cteno_run": (I, [V, I]),
         "cteno_get_state": (I, [V, C.c_int32, V, I]),
         "cteno_get_state_noalloc": (I, [V, C.c_int32, V]),
+        "cteno_set_state_all": (I, [V, V, I]),
+        "cteno_get_state_all": (I, [V, V, I]),
         "cteno_get_dt": (I, [V, V]),
         "cteno_record_flags": (I, [V, I]),
         "cteno_get_flags": (I, [V, C.c_int32, V]),
@@ -150,6 +152,30 @@ def cteno_get_state(ctx, mesh_id: int, out=None, is_device: bool = False):
     if out is None:
         out = np.empty((info[4], info[7]))
     _check(ctx, load_library().cteno_get_state(ctx, mesh_id, _ptr(out), 0))
+    return out
+
+
+def cteno_set_state_all(ctx, U, is_device: bool = False):
+    """All meshes at once. U: a flat float64 array holding mesh after mesh, each block
+    [nv, ncells] (or a list of those blocks), or with is_device a device address (int)."""
+    if is_device:
+        _check(ctx, load_library().cteno_set_state_all(ctx, C.c_void_p(U), 1))
+        return
+    if isinstance(U, (list, tuple)):
+        U = np.concatenate([np.ascontiguousarray(u, np.float64).ravel() for u in U])
+    U = np.ascontiguousarray(U, np.float64)
+    _check(ctx, load_library().cteno_set_state_all(ctx, _ptr(U), 0))
+
+
+def cteno_get_state_all(ctx, out=None, is_device: bool = False):
+    """All meshes at once into a flat float64 array (mesh after mesh, [nv, ncells] blocks)."""
+    if is_device:
+        _check(ctx, load_library().cteno_get_state_all(ctx, C.c_void_p(out), 1))
+        return out
+    info = cteno_info(ctx, -1)
+    if out is None:
+        out = np.empty(int(info[4]) * int(info[1]))
+    _check(ctx, load_library().cteno_get_state_all(ctx, _ptr(out), 0))
     return out
 
 
