@@ -77,7 +77,10 @@ typedef struct cteno_ctx cteno_ctx;
 void cteno_default_params(cteno_params *p);
 
 /* Create a context on the current CUDA device. `cuda_stream` is a cudaStream_t (may be NULL for
- * the legacy default stream); it is borrowed for the life of the context. */
+ * the legacy default stream); it is borrowed for the life of the context. The stage kernels use
+ * programmatic dependent launch (each kernel is launched as the previous one's blocks exit and
+ * waits for its results on the GPU); the environment variable CTENO_PDL=0, read here, launches
+ * them plainly instead. */
 int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream);
 
 /* Append one mesh to the context (Sec. 2: the physical domain as triangles / tetrahedra).

@@ -3,6 +3,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -55,6 +56,7 @@ struct cteno_ctx {
   int64_t member_sum = 0;            // admissible directional members over all cells
   int64_t adm_faces = 0;             // admissible directional stencils over all cells
   bool timing = false;
+  int pdl = 1;                       // programmatic dependent launch of the stage kernels
   cudaEvent_t tev[7] = {};           // event record nodes of the step graph
 };
 
@@ -91,6 +93,7 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.U = ctx->U;
   a.Un = ctx->Un;
   a.U32 = ctx->U32;
+  a.pdl = ctx->pdl;
   a.st = ctx->st;
   a.hl = ctx->hl;
   a.lidx = ctx->lidx;
@@ -244,6 +247,7 @@ int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream) {
   cteno_ctx *ctx = new (std::nothrow) cteno_ctx();
   if (!ctx) return CTENO_ERR_NOMEM;
   ctx->p = *p;
+  if (const char *e = std::getenv("CTENO_PDL")) ctx->pdl = std::atoi(e) != 0;
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->d = p->dim;
   ctx->nv = p->dim + 2;

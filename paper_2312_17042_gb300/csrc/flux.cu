@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
   using L = Lay<D>;
   constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, FB = NQ * NV;
   constexpr bool F32 = sizeof(T) == 4;
+  pdl_wait(a);  // face states of the reconstruction, the state of the previous stage
   const int64_t N = a.N;
   const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // threads past the last cell shadow it and store nothing, so that every lane of the warp
@@ -473,25 +474,25 @@ void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s) {
     const int threads = block - kLaneSchedule, cpw = 32 / (dim + 1);
     const int64_t cells_per_block = (int64_t)(threads / 32) * cpw;
     const unsigned grid = (unsigned)((a.N + cells_per_block - 1) / cells_per_block);
-    if (dim == 2 && fp32) flux_lanes_kernel<2, float><<<grid, threads, 0, s>>>(a);
-    if (dim == 2 && !fp32) flux_lanes_kernel<2, double><<<grid, threads, 0, s>>>(a);
-    if (dim == 3 && fp32) flux_lanes_kernel<3, float><<<grid, threads, 0, s>>>(a);
-    if (dim == 3 && !fp32) flux_lanes_kernel<3, double><<<grid, threads, 0, s>>>(a);
+    if (dim == 2 && fp32) launch_stage_kernel(flux_lanes_kernel<2, float>, grid, threads, 0, s, a);
+    if (dim == 2 && !fp32) launch_stage_kernel(flux_lanes_kernel<2, double>, grid, threads, 0, s, a);
+    if (dim == 3 && fp32) launch_stage_kernel(flux_lanes_kernel<3, float>, grid, threads, 0, s, a);
+    if (dim == 3 && !fp32) launch_stage_kernel(flux_lanes_kernel<3, double>, grid, threads, 0, s, a);
     return;
   }
   const bool capped = block < 0;  // register-capped variant (FP32 only)
   if (capped) block = -block;
   const unsigned grid = grid_for(a.N, block);
   if (dim == 2 && fp32) {
-    if (capped) flux_kernel<2, float, 8><<<grid, block, 0, s>>>(a);
-    else flux_kernel<2, float, 0><<<grid, block, 0, s>>>(a);
+    if (capped) launch_stage_kernel(flux_kernel<2, float, 8>, grid, block, 0, s, a);
+    else launch_stage_kernel(flux_kernel<2, float, 0>, grid, block, 0, s, a);
   }
   if (dim == 3 && fp32) {
-    if (capped) flux_kernel<3, float, 8><<<grid, block, 0, s>>>(a);
-    else flux_kernel<3, float, 0><<<grid, block, 0, s>>>(a);
+    if (capped) launch_stage_kernel(flux_kernel<3, float, 8>, grid, block, 0, s, a);
+    else launch_stage_kernel(flux_kernel<3, float, 0>, grid, block, 0, s, a);
   }
-  if (dim == 2 && !fp32) flux_kernel<2, double, 0><<<grid, block, 0, s>>>(a);
-  if (dim == 3 && !fp32) flux_kernel<3, double, 0><<<grid, block, 0, s>>>(a);
+  if (dim == 2 && !fp32) launch_stage_kernel(flux_kernel<2, double, 0>, grid, block, 0, s, a);
+  if (dim == 3 && !fp32) launch_stage_kernel(flux_kernel<3, double, 0>, grid, block, 0, s, a);
 }
 
 namespace {

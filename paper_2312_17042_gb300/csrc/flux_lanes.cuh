@@ -16,6 +16,7 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
   constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, FB = NQ * NV;
   constexpr int CPW = 32 / NF;
   constexpr bool F32 = sizeof(T) == 4;
+  pdl_wait(a);
   const int lane = threadIdx.x & 31;
   const int grp = lane / NF;
   const int f = lane - grp * NF;  // this lane's face (spare lanes: a face index < NF as well)

@@ -485,6 +485,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
     }
     __syncthreads();
   }
+  pdl_wait(a);  // the state written by the previous stage's update
 
   const int64_t N = a.N;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -769,6 +770,7 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
     }
     __syncthreads();
   }
+  pdl_wait(a);
   const int lane = threadIdx.x & 31;
   const int grp = lane / NV;                // cell slot in the warp (CPW = spare lanes)
   const int v = lane - grp * NV;            // this lane's variable
@@ -855,6 +857,9 @@ __global__ void __launch_bounds__(256) recon_staged_kernel(const KArgs a) {
     if ((int64_t)blockIdx.x < tiles) issue(blockIdx.x, 0);
     if ((int64_t)blockIdx.x + gridDim.x < tiles) issue((int64_t)blockIdx.x + gridDim.x, 1);
   }
+  // the operator records do not depend on the previous kernel: their copies were issued above;
+  // the states it writes (and the face states it may still read) are touched only after this
+  pdl_wait(a);
   // CFL time step bookkeeping at the first stage of a step: dt[next] -> dt[cur]
   if (a.dt_swap && blockIdx.x == 0)
     for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {
@@ -994,6 +999,9 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
     if ((int64_t)blockIdx.x < tiles) issue(blockIdx.x, 0);
     if (!ONE && (int64_t)blockIdx.x + gridDim.x < tiles) issue((int64_t)blockIdx.x + gridDim.x, 1);
   }
+  // the operator records and member lists do not depend on the previous kernel: their copies
+  // were issued above; member states, face states and dt are touched only after this
+  pdl_wait(a);
   if (a.dt_swap && blockIdx.x == 0)
     for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {
       a.dt[t] = a.dt[a.nmesh + t];
@@ -1065,7 +1073,7 @@ void launch_recon_halo(const KArgs &a, cudaStream_t s) {
   }
   const int64_t tiles = (a.N + C - 1) / C;
   const unsigned grid = ONE ? (unsigned)tiles : (unsigned)std::min<int64_t>(tiles, (int64_t)resident * sms);
-  kern<<<grid, threads, smem, s>>>(a);
+  launch_stage_kernel(kern, grid, threads, smem, s, a);
 }
 
 // Host side: persistent launch of the staged kernel, grid = (co-resident blocks per SM) x SMs.
@@ -1087,7 +1095,7 @@ void launch_recon_staged(const KArgs &a, int threads, cudaStream_t s) {
   }
   const int64_t tiles = (a.N + C - 1) / C;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)nb * sms);
-  kern<<<grid, threads, smem, s>>>(a);
+  launch_stage_kernel(kern, grid, threads, smem, s, a);
 }
 
 }  // namespace cteno

@@ -34,7 +34,7 @@ void launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block
     const int threads = block - kLaneSchedule, cpw = 32 / (3 + 2);
     const int64_t cells_per_block = (int64_t)(threads / 32) * cpw;
     const unsigned grid = (unsigned)((a.N + cells_per_block - 1) / cells_per_block);
-#define CTENO_LANES(R, T, SC) recon_lanes_kernel<3, R, T, SC><<<grid, threads, 0, s>>>(a)
+#define CTENO_LANES(R, T, SC) launch_stage_kernel(recon_lanes_kernel<3, R, T, SC>, grid, threads, 0, s, a)
     if (degree == 2 && fp32 && scheme == 0) CTENO_LANES(2, float, 0);
     if (degree == 2 && fp32 && scheme == 1) CTENO_LANES(2, float, 1);
     if (degree == 3 && fp32 && scheme == 0) CTENO_LANES(3, float, 0);
@@ -49,7 +49,7 @@ void launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block
   const bool capped = block < 0;  // register-capped variant (FP32 only)
   if (capped) block = -block;
   const unsigned grid = (unsigned)((a.N + block - 1) / block);
-#define CTENO_RECON(R, T, SC, MB) recon_kernel<3, R, T, SC, MB><<<grid, block, 0, s>>>(a)
+#define CTENO_RECON(R, T, SC, MB) launch_stage_kernel(recon_kernel<3, R, T, SC, MB>, grid, block, 0, s, a)
   if (degree == 2 && fp32 && scheme == 0) { if (capped) CTENO_RECON(2, float, 0, 8); else CTENO_RECON(2, float, 0, 0); }
   if (degree == 2 && fp32 && scheme == 1) { if (capped) CTENO_RECON(2, float, 1, 8); else CTENO_RECON(2, float, 1, 0); }
   if (degree == 3 && fp32 && scheme == 0) { if (capped) CTENO_RECON(3, float, 0, 8); else CTENO_RECON(3, float, 0, 0); }
