@@ -43,6 +43,11 @@ __device__ __forceinline__ T sqrt_(T x) {
   }
 }
 
+// Finite FP64 value (exponent field not all ones), tested with integer operations.
+__device__ __forceinline__ bool finite64(double x) {
+  return ((__double2hiint(x) >> 20) & 0x7FF) != 0x7FF;
+}
+
 // Exact FP32 -> FP64 conversion in integer operations (the FP64 pipe of this GPU is narrow);
 // subnormal FP32 values become zero, infinities and NaNs stay non-finite.
 __device__ __forceinline__ double f32_to_f64(float x) {
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
     acc_lo[v] = 0.0f;
   }
   // faces in groups of FG: all loads of a group are issued before its arithmetic
-  constexpr int FG = (D == 2) ? NF : 2;
+  constexpr int FG = MINB ? 1 : ((D == 2) ? NF : 2);  // the register-capped variant: one face at a time
 #pragma unroll
   for (int f0 = 0; f0 < NF; f0 += FG) {
     T gf[FG][4], uI[FG][FB], uO[FG][FB];
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
     if (a.stage == 0) res[v] = upd;
     else if (a.stage == 1) res[v] = 0.75 * un[v] + 0.25 * upd;
     else res[v] = (1.0 / 3.0) * un[v] + (2.0 / 3.0) * upd;
-    finite = finite && isfinite(res[v]);
+    finite = finite && finite64(res[v]);
   }
   if (active) {
 #pragma unroll

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
       else if (a.stage == 1) r = 0.75 * a.Un[i * NVP + v] + 0.25 * upd;
       else r = (1.0 / 3.0) * a.Un[i * NVP + v] + (2.0 / 3.0) * upd;
       res[v] = r;
-      finite = finite && isfinite(r);
+      finite = finite && finite64(r);
       if (active) {
         if (a.stage == 0) a.Un[i * NVP + v] = u;
         a.U[i * NVP + v] = r;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
     for (int v = 0; v < NV; ++v) full[v] = __shfl_sync(0xffffffffu, res[v], base + (v % NF));
     bool fin = active && f == 0;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) fin = fin && isfinite(full[v]);
+    for (int v = 0; v < NV; ++v) fin = fin && finite64(full[v]);
     T ft[NVP];
 #pragma unroll
     for (int v = 0; v < NVP; ++v) {
