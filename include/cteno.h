@@ -115,7 +115,8 @@ int cteno_set_state(cteno_ctx *ctx, int32_t mesh_id, const double *U, int is_dev
 /* Set the conserved cell means of every mesh at once (one copy and one launch for the batch):
  * U holds mesh after mesh, in the order the meshes were added, each mesh's block laid out as
  * for cteno_set_state (nv * ncells values, [v][c] in its own numbering); nv * (total cells)
- * doubles, host or device. Also computes every mesh's CFL time step. */
+ * doubles, host or device. Also computes every mesh's CFL time step. A page-locked host buffer
+ * is read by the kernel directly; pageable host memory is staged through device memory. */
 int cteno_set_state_all(cteno_ctx *ctx, const double *U, int is_device);
 
 /* One stage (stage = 0, 1, 2) of the SSP-RK3 step, for every mesh, with the time step dt[mesh]
@@ -131,7 +132,8 @@ int cteno_run(cteno_ctx *ctx, int nsteps);
 int cteno_get_state(cteno_ctx *ctx, int32_t mesh_id, double *U_out, int is_device);
 
 /* Read the conserved cell means of every mesh at once into U_out (host or device), laid out as
- * for cteno_set_state_all. A host read synchronises the stream once for the whole batch. */
+ * for cteno_set_state_all. A host read synchronises the stream once for the whole batch; a
+ * page-locked host buffer is written by the kernel directly. */
 int cteno_get_state_all(cteno_ctx *ctx, double *U_out, int is_device);
 
 /* Like cteno_get_state with a host output, but allocating nothing. The paper has no counterpart;

@@ -546,6 +546,19 @@ int cteno_set_state(cteno_ctx *ctx, int32_t mesh_id, const double *U, int is_dev
   return CTENO_OK;
 }
 
+namespace {
+// Device address of page-locked host memory (the kernels then read or write it directly over
+// the host link), or nullptr for pageable memory.
+const void *pinned_device_address(const void *p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear: an unregistered pointer is not an error here
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+}  // namespace
+
 int cteno_set_state_all(cteno_ctx *ctx, const double *U, int is_device) {
   int rc = check_built(ctx);
   if (rc) return rc;
@@ -553,13 +566,14 @@ int cteno_set_state_all(cteno_ctx *ctx, const double *U, int is_device) {
   const size_t cnt = (size_t)ctx->nv * ctx->N;
   const double *src = U;
   if (!is_device) {
-    if ((rc = ensure_stage_buf(ctx, cnt))) return rc;
-    CK(cudaMemcpyAsync(ctx->stage_buf, U, cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    src = ctx->stage_buf;
+    src = static_cast<const double *>(pinned_device_address(U));
+    if (!src) {  // pageable: stage through device memory
+      if ((rc = ensure_stage_buf(ctx, cnt))) return rc;
+      CK(cudaMemcpyAsync(ctx->stage_buf, U, cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+      src = ctx->stage_buf;
+    }
   }
-  launch_permute_in_all(ctx->nv, lay_nvp(ctx->d), ctx->N, (int)ctx->meshes.size(), ctx->d_mesh_off,
-                        ctx->d_grank, src, ctx->U, ctx->U32, ctx->stream);
-  launch_dt(ctx->d, make_args(ctx, 0, 0), ctx->stream);
+  launch_set_state_all(ctx->d, make_args(ctx, 0, 0), ctx->d_grank, src, ctx->stream);
   CK(cudaGetLastError());
   return CTENO_OK;
 }
@@ -575,6 +589,13 @@ int cteno_get_state_all(cteno_ctx *ctx, double *U_out, int is_device) {
                            U_out, ctx->stream);
     CK(cudaGetLastError());
     return CTENO_OK;
+  }
+  if (double *dst = static_cast<double *>(const_cast<void *>(pinned_device_address(U_out)))) {
+    // page-locked output: the kernel writes it directly
+    launch_permute_out_all(ctx->nv, lay_nvp(ctx->d), ctx->N, nmesh, ctx->d_mesh_off, ctx->d_grank, ctx->U, dst,
+                           ctx->stream);
+    CK(cudaGetLastError());
+    return device_status(ctx);
   }
   if ((rc = ensure_stage_buf(ctx, cnt))) return rc;
   launch_permute_out_all(ctx->nv, lay_nvp(ctx->d), ctx->N, nmesh, ctx->d_mesh_off, ctx->d_grank, ctx->U,

@@ -392,9 +392,12 @@ __global__ void dt_kernel(const KArgs a, int64_t first, int64_t count) {
   double u[NVP];
 #pragma unroll
   for (int v = 0; v < NVP; ++v) u[v] = a.U[i * NVP + v];
-  T uu[NVP];
+  T uu[NVP];  // FP32 path: the hi part of the (hi, lo) split, as in the stage update
 #pragma unroll
-  for (int v = 0; v < NVP; ++v) uu[v] = (T)u[v];
+  for (int v = 0; v < NVP; ++v) {
+    if constexpr (sizeof(T) == 4) uu[v] = f64_split(u[v]).x;
+    else uu[v] = u[v];
+  }
   const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
   warp_min_to(a.dt, a.nmesh + mesh, active ? a.cfl * local_dt<D, T>(a, i, uu) : 1e300);
 }
@@ -433,6 +436,38 @@ __global__ void permute_in_all_kernel(int nv, int nvp, int64_t N, int nmesh, con
       U32[(g * nvp + v) * 2 + 1] = s.y;
     }
   }
+}
+
+// Set every mesh's state and compute each mesh's CFL step of it in the same pass (dt[next] must
+// have been reset). src may be device memory or page-locked host memory.
+template <int D, typename T>
+__global__ void permute_in_all_dt_kernel(const KArgs a, const int32_t *grank, const double *src) {
+  constexpr int NV = D + 2, NVP = Lay<D>::NVP;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = idx < a.N;
+  const int64_t c = active ? idx : a.N - 1;  // every lane reaches the reduction
+  const int k = mesh_of_offsets(a.mesh_off, a.nmesh, c);
+  const int64_t off = a.mesh_off[k], n = a.mesh_off[k + 1] - off, local = c - off;
+  const int64_t g = grank[c];
+  double u[NVP];
+  T ut[NVP];
+#pragma unroll
+  for (int v = 0; v < NVP; ++v) {
+    u[v] = (v < NV) ? src[NV * off + v * n + local] : 0.0;
+    if constexpr (sizeof(T) == 4) ut[v] = f64_split(u[v]).x;
+    else ut[v] = u[v];
+  }
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < NVP / 2; ++q) {
+      reinterpret_cast<double2 *>(a.U + g * NVP)[q] = make_double2(u[2 * q], u[2 * q + 1]);
+      if (a.U32) {
+        const float2 s0 = f64_split(u[2 * q]), s1 = f64_split(u[2 * q + 1]);
+        reinterpret_cast<float4 *>(a.U32 + g * 2 * NVP)[q] = make_float4(s0.x, s0.y, s1.x, s1.y);
+      }
+    }
+  }
+  warp_min_to(a.dt, a.nmesh + k, active ? a.cfl * local_dt<D, T>(a, g, ut) : 1e300);
 }
 
 __global__ void permute_out_all_kernel(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
@@ -524,6 +559,16 @@ void launch_dt_mesh(int dim, const KArgs &a, int mesh, int64_t first, int64_t co
 void launch_permute_in_all(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
                            const int32_t *grank, const double *src, double *U, float *U32, cudaStream_t s) {
   permute_in_all_kernel<<<grid_for(N, 256), 256, 0, s>>>(nv, nvp, N, nmesh, mesh_off, grank, src, U, U32);
+}
+
+void launch_set_state_all(int dim, const KArgs &a, const int32_t *grank, const double *src, cudaStream_t s) {
+  dt_reset_kernel<<<grid_for(a.nmesh, 64), 64, 0, s>>>(a.dt, a.nmesh);
+  const bool f32 = a.geo32 != nullptr;
+  const unsigned g = grid_for(a.N, 256);
+  if (dim == 2 && f32) permute_in_all_dt_kernel<2, float><<<g, 256, 0, s>>>(a, grank, src);
+  if (dim == 2 && !f32) permute_in_all_dt_kernel<2, double><<<g, 256, 0, s>>>(a, grank, src);
+  if (dim == 3 && f32) permute_in_all_dt_kernel<3, float><<<g, 256, 0, s>>>(a, grank, src);
+  if (dim == 3 && !f32) permute_in_all_dt_kernel<3, double><<<g, 256, 0, s>>>(a, grank, src);
 }
 
 void launch_permute_out_all(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,

@@ -417,13 +417,26 @@ def test_batch_wide_state_calls_match_per_mesh_calls(precision):
         assert np.array_equal(native.cteno_get_state(a.ctx, k), u)
     assert np.array_equal(native.cteno_get_state_all(b.ctx), flat)
     assert np.array_equal(native.cteno_get_state_all(a.ctx), flat)
+    # page-locked host buffers are read and written by the kernels directly
+    import torch
+    pin_in = torch.empty(flat.size, dtype=torch.float64, pin_memory=True).numpy()
+    pin_out = torch.empty(flat.size, dtype=torch.float64, pin_memory=True).numpy()
+    pin_in[:] = flat
+    c = _solver(native, meshes, 2, degree=2, scheme=1, precision=precision)
+    native.cteno_set_state_all(c.ctx, pin_in)
+    native.cteno_get_state_all(c.ctx, pin_out)
+    assert np.array_equal(pin_out, flat)
     a.run(3)
     b.run(3)
-    assert np.array_equal(a.dt(), b.dt())
+    c.run(3)
+    assert np.array_equal(a.dt(), b.dt()) and np.array_equal(a.dt(), c.dt())
     got = native.cteno_get_state_all(a.ctx)
     assert np.array_equal(got, np.concatenate([native.cteno_get_state(b.ctx, k).ravel() for k in range(5)]))
+    native.cteno_get_state_all(c.ctx, pin_out)
+    assert np.array_equal(pin_out, got)
     a.close()
     b.close()
+    c.close()
 
 
 def test_rejects_bad_calls_without_faulting():
