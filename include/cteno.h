@@ -196,7 +196,10 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
  * CTENO_ERR_DEVICE. 4096 (mixed path) selects that lane schedule with 4 warps whose tiles also copy
  * the states of their distinct stencil members into shared memory (lists built by cteno_lsq_build);
  * 4097 the same with one tile per block and a single stage (half the shared memory); both refused
- * like the staged values when they do not fit. */
+ * like the staged values when they do not fit. Flux only: 8192 + b (b a multiple of 32 in
+ * [32, 256]) selects the face-based schedule: HLLC once per face, in its owner's orientation, into
+ * a face-flux array, then a per-cell gather and update (results bit-identical to the per-cell
+ * schedules). */
 int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block);
 
 /* Time the candidate launch configurations (block sizes 64/128/256, on the mixed path the

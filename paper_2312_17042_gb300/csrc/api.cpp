@@ -45,6 +45,9 @@ struct cteno_ctx {
   unsigned long long *guard = nullptr;
   std::vector<int32_t *> d_rank;
   int32_t *d_grank = nullptr;        // device cell of each concatenated original cell (all meshes)
+  int32_t *d_face = nullptr, *d_cellface = nullptr;  // face-based flux schedule
+  void *Ff = nullptr;
+  int64_t nfaces = 0;
   double *stage_buf = nullptr;       // staging for host <-> device state copies
   size_t stage_cap = 0;
   double *backup = nullptr;          // autotune state backup
@@ -94,6 +97,10 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.Un = ctx->Un;
   a.U32 = ctx->U32;
   a.pdl = ctx->pdl;
+  a.face = ctx->d_face;
+  a.cellface = ctx->d_cellface;
+  a.Ff = ctx->Ff;
+  a.nfaces = ctx->nfaces;
   a.st = ctx->st;
   a.hl = ctx->hl;
   a.lidx = ctx->lidx;
@@ -421,8 +428,32 @@ int cteno_lsq_build(cteno_ctx *ctx) {
       hmeta[g] = meta;
     }
   }
+  // face list of the face-based flux schedule: owner cell-faces in (cell, face) order; every
+  // cell-face refers to its face, flagged where the cell is not the owner
+  std::vector<int32_t> hface, hcellface((size_t)N * 4, 0);
+  for (int64_t g = 0; g < N; ++g)
+    for (int f = 0; f < nf; ++f)
+      if ((hmeta[g] >> (kMetaOwnerShift + f)) & 1u) {
+        hcellface[(size_t)g * 4 + f] = (int32_t)hface.size();
+        hface.push_back((int32_t)(g * 4 + f));
+      }
+  for (int64_t g = 0; g < N; ++g)
+    for (int f = 0; f < nf; ++f)
+      if (!((hmeta[g] >> (kMetaOwnerShift + f)) & 1u)) {
+        const int64_t gn = hnbr[(size_t)g * 4 + f];
+        const int fn = (hmeta[g] >> (2 * f)) & 3u;
+        hcellface[(size_t)g * 4 + f] = (int32_t)(hcellface[(size_t)gn * 4 + fn] | 0x80000000u);
+      }
   // device allocations
   const size_t sT = ctx->fp32 ? sizeof(float) : sizeof(double);
+  ctx->nfaces = (int64_t)hface.size();
+  CK(dalloc(ctx, &ctx->d_face, sizeof(int32_t) * hface.size()));
+  CK(dalloc(ctx, &ctx->d_cellface, sizeof(int32_t) * hcellface.size()));
+  CK(dalloc(ctx, &ctx->Ff, sT * ((ctx->nv + 3) & ~3) * hface.size()));
+  CK(cudaMemcpyAsync(ctx->d_face, hface.data(), sizeof(int32_t) * hface.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_cellface, hcellface.data(), sizeof(int32_t) * hcellface.size(),
+                     cudaMemcpyHostToDevice, ctx->stream));
   double *dX = nullptr;
   CK(cudaMalloc(&dX, hX.size() * sizeof(double)));
   CK(dalloc(ctx, &ctx->d_tab, sizeof(DevTables)));
@@ -769,6 +800,8 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
   // variant (mixed path only, at most 128 threads)
   auto ok = [&](int b, bool recon) {
     if (b == 0) return true;
+    if (b >= kFaceFlux)  // face-based flux schedule
+      return !recon && b - kFaceFlux >= 32 && b - kFaceFlux <= 256 && b % 32 == 0;
     if (b == kHaloLanes || b == kHaloLanes + 1)  // gather-staged: reconstruction, mixed, lists built, fits
       return recon && ctx->fp32 && ctx->hl &&
              recon_halo_smem(ctx->d, ctx->p.degree, ctx->hrec) / (b == kHaloLanes ? 1 : 2) <= kMaxStagedSmem;
@@ -852,7 +885,9 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
     CK(cudaEventElapsedTime(&ms, e0, e1));
     if (ms < best_r) best_r = ms, br = b;
   }
-  for (int b : cand) {
+  std::vector<int> fcand = cand;  // flux: also the face-based schedule
+  for (int b : {kFaceFlux + 128, kFaceFlux + 256}) fcand.push_back(b);
+  for (int b : fcand) {
     float tot = 0;
     for (int r = 0; r < reps; ++r) {
       CK(save_restore(false));

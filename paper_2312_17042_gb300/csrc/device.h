@@ -110,6 +110,12 @@ struct KArgs {
   const int32_t *hl;
   const uint16_t *lidx;
   int htile, hrec, hms;
+  // face-based flux schedule: face e = (owner device cell << 2 | local face); cellface[i*4+f] =
+  // face id, bit 31 set where cell i is not the owner; Ff [nfaces][(nv+3)&~3] face fluxes (T)
+  const int32_t *face;
+  const int32_t *cellface;
+  void *Ff;
+  int64_t nfaces;
   int pdl;                  // launched with programmatic dependent launch (see pdl_wait)
   int stage;                // 0, 1, 2
   int dt_swap;              // stage 0 of a CFL step: move dt[next] to dt[cur] first
@@ -144,6 +150,9 @@ constexpr int kMaxStagedSmem = 200 * 1024;  // dynamic shared memory of the two 
 // kHaloLanes: the staged lane schedule (4 warps) that also stages each tile's distinct stencil
 // members' states in shared memory (mixed path).
 constexpr int kHaloLanes = 4096;
+// Flux launch value kFaceFlux + b: the face-based schedule (HLLC once per face, then a per-cell
+// gather and update), b threads per block.
+constexpr int kFaceFlux = 8192;
 constexpr int kHaloWarps = 4;
 inline int halo_tile(int d) { return kHaloWarps * (32 / (d + 2)); }
 inline int halo_ms(int M) { return (M + 1 + 7) / 8 * 8; }

@@ -374,6 +374,173 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
     warp_min_to(a.dt, a.nmesh + mesh, (finite && active) ? a.cfl * local_dt<D, T>(a, i, ust) : 1e300);
 }
 
+// Face flux of the face-based schedule: one thread per face, HLLC at the face's Gauss points in
+// its owner's orientation (the same operands and order as flux_kernel's owner side), weighted and
+// scaled by the area; record e holds |A| sum_q w_q F_q, padded to NFP values.
+template <int D, typename T>
+__global__ void __launch_bounds__(256) face_flux_kernel(const KArgs a) {
+  using L = Lay<D>;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, FB = NQ * NV;
+  constexpr int NFP = (NV + 3) & ~3;
+  constexpr bool F32 = sizeof(T) == 4;
+  pdl_wait(a);  // face states of the reconstruction
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.nfaces) return;
+  const int32_t code = __ldg(a.face + e);
+  const int64_t i = code >> 2;
+  const int f = code & 3;
+  const T *__restrict__ Uf = (const T *)a.Uf;
+  const T *__restrict__ G = F32 ? (const T *)a.geo32 : (const T *)a.geo;
+  T g;
+  if constexpr (F32) g = a.gamma32; else g = a.gamma;
+  T gf[4], uI[FB], uO[FB];
+  load16<T, 4>(G + (i * NF + f) * 4, gf);
+  load16<T, FB>(Uf + (i * NF + f) * FB, uI);
+  const int64_t j = __ldg(a.nbr + i * 4 + f);
+  if (j >= 0) {
+    const int fj = (__ldg(a.fmeta + i) >> (2 * f)) & 3u;
+    load16<T, FB>(Uf + (j * NF + fj) * FB, uO);
+  } else {  // transmissive boundary: the cell mean outside
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T m = (T)a.U[i * NVP + v];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) uO[q * NV + v] = m;
+    }
+  }
+  T n[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) n[k] = gf[k];
+  T Ff[NV];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    T F[NV];
+    hllc<D, T>(uI + q * NV, uO + q * NV, n, g, F);
+    T w;
+    if constexpr (F32) w = a.fw32[q]; else w = a.fw[q];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ff[v] = (q == 0) ? w * F[v] : Ff[v] + w * F[v];
+  }
+  T out[NFP];
+#pragma unroll
+  for (int v = 0; v < NFP; ++v) out[v] = (v < NV) ? gf[3] * Ff[v] : (T)0;
+  store16<T, NFP>((T *)a.Ff + e * NFP, out);
+}
+
+// Residual and stage update of the face-based schedule: as flux_kernel with its face fluxes read
+// from face_flux_kernel's records.
+template <int D, typename T, int MINB>
+__global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) cell_update_kernel(const KArgs a) {
+  using L = Lay<D>;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF;
+  constexpr bool F32 = sizeof(T) == 4;
+  pdl_wait(a);  // the face fluxes of this stage
+  const int64_t N = a.N;
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // threads past the last cell shadow it and store nothing, so that every lane of the warp
+  // reaches the time-step reduction
+  const bool active = cell < N;
+  const int64_t i = active ? cell : N - 1;
+  // this cell's FP64 record (read before it is overwritten by this same thread)
+  double u64[NVP];
+#pragma unroll
+  for (int c = 0; c < NVP / 2; ++c) {
+    const double2 x = reinterpret_cast<const double2 *>(a.U + i * NVP)[c];
+    u64[2 * c] = x.x;
+    u64[2 * c + 1] = x.y;
+  }
+  double acc[NV];
+  float acc_hi[NV], acc_lo[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    acc[v] = 0.0;
+    acc_hi[v] = 0.0f;
+    acc_lo[v] = 0.0f;
+  }
+  // face fluxes computed once per face (face_flux_kernel), signed for this cell, summed in face
+  // order exactly as in flux_kernel
+  const int4 cf4 = __ldg(reinterpret_cast<const int4 *>(a.cellface) + i);
+  const int cfv[4] = {cf4.x, cf4.y, cf4.z, cf4.w};
+  constexpr int NFP = (NV + 3) & ~3;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int64_t e = cfv[f] & 0x7FFFFFFF;
+    const bool neg = cfv[f] < 0;
+    T x[NFP];
+    load16<T, NFP>((const T *)a.Ff + e * NFP, x);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T c = neg ? -x[v] : x[v];
+      if constexpr (F32) {
+        float s, er;
+        two_sum(acc_hi[v], c, s, er);
+        acc_hi[v] = s;
+        acc_lo[v] += er;
+      } else {
+        acc[v] += c;
+      }
+    }
+  }
+  if constexpr (F32) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = f32_to_f64(acc_hi[v]) + f32_to_f64(acc_lo[v]);
+  }
+  // residual and SSP-RK3 (Shu-Osher) stage update in FP64
+  const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
+  const double dtv = a.dt[mesh] * a.vol[i];  // dt / |V_i|
+  double un[NVP], res[NVP];
+  if (a.stage != 0) {
+#pragma unroll
+    for (int c = 0; c < NVP / 2; ++c) {
+      const double2 x = reinterpret_cast<const double2 *>(a.Un + i * NVP)[c];
+      un[2 * c] = x.x;
+      un[2 * c + 1] = x.y;
+    }
+  }
+  bool finite = true;
+#pragma unroll
+  for (int v = 0; v < NVP; ++v) {
+    if (v >= NV) {
+      res[v] = 0.0;
+      continue;
+    }
+    const double upd = u64[v] - dtv * acc[v];
+    if (a.stage == 0) res[v] = upd;
+    else if (a.stage == 1) res[v] = 0.75 * un[v] + 0.25 * upd;
+    else res[v] = (1.0 / 3.0) * un[v] + (2.0 / 3.0) * upd;
+    finite = finite && finite64(res[v]);
+  }
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < NVP / 2; ++c) {
+      reinterpret_cast<double2 *>(a.U + i * NVP)[c] = make_double2(res[2 * c], res[2 * c + 1]);
+      if (a.stage == 0)
+        reinterpret_cast<double2 *>(a.Un + i * NVP)[c] = make_double2(u64[2 * c], u64[2 * c + 1]);
+    }
+  }
+  T ust[NVP];  // the new state in the path's type, for the CFL step
+  if constexpr (F32) {  // FP32 (hi, lo) shadow of the new state
+    float4 hl[NVP / 2];
+#pragma unroll
+    for (int c = 0; c < NVP / 2; ++c) {
+      const float2 s0 = f64_split(res[2 * c]), s1 = f64_split(res[2 * c + 1]);
+      hl[c] = make_float4(s0.x, s0.y, s1.x, s1.y);
+      ust[2 * c] = s0.x;
+      ust[2 * c + 1] = s1.x;
+    }
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < NVP / 2; ++c) reinterpret_cast<float4 *>(a.U32 + i * 2 * NVP)[c] = hl[c];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NVP; ++v) ust[v] = res[v];
+  }
+  if (!finite && active) atomicOr(a.err, kErrNonFinite);
+  if (a.stage == 2)
+    warp_min_to(a.dt, a.nmesh + mesh, (finite && active) ? a.cfl * local_dt<D, T>(a, i, ust) : 1e300);
+}
+
 }  // namespace
 }  // namespace cteno
 
@@ -510,6 +677,27 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 }  // namespace
 
 void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s) {
+  if (block >= kFaceFlux) {  // face-based: HLLC once per face, then the per-cell gather and update
+    const int threads = block - kFaceFlux;
+    const unsigned gf = grid_for(a.nfaces, 256), gc = grid_for(a.N, threads);
+    if (dim == 2 && fp32) {
+      launch_stage_kernel(face_flux_kernel<2, float>, gf, 256, 0, s, a);
+      launch_stage_kernel(cell_update_kernel<2, float, 0>, gc, threads, 0, s, a);
+    }
+    if (dim == 3 && fp32) {
+      launch_stage_kernel(face_flux_kernel<3, float>, gf, 256, 0, s, a);
+      launch_stage_kernel(cell_update_kernel<3, float, 0>, gc, threads, 0, s, a);
+    }
+    if (dim == 2 && !fp32) {
+      launch_stage_kernel(face_flux_kernel<2, double>, gf, 256, 0, s, a);
+      launch_stage_kernel(cell_update_kernel<2, double, 0>, gc, threads, 0, s, a);
+    }
+    if (dim == 3 && !fp32) {
+      launch_stage_kernel(face_flux_kernel<3, double>, gf, 256, 0, s, a);
+      launch_stage_kernel(cell_update_kernel<3, double, 0>, gc, threads, 0, s, a);
+    }
+    return;
+  }
   if (block >= kLaneSchedule) {  // face-per-lane schedule, block - kLaneSchedule threads
     const int threads = block - kLaneSchedule, cpw = 32 / (dim + 1);
     const int64_t cells_per_block = (int64_t)(threads / 32) * cpw;
