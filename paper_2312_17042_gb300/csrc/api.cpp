@@ -434,8 +434,10 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   for (int64_t g = 0; g < N; ++g)
     for (int f = 0; f < nf; ++f)
       if ((hmeta[g] >> (kMetaOwnerShift + f)) & 1u) {
-        hcellface[(size_t)g * 4 + f] = (int32_t)hface.size();
+        hcellface[(size_t)g * 4 + f] = (int32_t)(hface.size() / 2);
+        const int64_t gn = hnbr[(size_t)g * 4 + f];
         hface.push_back((int32_t)(g * 4 + f));
+        hface.push_back(gn < 0 ? -1 : (int32_t)(gn * 4 + ((hmeta[g] >> (2 * f)) & 3u)));
       }
   for (int64_t g = 0; g < N; ++g)
     for (int f = 0; f < nf; ++f)
@@ -446,10 +448,10 @@ int cteno_lsq_build(cteno_ctx *ctx) {
       }
   // device allocations
   const size_t sT = ctx->fp32 ? sizeof(float) : sizeof(double);
-  ctx->nfaces = (int64_t)hface.size();
+  ctx->nfaces = (int64_t)hface.size() / 2;
   CK(dalloc(ctx, &ctx->d_face, sizeof(int32_t) * hface.size()));
   CK(dalloc(ctx, &ctx->d_cellface, sizeof(int32_t) * hcellface.size()));
-  CK(dalloc(ctx, &ctx->Ff, sT * ((ctx->nv + 3) & ~3) * hface.size()));
+  CK(dalloc(ctx, &ctx->Ff, sT * ((ctx->nv + 3) & ~3) * ctx->nfaces));
   CK(cudaMemcpyAsync(ctx->d_face, hface.data(), sizeof(int32_t) * hface.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_cellface, hcellface.data(), sizeof(int32_t) * hcellface.size(),

@@ -110,7 +110,8 @@ struct KArgs {
   const int32_t *hl;
   const uint16_t *lidx;
   int htile, hrec, hms;
-  // face-based flux schedule: face e = (owner device cell << 2 | local face); cellface[i*4+f] =
+  // face-based flux schedule: face e = {owner device cell << 2 | local face, the same for the
+  // neighbour side or -1 on a boundary}; cellface[i*4+f] =
   // face id, bit 31 set where cell i is not the owner; Ff [nfaces][(nv+3)&~3] face fluxes (T)
   const int32_t *face;
   const int32_t *cellface;

@@ -386,9 +386,9 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const KArgs a) {
   pdl_wait(a);  // face states of the reconstruction
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.nfaces) return;
-  const int32_t code = __ldg(a.face + e);
-  const int64_t i = code >> 2;
-  const int f = code & 3;
+  const int2 codes = __ldg(reinterpret_cast<const int2 *>(a.face) + e);  // owner, neighbour side
+  const int64_t i = codes.x >> 2;
+  const int f = codes.x & 3;
   const T *__restrict__ Uf = (const T *)a.Uf;
   const T *__restrict__ G = F32 ? (const T *)a.geo32 : (const T *)a.geo;
   T g;
@@ -396,9 +396,9 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const KArgs a) {
   T gf[4], uI[FB], uO[FB];
   load16<T, 4>(G + (i * NF + f) * 4, gf);
   load16<T, FB>(Uf + (i * NF + f) * FB, uI);
-  const int64_t j = __ldg(a.nbr + i * 4 + f);
-  if (j >= 0) {
-    const int fj = (__ldg(a.fmeta + i) >> (2 * f)) & 3u;
+  if (codes.y >= 0) {
+    const int64_t j = codes.y >> 2;
+    const int fj = codes.y & 3;
     load16<T, FB>(Uf + (j * NF + fj) * FB, uO);
   } else {  // transmissive boundary: the cell mean outside
 #pragma unroll
