@@ -936,7 +936,9 @@ int cteno_kernel_stats(cteno_ctx *ctx, double *out) {
                 (ctx->fp32 ? 8.0 * nvp : 0.0));
   // FLOPs: central and directional products, p_1, SI, selection (~30 per stencil), face values
   const double st = 1.0 + (N > 0 ? members / N / d : 0.0);
-  out[2] = N * (2.0 * nk * M * nv + 2.0 * nv * (nk * nk + nk) + nv * 30.0 * st + 2.0 * nv * nf * nq * nk) +
+  // (SI = a^T O a counted in its symmetric form: nk(nk+1)/2 products and nk more per variable)
+  out[2] = N * (2.0 * nk * M * nv + 2.0 * nv * (nk * (nk + 1) / 2.0 + nk) + nv * 30.0 * st +
+                2.0 * nv * nf * nq * nk) +
            members * 2.0 * d * nv;
   // HLLC ~ 90 + 20 d operations per Gauss point, plus accumulation and the update
   out[3] = N * (nf * nq * (90.0 + 20.0 * d + 3.0 * nv) + 6.0 * nv);

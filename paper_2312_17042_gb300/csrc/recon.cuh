@@ -32,7 +32,7 @@ struct Shape {
 };
 
 // Constant-bank copies of the universal tables of this module's degrees (filled by
-// upload_recon_tables_*): the smoothness matrix O (eq. 15) and, in 2D, the face-point basis values
+// upload_recon_tables_*): the smoothness matrix O (eq. 15; upper triangle, off-diagonal doubled) and, in 2D, the face-point basis values
 // phi_k at the two Gauss points of each local edge taken in local vertex order (the other edge
 // orientation visits the same two symmetric points in the opposite order). Indexed with
 // compile-time offsets only, so they become instruction operands.
@@ -62,10 +62,12 @@ __device__ __forceinline__ T cPhi2(int idx) {
 inline cudaError_t upload_recon_tables(int dim, int degree, const Tables &t, cudaStream_t s) {
   double Od[kMaxNK * kMaxNK] = {}, Pd2[3 * 2 * kMaxNK] = {};
   float Of[kMaxNK * kMaxNK] = {}, Pf2[3 * 2 * kMaxNK] = {};
+  // O is symmetric: the kernels use the upper triangle only, with the off-diagonal entries doubled
+  // (exact), a^T O a = sum_k a_k (O_kk a_k + sum_{l>k} 2 O_kl a_l)
   for (int k = 0; k < t.nk; ++k)
-    for (int l = 0; l < t.nk; ++l) {
-      Od[k * t.nk + l] = t.O[k][l];
-      Of[k * t.nk + l] = (float)t.O[k][l];
+    for (int l = k; l < t.nk; ++l) {
+      Od[k * t.nk + l] = (l == k ? 1.0 : 2.0) * t.O[k][l];
+      Of[k * t.nk + l] = (float)Od[k * t.nk + l];
     }
   if (dim == 2)
     for (int f = 0; f < 3; ++f)
@@ -368,7 +370,7 @@ __device__ __forceinline__ void recon_cell(const KArgs &a, const int64_t i, cons
     for (int k = 0; k < NK; ++k) {
       T r = (T)0;
 #pragma unroll
-      for (int l = 0; l < NK; ++l) r += cO<T, R>(k * NK + l) * a1[l];
+      for (int l = k; l < NK; ++l) r += cO<T, R>(k * NK + l) * a1[l];
       SI0 += a1[k] * r;
     }
     T SId[NF];
@@ -657,7 +659,7 @@ __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, cons
     for (int k = 0; k < NK; ++k) {
       T rr = (T)0;
 #pragma unroll
-      for (int l = 0; l < NK; ++l) rr += cO<T, R>(k * NK + l) * a1[l];
+      for (int l = k; l < NK; ++l) rr += cO<T, R>(k * NK + l) * a1[l];
       SI0 += a1[k] * rr;
     }
     T SId[NF];
