@@ -172,8 +172,8 @@ def cteno_get_state_all(ctx, out=None, is_device: bool = False):
     if is_device:
         _check(ctx, load_library().cteno_get_state_all(ctx, C.c_void_p(out), 1))
         return out
-    info = cteno_info(ctx, -1)
     if out is None:
+        info = cteno_info(ctx, -1)
         out = np.empty(int(info[4]) * int(info[1]))
     _check(ctx, load_library().cteno_get_state_all(ctx, _ptr(out), 0))
     return out
