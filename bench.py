@@ -413,7 +413,9 @@ def run_ours(args, rank, world, local):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 6 * args.steps,
+        # per stage: one reconstruction launch and one flux/update launch, or two for the
+        # face-based flux schedule (face fluxes, then the per-cell update)
+        "gpu_launches": 3 * (1 + (2 if blocks[1] >= 8192 else 1)) * args.steps,
         "clocks": clk,
         "variants": variants,
         "alu_peak_measured": alu,
