@@ -195,10 +195,8 @@ void launch_dt_reset(const KArgs &a, cudaStream_t s);
 void launch_dt_mesh(int dim, const KArgs &a, int mesh, int64_t first, int64_t count, cudaStream_t s);
 // All meshes in one launch: host-side order is mesh after mesh, [v][cell] per mesh in the mesh's
 // original numbering; grank[c] is the device cell of concatenated original cell c.
-void launch_permute_in_all(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
-                           const int32_t *grank, const double *src, double *U, float *U32, cudaStream_t s);
-// Set every mesh's state from src (device or page-locked host memory, layout as for
-// launch_permute_in_all) and compute each mesh's CFL step of it, in one pass.
+// Set every mesh's state from src (device or page-locked host memory, layout above) and compute
+// each mesh's CFL step of it, in one pass.
 void launch_set_state_all(int dim, const KArgs &a, const int32_t *grank, const double *src, cudaStream_t s);
 void launch_permute_out_all(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
                             const int32_t *grank, const double *U, double *dst, cudaStream_t s);

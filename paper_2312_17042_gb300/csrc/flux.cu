@@ -587,24 +587,6 @@ __device__ __forceinline__ int mesh_of_offsets(const int64_t *off, int nmesh, in
   return lo;
 }
 
-__global__ void permute_in_all_kernel(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
-                                      const int32_t *grank, const double *src, double *U, float *U32) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= N) return;
-  const int k = mesh_of_offsets(mesh_off, nmesh, c);
-  const int64_t off = mesh_off[k], n = mesh_off[k + 1] - off, local = c - off;
-  const int64_t g = grank[c];
-  for (int v = 0; v < nvp; ++v) {
-    const double x = (v < nv) ? src[nv * off + v * n + local] : 0.0;
-    U[g * nvp + v] = x;
-    if (U32) {
-      const float2 s = f64_split(x);
-      U32[(g * nvp + v) * 2] = s.x;
-      U32[(g * nvp + v) * 2 + 1] = s.y;
-    }
-  }
-}
-
 // Set every mesh's state and compute each mesh's CFL step of it in the same pass (dt[next] must
 // have been reset). src may be device memory or page-locked host memory.
 template <int D, typename T>
@@ -742,11 +724,6 @@ void launch_dt(int dim, const KArgs &a, cudaStream_t s) {
 void launch_dt_mesh(int dim, const KArgs &a, int mesh, int64_t first, int64_t count, cudaStream_t s) {
   dt_reset_one_kernel<<<1, 1, 0, s>>>(a.dt, a.nmesh, mesh);
   launch_dt_cells(dim, a, first, count, s);
-}
-
-void launch_permute_in_all(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
-                           const int32_t *grank, const double *src, double *U, float *U32, cudaStream_t s) {
-  permute_in_all_kernel<<<grid_for(N, 256), 256, 0, s>>>(nv, nvp, N, nmesh, mesh_off, grank, src, U, U32);
 }
 
 void launch_set_state_all(int dim, const KArgs &a, const int32_t *grank, const double *src, cudaStream_t s) {
