@@ -60,6 +60,7 @@ struct cteno_ctx {
   int64_t adm_faces = 0;             // admissible directional stencils over all cells
   bool timing = false;
   int pdl = 1;                       // programmatic dependent launch of the stage kernels
+  int zerocopy = 1;                  // batch-wide calls access page-locked host buffers directly
   cudaEvent_t tev[7] = {};           // event record nodes of the step graph
 };
 
@@ -255,6 +256,7 @@ int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream) {
   if (!ctx) return CTENO_ERR_NOMEM;
   ctx->p = *p;
   if (const char *e = std::getenv("CTENO_PDL")) ctx->pdl = std::atoi(e) != 0;
+  if (const char *e = std::getenv("CTENO_ZEROCOPY")) ctx->zerocopy = std::atoi(e) != 0;
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->d = p->dim;
   ctx->nv = p->dim + 2;
@@ -599,7 +601,7 @@ int cteno_set_state_all(cteno_ctx *ctx, const double *U, int is_device) {
   const size_t cnt = (size_t)ctx->nv * ctx->N;
   const double *src = U;
   if (!is_device) {
-    src = static_cast<const double *>(pinned_device_address(U));
+    src = ctx->zerocopy ? static_cast<const double *>(pinned_device_address(U)) : nullptr;
     if (!src) {  // pageable: stage through device memory
       if ((rc = ensure_stage_buf(ctx, cnt))) return rc;
       CK(cudaMemcpyAsync(ctx->stage_buf, U, cnt * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
@@ -623,7 +625,8 @@ int cteno_get_state_all(cteno_ctx *ctx, double *U_out, int is_device) {
     CK(cudaGetLastError());
     return CTENO_OK;
   }
-  if (double *dst = static_cast<double *>(const_cast<void *>(pinned_device_address(U_out)))) {
+  if (double *dst = ctx->zerocopy ? static_cast<double *>(const_cast<void *>(pinned_device_address(U_out)))
+                                   : nullptr) {
     // page-locked output: the kernel writes it directly
     launch_permute_out_all(ctx->nv, lay_nvp(ctx->d), ctx->N, nmesh, ctx->d_mesh_off, ctx->d_grank, ctx->U, dst,
                            ctx->stream);
