@@ -459,6 +459,32 @@ def test_face_based_flux_is_bit_identical_to_per_cell_flux(precision):
         assert np.array_equal(out[0][1], out[1][1])
 
 
+def test_launch_and_host_access_switches_do_not_change_results(monkeypatch):
+    """CTENO_PDL (programmatic dependent launch of the stage kernels) and CTENO_ZEROCOPY (kernels
+    accessing page-locked host buffers directly in the batch-wide state calls) change how work is
+    launched and moved, not what is computed: states after a few steps are bit-identical."""
+    import torch
+    native = _native()
+    wls = W.quadrants_batch(3, seed=5, nmin=16, nmax=24)
+    meshes = [w.mesh for w in wls]
+    flat = np.concatenate([w.U0.ravel() for w in wls])
+    pin_in = torch.empty(flat.size, dtype=torch.float64, pin_memory=True).numpy()
+    pin_out = torch.empty(flat.size, dtype=torch.float64, pin_memory=True).numpy()
+    pin_in[:] = flat
+    results = []
+    for pdl, zc in (("1", "1"), ("0", "1"), ("1", "0")):
+        monkeypatch.setenv("CTENO_PDL", pdl)
+        monkeypatch.setenv("CTENO_ZEROCOPY", zc)
+        s = _solver(native, meshes, 2, degree=2, scheme=1, precision=1)
+        native.cteno_set_launch(s.ctx, 4097, 8192 + 128)
+        native.cteno_set_state_all(s.ctx, pin_in)
+        s.run(3)
+        native.cteno_get_state_all(s.ctx, pin_out)
+        results.append(pin_out.copy())
+        s.close()
+    assert np.array_equal(results[0], results[1]) and np.array_equal(results[0], results[2])
+
+
 def test_rejects_bad_calls_without_faulting():
     native = _native()
     wl = W.density_wave_2d(8)
