@@ -27,8 +27,8 @@ def _load():
     lib = C.CDLL(LIB)
     V = C.c_void_p
     lib.orc_create.restype = V
-    lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
-                               C.c_double, C.c_double, C.c_int, C.c_int, _dp, C.c_int, _ip, _dp,
+    lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                               C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _dp, C.c_int, _ip, _dp,
                                C.POINTER(C.c_int)]
     lib.orc_destroy.argtypes = [V]
     lib.orc_setup_all.argtypes = [V]
@@ -43,6 +43,11 @@ def _load():
     lib.orc_residual.argtypes = [V, _dp]
     lib.orc_residual_cells.argtypes = [V, C.c_int, _ip, _dp]
     lib.orc_reconstruct_cells.argtypes = [V, C.c_int, _ip]
+    lib.orc_residual_subset.argtypes = [V, C.c_int, _ip, _dp]
+    lib.orc_get_chi.argtypes = [V, _dp]
+    lib.orc_select.restype = C.c_uint
+    lib.orc_select.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int,
+                               _dp, _dp]
     lib.orc_info.argtypes = [V, _ip]
     lib.orc_get_geometry.argtypes = [V, V, V, V, V, V, V, V]
     lib.orc_get_face_points.argtypes = [V, V, V]
@@ -73,8 +78,17 @@ def num_threads() -> int:
     return int(_load().orc_num_threads())
 
 
-DEFAULTS = dict(degree=2, scheme=0, lam_gamma=1, C_T=1e-6, lambda1p=1e15, eps=1e-40, gamma=1.4, cfl=0.5,
-                guard=1)
+DEFAULTS = dict(degree=2, scheme=0, lam_gamma=1, ctenoz_form=0, C_T=1e-6, lambda1p=1e15, eps=1e-24,
+                gamma=1.4, cfl=0.5, guard=1)
+
+
+def select(SI, scheme=0, ctenoz_form=0, lam_gamma=1, C_T=1e-6, lambda1p=1e15, eps=1e-24):
+    """The oracle's selection (eqs. 19-23, Alg. 1 / 2) of one cell and variable from its smoothness
+    indicators SI[0] (central) .. SI[s_t - 1] (admissible directional stencils): (delta bits, chi)."""
+    SI = np.ascontiguousarray(SI, np.float64)
+    chi = np.empty(SI.size)
+    bits = _load().orc_select(scheme, ctenoz_form, lam_gamma, C_T, lambda1p, eps, SI.size, SI, chi)
+    return int(bits), chi
 
 
 class Oracle:
@@ -91,9 +105,9 @@ class Oracle:
         cells = np.ascontiguousarray(mesh.cells, dtype=np.int32)
         period = np.ascontiguousarray(mesh.period, dtype=np.float64)
         err = C.c_int(0)
-        self.h = self.lib.orc_create(self.dim, p["degree"], p["scheme"], p["lam_gamma"], p["C_T"], p["lambda1p"],
-                                     p["eps"], p["gamma"], p["cfl"], p["guard"], mesh.nverts, xyz,
-                                     mesh.ncells, cells, period, C.byref(err))
+        self.h = self.lib.orc_create(self.dim, p["degree"], p["scheme"], p["lam_gamma"], p["ctenoz_form"],
+                                     p["C_T"], p["lambda1p"], p["eps"], p["gamma"], p["cfl"], p["guard"],
+                                     mesh.nverts, xyz, mesh.ncells, cells, period, C.byref(err))
         if err.value:
             raise RuntimeError(f"oracle mesh set-up failed ({err.value})")
         info = np.zeros(8, np.int32)
@@ -145,6 +159,16 @@ class Oracle:
         rc = self.lib.orc_residual_cells(self.h, ids.size, ids, out)
         if rc:
             raise RuntimeError(f"oracle set-up failed ({rc})")
+        return out
+
+    def residual_subset(self, ids):
+        """Residual of the (set-up) cells `ids`, reconstructing them and their face neighbours
+        once each: [len(ids), nv]."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        out = np.empty((ids.size, self.nv))
+        rc = self.lib.orc_residual_subset(self.h, ids.size, ids, out)
+        if rc:
+            raise RuntimeError(f"oracle subset residual failed ({rc}): cells not set up")
         return out
 
     def reconstruct_cells(self, ids):
@@ -210,6 +234,13 @@ class Oracle:
     def smoothness_indicators(self):
         out = np.empty((self.ncells, self.nv, 1 + self.nf))
         self.lib.orc_get_si(self.h, out)
+        return out
+
+    def chi(self):
+        """chi_s of eq. 22 of the last reconstruction: [ncells, nv, 1 + nf] (central, then the
+        directional stencil of each local face; 0 where not admissible)."""
+        out = np.empty((self.ncells, self.nv, 1 + self.nf))
+        self.lib.orc_get_chi(self.h, out)
         return out
 
     def coefficients(self):

@@ -9,8 +9,8 @@
  * file includes nothing of the CUDA library: the two share no code.
  *
  * Every routine follows one passage of the paper, cited in its comment, in the paper's order
- * and notation. Readings where the paper is silent or garbled are marked "Reading:" and are the
- * same readings the CUDA library takes (they are listed in the design doc).
+ * and notation. Readings where the paper is silent or garbled are marked "Reading:"; the CUDA
+ * library takes the same readings, in code of its own.
  *
  * Parity pins (tests/test_oracle_*.py): quadrature exactness against the Dirichlet monomial
  * integral; least squares against numpy.linalg.lstsq; polynomial reproduction; mean
@@ -46,6 +46,7 @@ typedef struct {
   int dim, degree, scheme; /* scheme 0 = CTENO (Alg. 1), 1 = CTENOZ (Alg. 2) */
   int guard;               /* Reading: positivity fall-back to the cell mean */
   int lam_gamma;           /* Reading: 1 = gamma_s carries lambda_s (eq. 18), 0 = as printed */
+  int ctenoz_form;         /* Reading: 0 = CTENOZ measure as printed, 1 = WENO-Z form */
   double C_T, lambda1p, eps, gamma, cfl;
 } orc_params;
 
@@ -91,6 +92,7 @@ typedef struct {
   double *U, *Un, *Rres, *face; /* face: [ncells][nf][nq][nv] */
   uint8_t *flags;               /* [ncells][nv]: bit 0 central selected, bit 1+f directional f */
   double *SI;                   /* [ncells][nv][1+nf] smoothness indicators (debug) */
+  double *chi;                  /* [ncells][nv][1+nf] chi_s of eq. 22, 0 where inadmissible (debug) */
   double *coef;                 /* [ncells][nv][nk] final polynomial coefficients (debug) */
   int *stmask;                  /* [ncells]: bit 0 central, bit 1+f admissible directional f */
   int nguard;
@@ -758,6 +760,48 @@ static double pressure(const orc *o, const double *u) {
   return (o->p.gamma - 1.0) * (u[d + 1] - 0.5 * ke / u[0]);
 }
 
+/* Scale separation, smoothness measure and cut-off of one cell and one variable (Sec. 2.5-2.6).
+ * Stencil s = 0 is the central one (SI[0] = SI of p_1), s = 1 .. st-1 the admissible directional
+ * ones, so st is s_t. Linear coefficients of eq. 18: lambda_1 = 1 - 1/lambda_1' and
+ * lambda_s = (1 - lambda_1) / (s_t - 1).
+ *   CTENO (Alg. 1):  gamma_s = 1 / (SI_s + eps)^6.
+ *   CTENOZ (Alg. 2): tau = (sum_{s>=2} |SI_s - SI_1| / (s_t - 1))^6, gamma_s = 1 + tau / (SI_s + eps).
+ *     Reading (ctenoz_form = 1, not the printed form): the WENO-Z arrangement, with the power on
+ *     the ratio, tau = sum_{s>=2} |SI_s - SI_1| / (s_t - 1), gamma_s = 1 + (tau / (SI_s + eps))^6.
+ *   Reading (lam_gamma = 1): gamma_s is multiplied by lambda_s, the CWENO weight form of eq. 14;
+ *     without it lambda_1' could not influence the selection, which Tables 1 and 3 show it does.
+ * Then chi_s = gamma_s / sum_t gamma_t (eq. 22) and delta_s = 0 iff chi_s < C_T (eq. 23).
+ * Writes chi[0 .. st-1] and returns the delta bits (bit s = delta of stencil s). */
+static unsigned select_stencils(const orc_params *p, int st, const double *SI, double *chi) {
+  const double lam1 = 1.0 - 1.0 / p->lambda1p;
+  const double lams = (st > 1) ? (1.0 - lam1) / (st - 1) : 0.0;
+  double gam[1 + MAXNF], sum = 0.0;
+  if (p->scheme == 0) {
+    for (int s = 0; s < st; ++s) gam[s] = 1.0 / pow(SI[s] + p->eps, 6.0);
+  } else {
+    double tau = 0.0;
+    if (st > 1) {
+      double acc = 0.0;
+      for (int s = 1; s < st; ++s) acc += fabs(SI[s] - SI[0]);
+      tau = acc / (st - 1);
+      if (p->ctenoz_form == 0) tau = pow(tau, 6.0);
+    }
+    for (int s = 0; s < st; ++s) {
+      if (p->ctenoz_form == 0) gam[s] = 1.0 + tau / (SI[s] + p->eps);
+      else gam[s] = 1.0 + pow(tau / (SI[s] + p->eps), 6.0);
+    }
+  }
+  if (p->lam_gamma)
+    for (int s = 0; s < st; ++s) gam[s] *= (s == 0) ? lam1 : lams;
+  for (int s = 0; s < st; ++s) sum += gam[s];
+  unsigned bits = 0;
+  for (int s = 0; s < st; ++s) {
+    chi[s] = gam[s] / sum;                    /* eq. 22 */
+    if (!(chi[s] < p->C_T)) bits |= 1u << s;  /* eq. 23 */
+  }
+  return bits;
+}
+
 static void recon_cell(orc *o, int i, const double *U) {
   const int d = o->p.dim, nv = o->nv, nf = o->nf, nq = o->nq, nk = o->nk, n = o->ncells;
   orc_cell *c = o->cell[i];
@@ -805,30 +849,15 @@ static void recon_cell(orc *o, int i, const double *U) {
     for (int s = 0; s <= nf; ++s) o->SI[((size_t)i * nv + v) * (1 + nf) + s] = 0.0;
     o->SI[((size_t)i * nv + v) * (1 + nf)] = SI[0];
     for (int s = 0; s < na; ++s) o->SI[((size_t)i * nv + v) * (1 + nf) + 1 + adm[s]] = SI[1 + s];
-    /* scale separation: CTENO gamma_s = (SI_s + eps)^-6 (Alg. 1); CTENOZ
-     * tau = (sum_{s>=2} |SI_s - SI_1| / (s_t - 1))^6, gamma_s = 1 + tau / (SI_s + eps) (Alg. 2).
-     * Reading: with lam_gamma = 1 each gamma_s is multiplied by its linear coefficient lambda_s
-     * of eq. 18 (the CWENO weight form of eq. 14); without it lambda_1' could not influence the
-     * selection, which Tables 1 and 3 show it does. */
-    double gam[1 + MAXNF], sum = 0.0;
-    if (o->p.scheme == 0) {
-      for (int s = 0; s < st; ++s) gam[s] = 1.0 / pow(SI[s] + o->p.eps, 6.0);
-    } else {
-      double tau = 0.0;
-      if (st > 1) {
-        double acc = 0.0;
-        for (int s = 1; s < st; ++s) acc += fabs(SI[s] - SI[0]);
-        tau = pow(acc / (st - 1), 6.0);
-      }
-      for (int s = 0; s < st; ++s) gam[s] = 1.0 + tau / (SI[s] + o->p.eps);
-    }
-    if (o->p.lam_gamma)
-      for (int s = 0; s < st; ++s) gam[s] *= (s == 0) ? lam1 : lams;
-    for (int s = 0; s < st; ++s) sum += gam[s];
+    /* scale separation and cut-off (eqs. 19-23, Alg. 1 / Alg. 2) */
+    double chi[1 + MAXNF];
+    const unsigned dbits = select_stencils(&o->p, st, SI, chi);
+    for (int s = 0; s <= nf; ++s) o->chi[((size_t)i * nv + v) * (1 + nf) + s] = 0.0;
+    o->chi[((size_t)i * nv + v) * (1 + nf)] = chi[0];
+    for (int s = 0; s < na; ++s) o->chi[((size_t)i * nv + v) * (1 + nf) + 1 + adm[s]] = chi[1 + s];
     int delta[1 + MAXNF] = {0, 0, 0, 0, 0}, ndel = 0;
     for (int s = 0; s < st; ++s) {
-      double chi = gam[s] / sum;            /* eq. 22 */
-      delta[s] = (chi < o->p.C_T) ? 0 : 1;  /* eq. 23 */
+      delta[s] = (dbits >> s) & 1u;
       if (s > 0) ndel += delta[s];
     }
     /* final polynomial: p_1 if delta_1, else sum_{s>=2} delta_s p_s / sum delta_s */
@@ -1020,9 +1049,9 @@ double orc_step(orc *o, double dt) {
 /* ------------------------------------------------------------------------------------------ */
 /* Construction and accessors (ctypes interface)                                               */
 /* ------------------------------------------------------------------------------------------ */
-orc *orc_create(int dim, int degree, int scheme, int lam_gamma, double C_T, double lambda1p,
-                double eps, double gamma, double cfl, int guard, int nverts, const double *xyz, int ncells,
-                const int *cells, const double *period, int *err) {
+orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form, double C_T,
+                double lambda1p, double eps, double gamma, double cfl, int guard, int nverts,
+                const double *xyz, int ncells, const int *cells, const double *period, int *err) {
   *err = 0;
   if ((dim != 2 && dim != 3) || degree < 1 || degree > 3) {
     *err = -1;
@@ -1039,6 +1068,7 @@ orc *orc_create(int dim, int degree, int scheme, int lam_gamma, double C_T, doub
   o->p.cfl = cfl;
   o->p.guard = guard;
   o->p.lam_gamma = lam_gamma;
+  o->p.ctenoz_form = ctenoz_form;
   o->nverts = nverts;
   o->ncells = ncells;
   o->nv = dim + 2;
@@ -1073,6 +1103,7 @@ orc *orc_create(int dim, int degree, int scheme, int lam_gamma, double C_T, doub
   o->face = (double *)calloc(n * o->nf * o->nq * o->nv, sizeof(double));
   o->flags = (uint8_t *)calloc(n * o->nv, 1);
   o->SI = (double *)calloc(n * o->nv * (1 + o->nf), sizeof(double));
+  o->chi = (double *)calloc(n * o->nv * (1 + o->nf), sizeof(double));
   o->stmask = (int *)calloc(n, sizeof(int));
   o->coef = (double *)calloc(n * o->nv * o->nk, sizeof(double));
   return o;
@@ -1092,13 +1123,23 @@ int orc_setup_all(orc *o) {
   return bad;
 }
 
-/* Set-up of a subset of cells only (for sampled checks on large meshes). */
+/* Set-up of a subset of cells only (for sampled checks on large meshes); parallel over the
+ * distinct cells of the list. */
 int orc_setup_cells(orc *o, int count, const int *ids) {
-  for (int k = 0; k < count; ++k) {
-    int rc = cell_setup(o, ids[k]);
-    if (rc) return rc;
+  uint8_t *want = (uint8_t *)calloc(o->ncells, 1);
+  for (int k = 0; k < count; ++k) want[ids[k]] = 1;
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int i = 0; i < o->ncells; ++i) {
+    if (!want[i]) continue;
+    int rc = cell_setup(o, i);
+    if (rc) {
+#pragma omp critical
+      bad = rc;
+    }
   }
-  return 0;
+  free(want);
+  return bad;
 }
 
 void orc_destroy(orc *o) {
@@ -1115,7 +1156,7 @@ void orc_destroy(orc *o) {
   free(o->cv); free(o->X); free(o->vol); free(o->cen); free(o->Jinv); free(o->detJ);
   free(o->nbr); free(o->nbrf); free(o->area); free(o->nrm); free(o->fq);
   free(o->v2c_off); free(o->v2c); free(o->qlam); free(o->qw);
-  free(o->U); free(o->Un); free(o->Rres); free(o->face); free(o->flags); free(o->SI);
+  free(o->U); free(o->Un); free(o->Rres); free(o->face); free(o->flags); free(o->SI); free(o->chi);
   free(o->stmask);
   free(o->coef);
   free(o);
@@ -1148,6 +1189,39 @@ int orc_residual_cells(orc *o, int count, const int *ids, double *R_out) {
     residual_cell(o, i, R_out + (size_t)k * o->nv);
   }
   return 0;
+}
+
+/* Residual of a subset of cells, reconstructing each cell of the subset and of its face
+ * neighbours once (parallel over cells). Cells must be set up (orc_setup_cells), their face
+ * neighbours included. R_out: [count][nv]. */
+int orc_residual_subset(orc *o, int count, const int *ids, double *R_out) {
+  const int nf = o->nf;
+  uint8_t *need = (uint8_t *)calloc(o->ncells, 1);
+  for (int k = 0; k < count; ++k) {
+    need[ids[k]] = 1;
+    for (int f = 0; f < nf; ++f) {
+      int j = o->nbr[ids[k] * nf + f];
+      if (j >= 0) need[j] = 1;
+    }
+  }
+  int nn = 0;
+  for (int i = 0; i < o->ncells; ++i) nn += need[i];
+  int *list = (int *)malloc(sizeof(int) * (nn ? nn : 1));
+  nn = 0;
+  for (int i = 0; i < o->ncells; ++i)
+    if (need[i]) list[nn++] = i;
+  free(need);
+  int bad = 0;
+  for (int k = 0; k < nn; ++k)
+    if (!o->cell[list[k]] || !o->cell[list[k]]->ready) bad = -8;
+  if (!bad) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int k = 0; k < nn; ++k) recon_cell(o, list[k], o->U);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < count; ++k) residual_cell(o, ids[k], R_out + (size_t)k * o->nv);
+  }
+  free(list);
+  return bad;
 }
 
 /* Reconstruct a subset of cells (face states, flags and SI are then readable for them). */
@@ -1221,6 +1295,9 @@ void orc_get_flags(const orc *o, uint8_t *out) { memcpy(out, o->flags, (size_t)o
 void orc_get_si(const orc *o, double *out) {
   memcpy(out, o->SI, sizeof(double) * o->ncells * o->nv * (1 + o->nf));
 }
+void orc_get_chi(const orc *o, double *out) {
+  memcpy(out, o->chi, sizeof(double) * o->ncells * o->nv * (1 + o->nf));
+}
 void orc_get_coeffs(const orc *o, double *out) {
   memcpy(out, o->coef, sizeof(double) * o->ncells * o->nv * o->nk);
 }
@@ -1238,6 +1315,20 @@ void orc_get_exponents(const orc *o, int *ex) {
 double orc_psibar(const orc *o, int k) { return o->psibar[k]; }
 
 /* Exposed pieces for the pin tests. */
+/* The selection of one cell and variable from given indicators (see select_stencils): SI[st],
+ * chi_out[st]; returns the delta bits. */
+unsigned orc_select(int scheme, int ctenoz_form, int lam_gamma, double C_T, double lambda1p, double eps,
+                    int st, const double *SI, double *chi_out) {
+  orc_params p;
+  memset(&p, 0, sizeof(p));
+  p.scheme = scheme;
+  p.ctenoz_form = ctenoz_form;
+  p.lam_gamma = lam_gamma;
+  p.C_T = C_T;
+  p.lambda1p = lambda1p;
+  p.eps = eps;
+  return select_stencils(&p, st, SI, chi_out);
+}
 void orc_hllc(const orc *o, const double *uL, const double *uR, const double *n, double *F) {
   hllc(o, uL, uR, n, F);
 }

@@ -56,7 +56,7 @@ def test_basis_means_are_dirichlet_integrals(dim, degree):
         assert abs(pb - ref) < 1e-15
 
 
-@pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 6)])
+@pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 6), (3, 3, 6)])
 def test_lsq_matrix_and_solution(dim, degree, n):
     """A_mk = int_{V'_m} phi_k (eq. 10) from exact integrals over the mapped neighbour; the
     solution of eq. 12 equals numpy's least-squares solution of A a = b."""
@@ -163,7 +163,7 @@ def _poly_state(mesh, polys):
     return np.array([[X.poly_cell_average(p, V[c]) for c in range(mesh.ncells)] for p in polys])
 
 
-@pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 6)])
+@pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 6), (3, 3, 5)])
 def test_linear_fields_reproduced_by_whole_reconstruction(dim, degree, n):
     """A linear field is reproduced exactly by every stencil, hence by any CTENO selection:
     the face-point states equal the field at the face points."""
@@ -182,10 +182,13 @@ def test_linear_fields_reproduced_by_whole_reconstruction(dim, degree, n):
     fs = o.face_states()
     fq, _ = o.face_points()
     interior = _interior_cells(o)
+    # round-off of the semi-normal equations of eq. 12 grows as cond(A)^2: the one-sided cubic
+    # stencils of a bounded tetrahedral mesh reach cond(A) ~ 1e2..1e3
+    tol = 1e-10 if (dim, degree) == (3, 3) else 1e-12
     for v in range(nv):
         ref = X.poly_eval(polys[v], fq)
         err = np.abs(fs[..., v] - ref)[interior]
-        assert err.max() < 1e-12, (v, err.max())
+        assert err.max() < tol, (v, err.max())
 
 
 def _interior_cells(o):
@@ -193,7 +196,7 @@ def _interior_cells(o):
     return np.arange(o.ncells)
 
 
-@pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 6)])
+@pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 6), (3, 3, 5)])
 def test_degree_r_fields_reproduced_by_central_polynomial(dim, degree, n):
     """A polynomial of degree r is reproduced by the central least squares (eq. 12); with the
     cut-off C_T = 0 the central stencil is always kept and p_1 = p_opt + O(1/lambda_1')."""
@@ -212,12 +215,13 @@ def test_degree_r_fields_reproduced_by_central_polynomial(dim, degree, n):
     fs = o.face_states()
     fq, _ = o.face_points()
     assert (o.flags() & 1).all()
+    tol = 1e-9 if (dim, degree) == (3, 3) else 1e-11   # cond(A)^2 round-off, as above
     for v in range(nv):
         ref = X.poly_eval(polys[v], fq)
-        assert np.abs(fs[..., v] - ref).max() < 1e-11
+        assert np.abs(fs[..., v] - ref).max() < tol
 
 
-@pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 6)])
+@pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 6), (3, 3, 6)])
 def test_reconstruction_preserves_cell_mean(dim, degree, n):
     """eq. 4: the cell average of the final polynomial equals U_i, for any selection."""
     wl = W.density_wave_2d(n) if dim == 2 else W.density_wave_3d(n)
@@ -341,10 +345,15 @@ def test_hllc_resolves_isolated_contact_and_supersonic_upwinding(mk):
 # --------------------------------------------------------------------------------------------
 # Selection (eqs. 19-23, Alg. 1, Alg. 2)
 # --------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("scheme", [0, 1], ids=["CTENO", "CTENOZ"])
-def test_selection_at_a_contact(scheme):
+@pytest.mark.parametrize("scheme,form,eps", [(0, 0, 1e-24), (1, 1, 1e-24), (1, 0, 1e-40), (1, 0, 1e-24)],
+                         ids=["CTENO", "CTENOZ-wenoz", "CTENOZ-eps40", "CTENOZ"])
+def test_selection_at_a_contact(scheme, form, eps):
     """A density step: cells whose central stencil straddles it drop the central stencil and
-    keep only directional stencils lying on one side; far from it the central one is kept."""
+    keep only directional stencils lying on one side; far from it the central one is kept.
+    The printed CTENOZ measure is not scale invariant: it drops the central stencil only where
+    tau / eps exceeds about (lambda_1'/C_T) (eqs. 18-23), so at eps = 1e-24 it detects this step
+    in the straddling cells with the largest indicators only (checked: no false drops, every
+    selected stencil on one side, some cells detected)."""
     mesh = W.tri_mesh(16, 8, periodic=False, jitter=0.1, seed=3)
     g_cen = W.cell_centroids(mesh)
 
@@ -356,23 +365,29 @@ def test_selection_at_a_contact(scheme):
         return prim
     # cell averages of a step the mesh does not follow: use cell-centroid states instead
     U = W.primitive_to_conserved(f(g_cen)).T.copy()
-    o = Oracle(mesh, degree=2, scheme=scheme)
+    o = Oracle(mesh, degree=2, scheme=scheme, ctenoz_form=form, eps=eps)
     o.set_state(U)
     o.residual()
     fl = o.flags()[:, 0]
     side = g_cen[:, 0] < 0.5
+    partial = (scheme, form, eps) == (1, 0, 1e-24)
+    detected = 0
     for i in range(mesh.ncells):
         central, dirm, dok = o.stencil(i)
         straddles = len(set(side[central]) | {side[i]}) > 1
         if not straddles:
             assert fl[i] & 1, i
             continue
+        if partial and fl[i] & 1:
+            continue
         assert not (fl[i] & 1), i
         assert fl[i] != 0
+        detected += 1
         for f in range(o.nf):
             if fl[i] & (1 << (1 + f)):
                 mem = central[dirm[f][dirm[f] >= 0]]
                 assert np.all(side[mem] == side[i]), (i, f)
+    assert detected >= 20
 
 
 @pytest.mark.parametrize("scheme", [0, 1], ids=["CTENO", "CTENOZ"])

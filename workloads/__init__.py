@@ -10,7 +10,7 @@ Randomness comes from SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudora
 generators", OOPSLA 2014), written out here with numpy uint64 arithmetic so the streams are
 identical on every machine and numpy version.
 
-Workloads (sizes of the paper's experiments, Sec. 3; recipes in the design doc):
+Workloads (sizes of the paper's experiments, Sec. 3):
   * density_wave_2d  : periodic unit square, rho = 1 + 0.2 sin(2 pi (x+y)), u = v = 1, p = 1
                        (Sec. 3.1.1, the order test).
   * shock_tube_2d    : [0,1]x[0,0.25], Sod states split at x = 0.5 (Sec. 3.2).
