@@ -1,20 +1,26 @@
 #!/usr/bin/env python
 """Throughput of the CTENO / CTENOZ hot path on one GB300: Mcell-RK-stage/s.
 
-Workload: the 2D shock tube on [0,1]x[0,0.25], 512x128 squares split into triangles with a
-seeded diagonal, interior vertices jittered +-0.1h (131072 cells), Sod states, transmissive
-boundaries, CFL 0.4. A step is one SSP-RK3 step (three stages of reconstruction + flux/update,
-with the CFL time step), i.e. the whole hot path once; the metric counts cells x 3 stages.
+Headline workload: the 3D blast on the unit cube, 96^3 cubes split into 6 tetrahedra each
+(5308416 cells), vertices jittered +-0.08h, rho = 1, u = 0, p = 10 inside r < 0.2 and 0.1
+outside, transmissive boundaries, CFL 0.3, CTENO at degree 3 (20-coefficient cubic), mixed
+precision (FP32 reconstruction and flux on FP64-accurate differences, FP64 accumulation and
+update): the largest configuration that runs on one GPU. A step is one SSP-RK3 step (three
+stages of reconstruction + flux/update, with the CFL time step), i.e. the whole hot path once;
+the metric counts cells x 3 stages.
 
-The headline line is the mixed-precision path (FP32 reconstruction and flux, FP64 accumulation)
-with CTENO at degree 2; `variants` gives every scheme / degree / precision combination of the
-workload. L2 (129 MB) is flushed between timed steps by a 256 MB write outside the timed events.
+`variants` times the other configurations with the same line fields, each with its own roofline
+object: the blast in FP64; the 2D shock tube (512x128 squares -> 131072 triangles, Sod, CFL 0.4)
+with CTENO and CTENOZ at degree 2 and 3; the 3D density wave (64^3 x 6 tetrahedra, CTENO degree
+2); the batch of 64 four-quadrant Riemann problems (1.74M triangles, CTENOZ degree 2, one launch
+per kernel for all meshes) -- each in both precisions. L2 (129 MB) is flushed between timed steps
+by a 256 MB write outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload shock_tube_2d|density_wave_3d_64|blast_3d_96|batch_2d] [--profile]
+                  [--workload blast_3d_96|shock_tube_2d|density_wave_3d_64|batch_2d]
+                  [--variants all|none] [--profile]
 
-The default workload is the shock tube; the others are the 3D and batched configurations, measured
-with the same line format (--profile runs only warm-up + steps of the headline variant, for ncu).
+--profile runs only warm-up + steps of the headline (a short command for ncu).
 
 Under torchrun each rank advances its own replica of the workload (the path does not shard
 within a mesh: replicas only); value = cells x stages of all ranks / max over ranks of the time.
@@ -40,17 +46,19 @@ METRIC = "Mcell-RK-stage/s (deg 2/3, 2D tri & 3D tet), FP32-mixed vs FP64 on one
 UNIT = "Mcell-RK-stage/s"
 SCHEMES = {0: "CTENO", 1: "CTENOZ"}
 PRECISIONS = {0: "fp64", 1: "mixed"}
+WORKLOADS = ["blast_3d_96", "shock_tube_2d", "density_wave_3d_64", "batch_2d"]
 
 
 class Case:
     """A workload: meshes + initial states + the scheme it is defined with."""
 
-    def __init__(self, name, description, meshes, states, dim, scheme, degree, cfl, variants):
+    def __init__(self, name, description, meshes, states, dim, scheme, degree, cfl, variants, sample_centre):
         self.name, self.description = name, description
         self.meshes, self.states, self.dim = meshes, states, dim
         self.scheme, self.degree, self.cfl = scheme, degree, cfl
         self.variants = variants          # (scheme, degree) pairs timed in both precisions
         self.ncells = sum(m.ncells for m in meshes)
+        self.sample_centre = sample_centre  # centre of the oracle's sub-box sample (first mesh)
 
 
 def make_case(name, n=0):
@@ -59,27 +67,26 @@ def make_case(name, n=0):
         wl = W.shock_tube_2d(512, 128)
         return Case(name, "2D shock tube [0,1]x[0,0.25], 512x128 squares -> 131072 triangles, jitter 0.1h, "
                     "Sod states, transmissive, CFL 0.4", [wl.mesh], [wl.U0], 2, 0, 2, 0.4,
-                    [(0, 2), (0, 3), (1, 2), (1, 3)])
+                    [(0, 2), (0, 3), (1, 2), (1, 3)], (0.5, 0.125))
     if name == "density_wave_3d_64":
         n = n or 64
         wl = W.density_wave_3d(n)
         return Case(name, f"3D periodic unit cube, {n}^3 cubes x 6 tetrahedra -> {wl.mesh.ncells} cells, "
-                    "jitter 0.08h, density wave, CFL 0.5", [wl.mesh], [wl.U0], 3, 0, 2, 0.5, [(0, 2)])
+                    "jitter 0.08h, density wave, CFL 0.5", [wl.mesh], [wl.U0], 3, 0, 2, 0.5, [(0, 2)],
+                    (0.5, 0.5, 0.5))
     if name == "blast_3d_96":
         n = n or 96
         wl = W.blast_3d(n)
         return Case(name, f"3D unit cube, {n}^3 cubes x 6 tetrahedra -> {wl.mesh.ncells} cells, jitter 0.08h, "
-                    "blast p=10 in r<0.2, transmissive, CFL 0.3", [wl.mesh], [wl.U0], 3, 0, 3, 0.3, [(0, 3)])
+                    "blast p=10 in r<0.2, transmissive, CFL 0.3", [wl.mesh], [wl.U0], 3, 0, 3, 0.3, [(0, 3)],
+                    (0.7, 0.5, 0.5))
     if name == "batch_2d":
         wls = W.quadrants_batch(64, seed=0)
         return Case(name, f"64 independent triangle meshes, side log-uniform in [16,256] -> "
                     f"{sum(w.mesh.ncells for w in wls)} cells, four-quadrant Riemann states, CFL 0.4, "
                     "one launch per kernel for all meshes", [w.mesh for w in wls], [w.U0 for w in wls],
-                    2, 1, 2, 0.4, [(1, 2)])
+                    2, 1, 2, 0.4, [(1, 2)], (0.5, 0.5))
     raise ValueError(name)
-
-
-HEADLINE = dict(precision=1)
 
 
 def variant_name(scheme, degree, precision):
@@ -89,21 +96,22 @@ def variant_name(scheme, degree, precision):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--variant-steps", type=int, default=60)
-    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variant-seconds", type=float, default=1.0,
+                    help="timed work per variant (steps chosen from the warm-up's step time)")
+    ap.add_argument("--variants", choices=["all", "none"], default="all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="shock_tube_2d",
-                    choices=["shock_tube_2d", "density_wave_3d_64", "blast_3d_96", "batch_2d"])
+    ap.add_argument("--workload", default="blast_3d_96", choices=WORKLOADS)
     ap.add_argument("--n", type=int, default=0,
                     help="override the mesh size of a 3D workload (cubes per side), e.g. for ncu")
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
+                    help="precision of the headline (1 = mixed, 0 = FP64)")
     ap.add_argument("--launch", default="",
                     help="R,F launch values (cteno_set_launch convention) instead of autotuning")
     ap.add_argument("--profile", action="store_true",
-                    help="only run the headline variant (warm-up + steps, no timing extras): a short "
-                         "command for ncu")
+                    help="only run the headline (warm-up + steps, no timing extras): a short command for ncu")
     return ap.parse_args()
 
 
@@ -219,9 +227,9 @@ def alu_peak(native):
     return {"fp64_tflops": round(f64, 3), "fp32_tflops": round(f32, 2)}
 
 
-def recon_kernel_name(dim, degree, scheme, launch):
-    """Name of the mixed-path reconstruction kernel a launch value selects."""
-    args = f"{dim},{degree},float,{SCHEMES[scheme]}"
+def recon_kernel_name(dim, degree, scheme, precision, launch):
+    """Name of the reconstruction kernel a launch value selects."""
+    args = f"{dim},{degree},{'float' if precision else 'double'},{SCHEMES[scheme]}"
     if launch in (4096, 4097):
         return f"recon_halo_kernel<{args},{'one-tile' if launch == 4097 else 'persistent'}> x128"
     if launch >= 3072:
@@ -235,7 +243,7 @@ def recon_kernel_name(dim, degree, scheme, launch):
     return f"recon_kernel<{args}> x{launch}"
 
 
-def ncu_traffic(variant):
+def ncu_traffic(key):
     """DRAM bytes per reconstruction launch from the committed ncu capture, if the kernel source
     has not changed since."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -245,14 +253,13 @@ def ncu_traffic(variant):
     src = open(os.path.join(ROOT, "paper_2312_17042_gb300", "csrc", "recon.cuh"), "rb").read()
     if d.get("recon_cuh_sha256") != hashlib.sha256(src).hexdigest():
         return None
-    return d.get("bytes_per_launch", {}).get(variant)
+    return d.get("bytes_per_launch", {}).get(key)
 
 
 def make_solver(native, case, scheme, degree, precision, stream):
     s = native.Solver(case.meshes, case.dim, degree=degree, scheme=scheme, precision=precision,
                       stream=stream, cfl=case.cfl)
-    for k, U in enumerate(case.states):
-        s.set_state(U, k)
+    native.cteno_set_state_all(s.ctx, case.states)
     return s
 
 
@@ -276,6 +283,95 @@ def time_steps(native, s, steps, warmup, flush, torch, kernel_times=False):
     return ms, (np.array(kms) if kernel_times else None)
 
 
+def roofline_of(case, scheme, degree, precision, launch, stats, recon_ms, peaks, peak_kind, alu):
+    """Roofline object of the reconstruction kernel (the dominant kernel of every workload): the
+    mixed path against the measured HBM copy bandwidth, the FP64 path against the measured FP64
+    FMA rate (it is bound by the FP64 pipe), both from algorithmic bytes / FLOPs per launch over
+    the mean launch time measured with CUDA events inside the replayed step graph."""
+    name = recon_kernel_name(case.dim, degree, scheme, precision, launch)
+    gbs = stats[0] / (recon_ms * 1e-3) / 1e9
+    key = f"{case.name}:{variant_name(scheme, degree, precision)}:{launch}"
+    if precision == 1 or alu is None:
+        return {"kernel": name, "bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(key),
+                "algorithmic_bytes_per_launch": stats[0], "launch_ms": round(recon_ms, 5),
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind}, of measured)"}
+    tfl = stats[2] / (recon_ms * 1e-3) / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": round(tfl, 4), "peak": alu["fp64_tflops"],
+            "unit": "TFLOP/s (FP64 FMA)", "frac": round(tfl / alu["fp64_tflops"], 4), "traffic": ncu_traffic(key),
+            "algorithmic_flops_per_launch": stats[2], "launch_ms": round(recon_ms, 5),
+            "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4),
+            "peak_source": "FP64 FMA rate measured on this GPU by cteno_measure_alu_peak (nominal 1.25 TFLOP/s)"}
+
+
+def measure(native, case, scheme, degree, precision, stream, flush, torch, dist, world, steps, warmup,
+            peaks, peak_kind, alu, launch=None, clocks=False, e2e=False, seconds=None):
+    """One (workload, scheme, degree, precision) measurement: set-up, autotune (or the given
+    launch), warm-up, the timed steps, a kernel-timing pass; optionally the clock record and the
+    end-to-end number through the C ABI with host buffers."""
+    s = make_solver(native, case, scheme, degree, precision, stream)
+    if launch is None:
+        launch = native.cteno_autotune(s.ctx)
+    else:
+        native.cteno_set_launch(s.ctx, *launch)
+    native.cteno_set_state_all(s.ctx, case.states)
+    stats = native.cteno_kernel_stats(s.ctx)
+    if seconds is not None:   # variants: choose the step count from one warm-up step's time
+        flush.zero_()
+        t0 = time.perf_counter()
+        s.run(1)
+        torch.cuda.synchronize()
+        one = time.perf_counter() - t0
+        steps = int(max(5, min(200, seconds / max(one, 1e-6))))
+    sampler = ClockSampler(torch.cuda.current_device()) if clocks else None
+    dist.barrier()
+    torch.cuda.synchronize()
+    ms, _ = time_steps(native, s, steps, warmup, flush, torch)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = sampler.stop() if sampler else None
+    guard = s.sync()
+    total_ms = dist.max(sum(ms), device="cuda")
+    out = {"value": round(whole_job_value(world, case.ncells, steps, total_ms), 2), "steps": steps,
+           "ms_per_step": round(total_ms / steps, 5), "launch": list(launch), "positivity_guard_cells": int(guard)}
+    native.cteno_set_timing(s.ctx, True)
+    _, kms = time_steps(native, s, max(5, min(steps, 50)), 2, flush, torch, kernel_times=True)
+    native.cteno_set_timing(s.ctx, False)
+    recon_ms, flux_ms = float(kms[:, 0].mean()) / 3.0, float(kms[:, 1].mean()) / 3.0
+    out["roofline"] = roofline_of(case, scheme, degree, precision, launch[0], stats, recon_ms, peaks, peak_kind, alu)
+    out["flux"] = {"launch_ms": round(flux_ms, 5), "algorithmic_bytes_per_launch": stats[1],
+                   "achieved_gbs": round(stats[1] / (flux_ms * 1e-3) / 1e9, 1)}
+    out["gpu_launches"] = 3 * (1 + (2 if launch[1] >= 8192 else 1)) * steps
+    if clk is not None:
+        out["clocks"] = clk
+    if e2e:
+        nv = case.dim + 2
+        pinned = torch.empty(nv * case.ncells, dtype=torch.float64, pin_memory=True).numpy()
+        outs = torch.empty(nv * case.ncells, dtype=torch.float64, pin_memory=True).numpy()
+        native.cteno_get_state_all(s.ctx, pinned)
+        n_e2e = max(5, min(steps, 50))
+        torch.cuda.synchronize()
+        t_total = 0.0
+        for it in range(n_e2e + 2):
+            flush.zero_()
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            native.cteno_set_state_all(s.ctx, pinned)
+            s.run(1)
+            native.cteno_get_state_all(s.ctx, outs)
+            b_.record()
+            b_.synchronize()
+            if it >= 2:
+                t_total += a.elapsed_time(b_)
+        t_total = dist.max(t_total, device="cuda")
+        out["e2e"] = {"value": round(whole_job_value(world, case.ncells, n_e2e, t_total), 2), "unit": UNIT,
+                      "h2d_bytes_per_step": int(pinned.nbytes), "d2h_bytes_per_step": int(outs.nbytes),
+                      "steps": n_e2e,
+                      "api": "cteno_set_state_all(host) + cteno_run(1) + cteno_get_state_all(host), pinned buffers"}
+    s.close()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -286,137 +382,83 @@ def run_ours(args, rank, world, local):
     dist = Dist(world, "nccl")
     stream = torch.cuda.current_stream().cuda_stream
     case = make_case(args.workload, args.n)
-    ncells = case.ncells
-    nv = case.dim + 2
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    peaks, peak_kind = measured_peaks()
+    h = dict(scheme=case.scheme, degree=case.degree, precision=args.precision)
+    launch = tuple(int(x) for x in args.launch.split(",")) if args.launch else None
 
-    # headline ---------------------------------------------------------------------------------
-    h = dict(scheme=case.scheme, degree=case.degree, precision=HEADLINE["precision"])
-    s = make_solver(native, case, h["scheme"], h["degree"], h["precision"], stream)
-    if args.launch:
-        blocks = tuple(int(x) for x in args.launch.split(","))
-        native.cteno_set_launch(s.ctx, *blocks)
-    else:
-        blocks = native.cteno_autotune(s.ctx)
-    if args.profile:
+    if args.profile:   # headline only: warm-up + steps, nothing else (a short command for ncu)
+        s = make_solver(native, case, h["scheme"], h["degree"], h["precision"], stream)
+        if launch:
+            native.cteno_set_launch(s.ctx, *launch)
+        else:
+            launch = native.cteno_autotune(s.ctx)
+            native.cteno_set_state_all(s.ctx, case.states)
         time_steps(native, s, args.steps, args.warmup, flush, torch)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_case": args.workload, "blocks": blocks, "guard": s.sync()}))
+        print(json.dumps({"profile_case": args.workload, "launch": launch, "guard": s.sync()}))
         s.close()
         dist.close()
         return
-    stats = native.cteno_kernel_stats(s.ctx)
-    clocks = ClockSampler(local)
-    dist.barrier()
-    torch.cuda.synchronize()
-    # the step graph as a user runs it (no timing nodes between its kernels)
-    ms, _ = time_steps(native, s, args.steps, args.warmup, flush, torch)
-    torch.cuda.synchronize()
-    dist.barrier()
-    clk = clocks.stop()
-    guard = s.sync()
-    total_ms = dist.max(sum(ms), device="cuda")
-    ms_per_step = total_ms / args.steps
-    value = whole_job_value(world, ncells, args.steps, total_ms)
-    # per-kernel durations: a separate pass of the step graph with event-record nodes between its
-    # kernels (which also serialises them)
-    native.cteno_set_timing(s.ctx, True)
-    _, kms = time_steps(native, s, max(10, min(args.steps, 100)), 2, flush, torch, kernel_times=True)
-    recon_ms_launch = float(kms[:, 0].mean()) / 3.0
-    flux_ms_launch = float(kms[:, 1].mean()) / 3.0
-    peaks, peak_kind = measured_peaks()
-    achieved = stats[0] / (recon_ms_launch * 1e-3) / 1e9
-    hv = f"{args.workload}:" + variant_name(**h) + f":{blocks[0]}"
-    roofline = {"kernel": recon_kernel_name(case.dim, h["degree"], h["scheme"], blocks[0]), "bound": "hbm",
-                "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(hv),
-                "algorithmic_bytes_per_launch": stats[0], "launch_ms": round(recon_ms_launch, 5),
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
-                "flux_kernel": {"achieved_gbs": round(stats[1] / (flux_ms_launch * 1e-3) / 1e9, 1),
-                                "launch_ms": round(flux_ms_launch, 5),
-                                "algorithmic_bytes_per_launch": stats[1]}}
-    native.cteno_set_timing(s.ctx, False)
 
-    # end to end through the C ABI with host buffers -------------------------------------------
-    # every mesh's state in one pinned host buffer, moved by the batch-wide calls
-    pinned = torch.empty(nv * ncells, dtype=torch.float64, pin_memory=True).numpy()
-    outs = torch.empty(nv * ncells, dtype=torch.float64, pin_memory=True).numpy()
-    native.cteno_get_state_all(s.ctx, pinned)
-    n_e2e = max(5, min(args.steps, 50))
-    torch.cuda.synchronize()
-    t_total = 0.0
-    for it in range(n_e2e + 2):
-        flush.zero_()
-        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        native.cteno_set_state_all(s.ctx, pinned)
-        s.run(1)
-        native.cteno_get_state_all(s.ctx, outs)
-        b_.record()
-        b_.synchronize()
-        if it >= 2:
-            t_total += a.elapsed_time(b_)
-    t_total = dist.max(t_total, device="cuda")
-    e2e = {"value": round(whole_job_value(world, ncells, n_e2e, t_total), 2), "unit": UNIT,
-           "h2d_bytes_per_step": int(pinned.nbytes), "d2h_bytes_per_step": int(outs.nbytes), "steps": n_e2e,
-           "api": "cteno_set_state_all(host) + cteno_run(1) + cteno_get_state_all(host), pinned buffers"}
-    s.close()
+    alu = alu_peak(native)
+    head = measure(native, case, h["scheme"], h["degree"], h["precision"], stream, flush, torch, dist, world,
+                   args.steps, args.warmup, peaks, peak_kind, alu, launch=launch, clocks=True, e2e=True)
 
-    # variants: every timed (scheme, degree) of the workload in both precisions -------------------
+    # variants: the headline workload in the other precision, then every other configuration ----
     variants = {}
-    alu = None
-    if not args.no_variants:
-        alu = alu_peak(native)
-        for scheme, degree in case.variants:
-            for precision in (1, 0):
-                name = variant_name(scheme, degree, precision)
-                sv = make_solver(native, case, scheme, degree, precision, stream)
-                native.cteno_autotune(sv.ctx)
-                st = native.cteno_kernel_stats(sv.ctx)
-                vms, _ = time_steps(native, sv, args.variant_steps, 3, flush, torch)
-                native.cteno_set_timing(sv.ctx, True)
-                _, vk = time_steps(native, sv, max(5, args.variant_steps // 2), 1, flush, torch, kernel_times=True)
-                tot = dist.max(sum(vms), device="cuda")
-                r_ms = float(vk[:, 0].mean()) / 3
-                entry = {"value": round(whole_job_value(world, ncells, args.variant_steps, tot), 2),
-                         "ms_per_step": round(tot / args.variant_steps, 4),
-                         "recon_ms_per_launch": round(r_ms, 5),
-                         "flux_ms_per_launch": round(float(vk[:, 1].mean()) / 3, 5)}
-                if precision == 1:
-                    entry["recon_gbs"] = round(st[0] / (r_ms * 1e-3) / 1e9, 1)
-                    entry["recon_hbm_frac"] = round(entry["recon_gbs"] / peaks["hbm_gbs"], 4)
-                else:
-                    tfl = st[2] / (r_ms * 1e-3) / 1e12
-                    entry["recon_fp64_tflops"] = round(tfl, 3)
-                    entry["recon_fp64_alu_frac"] = round(tfl / alu["fp64_tflops"], 4)
-                variants[name] = entry
-                sv.close()
-        for scheme, degree in case.variants:
-            m, f = variants[variant_name(scheme, degree, 1)], variants[variant_name(scheme, degree, 0)]
-            m["speedup_vs_fp64"] = round(m["value"] / f["value"], 2)
+    if args.variants == "all":
+        plan = [(case, sc, dg, pr) for sc, dg in case.variants for pr in (1, 0)
+                if (sc, dg, pr) != (h["scheme"], h["degree"], h["precision"])]
+        for other in WORKLOADS:
+            if other != case.name:
+                plan.append((other, None, None, None))
+        for item in plan:
+            if isinstance(item[0], str):
+                oc = make_case(item[0])
+                for sc, dg in oc.variants:
+                    for pr in (1, 0):
+                        variants[f"{oc.name}:{variant_name(sc, dg, pr)}"] = measure(
+                            native, oc, sc, dg, pr, stream, flush, torch, dist, world, 0, 3, peaks, peak_kind,
+                            alu, seconds=args.variant_seconds)
+                for sc, dg in oc.variants:
+                    m = variants[f"{oc.name}:{variant_name(sc, dg, 1)}"]
+                    m["speedup_vs_fp64"] = round(m["value"] / variants[f"{oc.name}:{variant_name(sc, dg, 0)}"]["value"], 2)
+                    m["config"] = oc.description
+                del oc
+            else:
+                oc, sc, dg, pr = item
+                variants[f"{oc.name}:{variant_name(sc, dg, pr)}"] = measure(
+                    native, oc, sc, dg, pr, stream, flush, torch, dist, world, 0, 3, peaks, peak_kind, alu,
+                    seconds=args.variant_seconds)
+    fp64_same = variants.get(f"{case.name}:{variant_name(h['scheme'], h['degree'], 0)}")
 
-    # CPU baseline: the oracle on the host cores ---------------------------------------------------
+    # CPU baseline: the oracle on the host cores -------------------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_timing(case, h)
+        cpu = oracle_sample_timing(case, h)
 
     result = {
-        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (reconstruction, flux) + f64 (accumulation)",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": head["steps"],
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (reconstruction, flux) + f64 (accumulation)" if h["precision"] else "f64",
         "data": "synthetic (seeded jittered simplex meshes, analytic initial data)",
         "config": {"workload": case.description, "scheme": SCHEMES[h["scheme"]], "degree": h["degree"],
-                   "precision": "mixed", "cells": ncells,
+                   "precision": PRECISIONS[h["precision"]], "cells": case.ncells,
                    "l2": "flushed before every timed step (256 MB write, untimed)",
-                   "parallelism": f"replicas x{world}", "recon_block": blocks[0], "flux_block": blocks[1],
-                   "positivity_guard_cells": int(guard)},
-        "roofline": roofline,
+                   "parallelism": f"replicas x{world}", "recon_block": head["launch"][0],
+                   "flux_block": head["launch"][1], "positivity_guard_cells": head["positivity_guard_cells"]},
+        "roofline": head["roofline"],
+        "flux_kernel": head["flux"],
         "cpu_baseline": cpu,
-        "e2e": e2e,
+        "e2e": head["e2e"],
         # per stage: one reconstruction launch and one flux/update launch, or two for the
         # face-based flux schedule (face fluxes, then the per-cell update)
-        "gpu_launches": 3 * (1 + (2 if blocks[1] >= 8192 else 1)) * args.steps,
-        "clocks": clk,
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
+        "fp64_same_workload": ({"value": fp64_same["value"], "speedup_mixed_vs_fp64":
+                                round(head["value"] / fp64_same["value"], 2)} if fp64_same else None),
         "variants": variants,
         "alu_peak_measured": alu,
     }
@@ -425,29 +467,47 @@ def run_ours(args, rank, world, local):
         print(json.dumps(result))
 
 
-def oracle_timing(case, h, budget_s=20.0):
-    """The oracle, as it stands, on the host cores: SSP-RK3 steps of the full first mesh of the
-    workload (a smaller mesh of the same construction when that mesh is large), set-up excluded."""
+def _subbox_sample(case, target):
+    """About `target` cells of the first mesh whose centroids lie in a cube (square) around the
+    workload's sample centre, as a sorted id array (all cells when the mesh is small)."""
     import workloads as W
+    mesh = case.meshes[0]
+    if mesh.ncells <= target:
+        return np.arange(mesh.ncells, dtype=np.int32)
+    cen = W.cell_centroids(mesh)
+    d = np.abs(cen - np.asarray(case.sample_centre)).max(axis=1)   # Chebyshev distance
+    return np.sort(np.argsort(d, kind="stable")[:target]).astype(np.int32)
+
+
+# cells of one oracle stage of the sample, by (dim, degree): about 1-2 s of one stage on 16 cores
+SAMPLE_CELLS = {(2, 2): 131072, (2, 3): 131072, (3, 2): 300000, (3, 3): 60000}
+
+
+def oracle_sample_timing(case, h, budget_s=20.0):
+    """The oracle, as it stands, on the host cores, on a bounded sample of the workload: RK stages
+    (reconstruction, HLLC flux and residual; the RK combination is negligible) of the cells of a
+    sub-box of the workload's first mesh (the whole mesh when it is small), each cell and its face
+    neighbours reconstructed once per stage. Set-up of the sample excluded."""
     from oracle import Oracle, num_threads
-    mesh, U0, note = case.meshes[0], case.states[0], "the full first mesh"
-    if mesh.ncells > 400000:   # 3D workloads: same construction at n = 16
-        sub = W.density_wave_3d(16) if case.name.startswith("density") else W.blast_3d(16)
-        mesh, U0, note = sub.mesh, sub.U0, f"the same construction at n=16 ({sub.mesh.ncells} cells)"
+    mesh, U0 = case.meshes[0], case.states[0]
+    ids = _subbox_sample(case, SAMPLE_CELLS[(case.dim, h["degree"])])
     t0 = time.perf_counter()
-    o = Oracle(mesh, degree=h["degree"], scheme=h["scheme"], cfl=case.cfl)
-    setup = time.perf_counter() - t0
+    o = Oracle(mesh, setup=False, degree=h["degree"], scheme=h["scheme"], cfl=case.cfl)
     o.set_state(U0)
-    steps, t = 0, 0.0
-    while steps < 2 or (t < budget_s / 4 and steps < 20):
+    nbr = o.geometry()["nbr"][ids]
+    o.setup_cells(np.unique(np.concatenate([ids, nbr[nbr >= 0]])))
+    setup = time.perf_counter() - t0
+    stages, t = 0, 0.0
+    while stages < 2 or (t < budget_s and stages < 20):
         t0 = time.perf_counter()
-        o.step(0.0)
+        o.residual_subset(ids)
         t += time.perf_counter() - t0
-        steps += 1
-    return {"value": round(mesh.ncells * 3 * steps / t / 1e6, 4), "unit": UNIT, "cores": num_threads(),
-            "kind": "oracle",
-            "sample": f"{steps} SSP-RK3 steps of {note}, {SCHEMES[h['scheme']]} degree {h['degree']}, FP64; "
-                      f"set-up ({setup:.1f} s) excluded"}
+        stages += 1
+    whole = ids.size == mesh.ncells
+    return {"value": round(ids.size * stages / t / 1e6, 5), "unit": UNIT, "cores": num_threads(), "kind": "oracle",
+            "sample": f"{stages} RK stages (reconstruction + HLLC residual) of "
+                      f"{'all' if whole else 'a sub-box of'} {ids.size} cells of the {mesh.ncells}-cell first mesh, "
+                      f"{SCHEMES[h['scheme']]} degree {h['degree']}, FP64; set-up of the sample ({setup:.1f} s) excluded"}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -458,33 +518,39 @@ def run_reference(args, rank, world):
         return
     from oracle import Oracle, num_threads
     case = make_case(args.workload, args.n)
+    h = dict(scheme=case.scheme, degree=case.degree)
     mesh, U0 = case.meshes[0], case.states[0]
-    o = Oracle(mesh, degree=case.degree, scheme=case.scheme, cfl=case.cfl)
+    ids = _subbox_sample(case, SAMPLE_CELLS[(case.dim, case.degree)])
+    o = Oracle(mesh, setup=False, degree=case.degree, scheme=case.scheme, cfl=case.cfl)
     o.set_state(U0)
-    # each step is one SSP-RK3 step of the whole (first) mesh; the number of timed steps is capped
-    # so the run stays within about a minute
+    nbr = o.geometry()["nbr"][ids]
+    o.setup_cells(np.unique(np.concatenate([ids, nbr[nbr >= 0]])))
+    # each step is one RK stage of the sample; the number of timed steps is capped so the run
+    # stays within about a minute
     t0 = time.perf_counter()
-    o.step(0.0)
+    o.residual_subset(ids)
     per = time.perf_counter() - t0
     steps = max(1, min(args.steps, int(60.0 / max(per, 1e-3))))
     warm = min(args.warmup, 1)
     for _ in range(warm):
-        o.step(0.0)
+        o.residual_subset(ids)
     t0 = time.perf_counter()
     for _ in range(steps):
-        o.step(0.0)
+        o.residual_subset(ids)
     t = time.perf_counter() - t0
-    value = mesh.ncells * 3 * steps / t / 1e6
-    sample = (f"{steps} SSP-RK3 steps (of {args.steps} requested, capped to ~1 min) of the full "
-              f"{mesh.ncells}-cell mesh, {SCHEMES[case.scheme]} degree {case.degree}, FP64")
+    value = ids.size * steps / t / 1e6
+    whole = ids.size == mesh.ncells
+    sample = (f"{steps} RK stages (of {args.steps} requested steps, capped to ~1 min; reconstruction + HLLC "
+              f"residual) of {'all' if whole else 'a sub-box of'} {ids.size} cells of the {mesh.ncells}-cell "
+              f"first mesh, {SCHEMES[case.scheme]} degree {case.degree}, FP64")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": warm, "ms_per_step": round(t / steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": case.description, "scheme": SCHEMES[case.scheme], "degree": case.degree},
-        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": num_threads(), "kind": "oracle",
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": num_threads(), "kind": "oracle",
                          "sample": sample},
-        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 

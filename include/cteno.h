@@ -11,8 +11,10 @@
  *
  * Conventions, for every entry point:
  *   - Return 0 on success or a negative CTENO_ERR_* code. The message of the last failure is
- *     cteno_last_error(ctx). A context whose device state reported a fault (non-finite state,
- *     bounds violation) returns CTENO_ERR_DEVICE from every later synchronising call.
+ *     cteno_last_error(ctx). A context whose device state reported a fault (a non-finite state,
+ *     or a bounded wait for a bulk copy that ran out) returns CTENO_ERR_DEVICE from every later
+ *     synchronising call. Every index the kernels gather with (stencil members, face neighbours,
+ *     staging lists) is checked on the host when cteno_lsq_build uploads it.
  *   - Input arrays are copied; the library never keeps a caller's pointer. Output arrays are
  *     allocated by the caller.
  *   - Host pointers are plain host memory; "device" pointers are CUDA device (or managed)
@@ -63,17 +65,25 @@ typedef struct {
                            eq. 19 / Alg. 1-2 */
   int positivity_guard; /* 1: a cell whose face state has rho <= 0 or p <= 0 uses its cell mean
                            at all its face points for that stage (not in the paper) */
+  int ctenoz_form;      /* CTENOZ smoothness measure (Sec. 2.6, Alg. 2). 0: as printed,
+                           tau = (sum_{s>=2} |SI_s - SI_1| / (s_t - 1))^6, gamma_s = 1 + tau/(SI_s + eps).
+                           1: the WENO-Z arrangement, tau = sum_{s>=2} |SI_s - SI_1| / (s_t - 1),
+                           gamma_s = 1 + (tau/(SI_s + eps))^6 (a reading; scale invariant) */
   double C_T;           /* cut-off of eq. 23 (paper: 1e-6) */
   double lambda1p;      /* lambda_1' of eq. 18 (paper: 1e4 or 1e15) */
-  double eps;           /* epsilon of eqs. 19 and CTENOZ (not given by the paper; default 1e-40) */
+  double eps;           /* epsilon of eqs. 19 and CTENOZ (not given by the paper; default 1e-24,
+                           above the rounding floor of the smoothness indicators of both paths for
+                           |U| up to ~100, so that no selection depends on rounding; the printed
+                           CTENOZ measure drops the central stencil only where tau/eps exceeds
+                           about lambda_1'/C_T, so eps also sets its detection threshold) */
   double cfl;           /* Courant number of the time step rule (cteno_run) */
   double gamma;         /* ratio of specific heats (1.4) */
 } cteno_params;
 
 typedef struct cteno_ctx cteno_ctx;
 
-/* Fill *p with the defaults: d = 2, r = 2, CTENO, FP64, lam_gamma 1, guard 1, C_T = 1e-6,
- * lambda_1' = 1e15, eps = 1e-40, CFL 0.5, gamma 1.4. */
+/* Fill *p with the defaults: d = 2, r = 2, CTENO, FP64, lam_gamma 1, guard 1, ctenoz_form 0,
+ * C_T = 1e-6, lambda_1' = 1e15, eps = 1e-24, CFL 0.5, gamma 1.4. */
 void cteno_default_params(cteno_params *p);
 
 /* Create a context on the current CUDA device. `cuda_stream` is a cudaStream_t (may be NULL for
@@ -118,11 +128,16 @@ int cteno_set_state(cteno_ctx *ctx, int32_t mesh_id, const double *U, int is_dev
  * U holds mesh after mesh, in the order the meshes were added, each mesh's block laid out as
  * for cteno_set_state (nv * ncells values, [v][c] in its own numbering); nv * (total cells)
  * doubles, host or device. Also computes every mesh's CFL time step. A page-locked host buffer
- * is read by the kernel directly; pageable host memory is staged through device memory. */
+ * is read by the kernel directly, asynchronously: the caller must not modify it until the stream
+ * has synchronised (e.g. cteno_sync, or any cteno_get_* call to host memory). Pageable host
+ * memory is staged through device memory before the call returns. */
 int cteno_set_state_all(cteno_ctx *ctx, const double *U, int is_device);
 
-/* One stage (stage = 0, 1, 2) of the SSP-RK3 step, for every mesh, with the time step dt[mesh]
- * (host array of length nmeshes). Stage 0 stores U^n. */
+/* One stage (stage = 0, 1, 2) of the SSP-RK3 step, for every mesh. dt: host array of the time
+ * step of each mesh (length nmeshes), or NULL: at stage 0 each mesh then takes the CFL step of its
+ * current state, dt = CFL min_i |V_i| / sum_f |A_f| (|u_i.n_f| + c_i) (the step cteno_run takes;
+ * it is computed by cteno_set_state / cteno_set_state_all and by every stage 2), and stages 1 and 2
+ * keep the step of the last stage 0. Stage 0 stores U^n. */
 int cteno_rk_stage(cteno_ctx *ctx, int stage, const double *dt);
 
 /* nsteps full SSP-RK3 steps, each with dt = CFL * min_i |V_i| / sum_f |A_f| (|u_i.n_f| + c_i)
@@ -130,7 +145,9 @@ int cteno_rk_stage(cteno_ctx *ctx, int stage, const double *dt);
  * once into a CUDA graph and replayed. */
 int cteno_run(cteno_ctx *ctx, int nsteps);
 
-/* Read the conserved cell means of one mesh into U_out[v][c] (host or device). */
+/* Read the conserved cell means of one mesh into U_out[v][c] (host or device). A host read
+ * stages through a device buffer that the context allocates on first use (and grows for a larger
+ * mesh); see cteno_get_state_noalloc for a read-back that allocates nothing. */
 int cteno_get_state(cteno_ctx *ctx, int32_t mesh_id, double *U_out, int is_device);
 
 /* Read the conserved cell means of every mesh at once into U_out (host or device), laid out as
@@ -146,11 +163,14 @@ int cteno_get_state_all(cteno_ctx *ctx, double *U_out, int is_device);
  * every GPU that loads the library holds until the process exits.
  *   U_out : host, U_out[v][c] (original numbering), nv * ncells doubles, caller-allocated.
  * Errors: CTENO_ERR_ARG when nv * ncells > 2^21 (the staging area's size); the usual state and
- * mesh checks. The first call on a device looks up the staging array's device address
- * (cudaGetSymbolAddress); make that first call before any CUDA stream capture. Every call, from
- * any context, shares the one staging array: calls whose work overlaps on the GPU (contexts on
- * different streams at the same time) race and must be serialised by the caller. Nothing in the
- * array needs clearing: each call writes every value it reads back. Synchronises the stream. */
+ * mesh checks. The staging array's device address is looked up (cudaGetSymbolAddress) by
+ * cteno_lsq_build, on the context's device, once per device; under CUDA's lazy module loading
+ * that lookup is also what loads the array onto the device (16 MiB, allocated then), and
+ * cteno_lsq_build loads the gather kernel this call launches as well, so the call itself neither
+ * allocates nor loads anything. Every call, from any context, shares the one staging array: calls
+ * whose work overlaps on the GPU (contexts on different streams at the same time) race and must be
+ * serialised by the caller. Nothing in the array needs clearing: each call writes every value it
+ * reads back. Synchronises the stream. */
 int cteno_get_state_noalloc(cteno_ctx *ctx, int32_t mesh_id, double *U_out);
 
 /* Time step used by the last step of cteno_run for each mesh: host dt_out[nmeshes]. */
@@ -198,19 +218,23 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
  * CTENO_ERR_DEVICE. 4096 (mixed path) selects that lane schedule with 4 warps whose tiles also copy
  * the states of their distinct stencil members into shared memory (lists built by cteno_lsq_build);
  * 4097 the same with one tile per block and a single stage (half the shared memory); both refused
- * like the staged values when they do not fit. Flux only: 8192 + b (b a multiple of 32 in
+ * like the staged values when they do not fit. 5120 + w (mixed path, w warps per block, 1..16)
+ * selects the streamed lane schedule: every warp walks its own tiles of floor(32/(d+2)) cells and
+ * streams their operator records through its own ring of shared-memory stages, in chunks of 4 or 8
+ * stencil members per cell, several chunks ahead of the arithmetic (bounded waits as above);
+ * refused when w warps' rings do not fit in the 227 KiB of shared memory of a block. Flux only:
+ * 8192 + b (b a multiple of 32 in
  * [32, 256]) selects the face-based schedule: HLLC once per face, in its owner's orientation, into
  * a face-flux array, then a per-cell gather and update (results bit-identical to the per-cell
  * schedules). */
 int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block);
 
 /* Time the candidate launch configurations (block sizes 64/128/256, on the mixed path the
- * register-capped variants at 64/128 and the staged and gather-staged reconstruction schedules
- * that fit, and the
- * lane schedules at 128/256 threads) on the current
- * state and keep the fastest; the state is
- * restored afterwards. best_out[2] (may be NULL) receives the chosen values, in the convention of
- * cteno_set_launch. */
+ * register-capped variants at 64/128 and the staged, gather-staged and streamed reconstruction
+ * schedules that fit, and the lane schedules at 128/256 threads) on the current state and keep the
+ * fastest; the state is restored afterwards. The current state must be a valid one (set it first:
+ * the kernels run on it). best_out[2] (may be NULL) receives the chosen values, in the convention
+ * of cteno_set_launch. */
 int cteno_autotune(cteno_ctx *ctx, int32_t *best_out);
 
 /* Kernel statistics for roofline accounting: out[0] = algorithmic DRAM bytes of one
@@ -234,6 +258,15 @@ int cteno_last_kernel_ms(cteno_ctx *ctx, double *ms_out);
 /* Measure the FP64 and FP32 FMA throughput of the current device (TFLOP/s, 2 FLOP per FMA) with
  * independent FMA chains on every SM; about 0.5 s. Used as the ALU roofline denominator. */
 int cteno_measure_alu_peak(double *fp64_tflops, double *fp32_tflops);
+
+/* Test hook of the failure path of the bounded waits (no counterpart in the paper). With
+ * limit_ns > 0 every launch of a staged reconstruction schedule (launch values 2048 + b, 3072 + b,
+ * 4096, 4097) first waits, for at most limit_ns nanoseconds, on a shared-memory barrier that nothing
+ * completes. The wait runs out: the kernel records the timeout in the context's error word, waits
+ * (bounded) for the bulk copies it has issued, and returns; the next synchronising call returns
+ * CTENO_ERR_DEVICE, as for a bulk copy that never completes. 0 (the default) turns it off; limit_ns
+ * is at most 1e9. The error word of the context stays set: use a new context afterwards. */
+int cteno_test_wait_timeout(cteno_ctx *ctx, int64_t limit_ns);
 
 const char *cteno_last_error(cteno_ctx *ctx);
 void cteno_destroy(cteno_ctx *ctx);

@@ -61,6 +61,9 @@ struct cteno_ctx {
   bool timing = false;
   int pdl = 1;                       // programmatic dependent launch of the stage kernels
   int zerocopy = 1;                  // batch-wide calls access page-locked host buffers directly
+  unsigned long long test_wait_ns = 0;  // test hook of the bounded waits (0 = off)
+  double *noalloc_stage = nullptr;   // device address of the allocation-free staging array
+  int64_t noalloc_cap = 0;           //   and its capacity in doubles (looked up by lsq_build)
   cudaEvent_t tev[7] = {};           // event record nodes of the step graph
 };
 
@@ -98,6 +101,7 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.Un = ctx->Un;
   a.U32 = ctx->U32;
   a.pdl = ctx->pdl;
+  a.test_wait_ns = ctx->test_wait_ns;
   a.face = ctx->d_face;
   a.cellface = ctx->d_cellface;
   a.Ff = ctx->Ff;
@@ -128,6 +132,7 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.gamma = ctx->p.gamma;
   a.cfl = ctx->p.cfl;
   a.lam_gamma = ctx->p.lam_gamma;
+  a.ctenoz_form = ctx->p.ctenoz_form;
   a.guard_on = ctx->p.positivity_guard;
   a.lam1 = 1.0 - 1.0 / ctx->p.lambda1p;
   a.inv_lam1 = 1.0 / a.lam1;
@@ -156,10 +161,12 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   return a;
 }
 
-void enqueue_stage(cteno_ctx *ctx, int stage, int dt_swap, cudaStream_t s) {
+cudaError_t enqueue_stage(cteno_ctx *ctx, int stage, int dt_swap, cudaStream_t s) {
   const KArgs a = make_args(ctx, stage, dt_swap);
-  launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, ctx->p.scheme, a, ctx->recon_block, s);
+  const cudaError_t e = launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, ctx->p.scheme, a, ctx->recon_block, s);
+  if (e != cudaSuccess) return e;
   launch_flux(ctx->d, ctx->fp32 ? 1 : 0, a, ctx->flux_block, s);
+  return cudaSuccess;
 }
 
 int check_built(cteno_ctx *ctx) {
@@ -205,11 +212,13 @@ void drop_graph(cteno_ctx *ctx) {
 
 namespace cteno {
 
-// Host read-back of one mesh's state through a caller-supplied device staging area of
-// `capacity` doubles (used by cteno_get_state_noalloc; allocates nothing).
-int get_state_staged(cteno_ctx *ctx, int32_t mesh_id, double *U_out, double *stage, int64_t capacity) {
+// Host read-back of one mesh's state through the staging array compiled into the library, whose
+// device address cteno_lsq_build looked up (used by cteno_get_state_noalloc; allocates nothing).
+int get_state_noalloc(cteno_ctx *ctx, int32_t mesh_id, double *U_out) {
   int rc = check_built(ctx);
   if (rc) return rc;
+  double *const stage = ctx->noalloc_stage;
+  const int64_t capacity = ctx->noalloc_cap;
   if ((rc = check_mesh(ctx, mesh_id))) return rc;
   if (!U_out) return fail(ctx, CTENO_ERR_ARG, "null output");
   const Mesh &m = ctx->meshes[mesh_id];
@@ -237,9 +246,10 @@ void cteno_default_params(cteno_params *p) {
   p->precision = CTENO_FP64;
   p->lam_gamma = 1;
   p->positivity_guard = 1;
+  p->ctenoz_form = 0;
   p->C_T = 1e-6;
   p->lambda1p = 1e15;
-  p->eps = 1e-40;
+  p->eps = 1e-24;
   p->cfl = 0.5;
   p->gamma = 1.4;
 }
@@ -249,6 +259,7 @@ int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream) {
   *out = nullptr;
   if ((p->dim != 2 && p->dim != 3) || (p->degree != 2 && p->degree != 3) ||
       (p->scheme != 0 && p->scheme != 1) || (p->precision != 0 && p->precision != 1) ||
+      (p->ctenoz_form != 0 && p->ctenoz_form != 1) || (p->lam_gamma != 0 && p->lam_gamma != 1) ||
       !(p->lambda1p > 1.0) || !(p->C_T >= 0.0 && p->C_T < 1.0) || !(p->eps >= 0.0) ||
       !(p->cfl > 0.0) || !(p->gamma > 1.0))
     return CTENO_ERR_ARG;
@@ -448,6 +459,19 @@ int cteno_lsq_build(cteno_ctx *ctx) {
         const int fn = (hmeta[g] >> (2 * f)) & 3u;
         hcellface[(size_t)g * 4 + f] = (int32_t)(hcellface[(size_t)gn * 4 + fn] | 0x80000000u);
       }
+  // every index the kernels gather with, checked once here: stencil members, face neighbours,
+  // face records of the face-based flux (the gather staging lists are derived from the members)
+  {
+    bool ok = true;
+    for (size_t k = 0; k < hst.size() && ok; ++k) ok = hst[k] >= 0 && hst[k] < N;
+    for (size_t k = 0; k < hnbr.size() && ok; ++k) ok = hnbr[k] >= -1 && hnbr[k] < N;
+    const int64_t nfc = (int64_t)hface.size() / 2;
+    for (size_t k = 0; k < hface.size() && ok; ++k)
+      ok = (k % 2 == 1 && hface[k] == -1) || (hface[k] >= 0 && hface[k] < 4 * N);
+    for (int64_t g = 0; g < N && ok; ++g)
+      for (int f = 0; f < nf && ok; ++f) ok = (int64_t)(hcellface[(size_t)g * 4 + f] & 0x7FFFFFFF) < nfc;
+    if (!ok) return fail(ctx, CTENO_ERR_MESH, "a gathered index is out of range (inconsistent connectivity)");
+  }
   // device allocations
   const size_t sT = ctx->fp32 ? sizeof(float) : sizeof(double);
   ctx->nfaces = (int64_t)hface.size() / 2;
@@ -556,6 +580,11 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   ctx->member_sum = ms;
   ctx->adm_faces = af;
   CK(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+  // the allocation-free read-back: its staging array's address on this (the context's) device,
+  // and the kernel it launches, loaded now (under lazy module loading a first use would load them
+  // later, and loading allocates device memory)
+  CK(noalloc_stage_address(&ctx->noalloc_stage, &ctx->noalloc_cap));
+  CK(preload_permute_out());
   ctx->built = true;
   return CTENO_OK;
 }
@@ -643,10 +672,15 @@ int cteno_get_state_all(cteno_ctx *ctx, double *U_out, int is_device) {
 int cteno_rk_stage(cteno_ctx *ctx, int stage, const double *dt) {
   int rc = check_built(ctx);
   if (rc) return rc;
-  if (stage < 0 || stage > 2 || !dt) return fail(ctx, CTENO_ERR_ARG, "bad stage or dt");
-  CK(cudaMemcpyAsync(ctx->dt, dt, sizeof(double) * ctx->meshes.size(), cudaMemcpyHostToDevice, ctx->stream));
-  if (stage == 0) launch_dt_reset(make_args(ctx, 0, 0), ctx->stream);
-  enqueue_stage(ctx, stage, 0, ctx->stream);
+  if (stage < 0 || stage > 2) return fail(ctx, CTENO_ERR_ARG, "bad stage");
+  int swap = 0;
+  if (dt) {
+    CK(cudaMemcpyAsync(ctx->dt, dt, sizeof(double) * ctx->meshes.size(), cudaMemcpyHostToDevice, ctx->stream));
+    if (stage == 0) launch_dt_reset(make_args(ctx, 0, 0), ctx->stream);
+  } else if (stage == 0) {
+    swap = 1;  // the CFL step of the current state (computed by set_state or the last stage 2)
+  }
+  CK(enqueue_stage(ctx, stage, swap, ctx->stream));
   CK(cudaGetLastError());
   return CTENO_OK;
 }
@@ -660,7 +694,14 @@ int cteno_run(cteno_ctx *ctx, int nsteps) {
     if (ctx->timing) CK(cudaEventRecordWithFlags(ctx->tev[0], ctx->capture, cudaEventRecordExternal));
     for (int s = 0; s < 3; ++s) {
       const KArgs a = make_args(ctx, s, s == 0 ? 1 : 0);
-      launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, ctx->p.scheme, a, ctx->recon_block, ctx->capture);
+      const cudaError_t le =
+          launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, ctx->p.scheme, a, ctx->recon_block, ctx->capture);
+      if (le != cudaSuccess) {  // end the capture before reporting
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(ctx->capture, &g);
+        if (g) cudaGraphDestroy(g);
+        return fail(ctx, CTENO_ERR_CUDA, std::string("reconstruction launch: ") + cudaGetErrorString(le));
+      }
       if (ctx->timing) CK(cudaEventRecordWithFlags(ctx->tev[2 * s + 1], ctx->capture, cudaEventRecordExternal));
       launch_flux(ctx->d, ctx->fp32 ? 1 : 0, a, ctx->flux_block, ctx->capture);
       if (ctx->timing) CK(cudaEventRecordWithFlags(ctx->tev[2 * s + 2], ctx->capture, cudaEventRecordExternal));
@@ -807,6 +848,8 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
     if (b == 0) return true;
     if (b >= kFaceFlux)  // face-based flux schedule
       return !recon && b - kFaceFlux >= 32 && b - kFaceFlux <= 256 && b % 32 == 0;
+    if (b > kStreamLanes && b <= kStreamLanes + 16)  // streamed lanes: reconstruction, mixed, fits
+      return recon && ctx->fp32 && recon_stream_smem(ctx->d, ctx->p.degree, b - kStreamLanes) <= kMaxStreamSmem;
     if (b == kHaloLanes || b == kHaloLanes + 1)  // gather-staged: reconstruction, mixed, lists built, fits
       return recon && ctx->fp32 && ctx->hl &&
              recon_halo_smem(ctx->d, ctx->p.degree, ctx->hrec) / (b == kHaloLanes ? 1 : 2) <= kMaxStagedSmem;
@@ -876,14 +919,18 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
     if (hs <= kMaxStagedSmem) rcand.push_back(kHaloLanes);
     if (hs / 2 <= kMaxStagedSmem) rcand.push_back(kHaloLanes + 1);
   }
+  // the streamed lane schedule (mixed path) at the block sizes that fit
+  if (ctx->fp32)
+    for (int w : {4, 8, 10, 12, 16})
+      if (recon_stream_smem(ctx->d, ctx->p.degree, w) <= kMaxStreamSmem) rcand.push_back(kStreamLanes + w);
   const int reps = 5;
   float best_r = 1e30f, best_f = 1e30f;
   int br = ctx->recon_block, bf = ctx->flux_block;
   const KArgs a = make_args(ctx, 1, 0);  // stage 1: reads U^n, writes U only
   for (int b : rcand) {  // the reconstruction writes only face states: no restore needed
-    launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, b, ctx->stream);
+    CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, b, ctx->stream));
     CK(cudaEventRecord(e0, ctx->stream));
-    for (int r = 0; r < reps; ++r) launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, b, ctx->stream);
+    for (int r = 0; r < reps; ++r) CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, b, ctx->stream));
     CK(cudaEventRecord(e1, ctx->stream));
     CK(cudaEventSynchronize(e1));
     float ms = 0;
@@ -959,7 +1006,7 @@ int cteno_profile_step(cteno_ctx *ctx, int nsteps, double *ms_out) {
     for (int s = 0; s < 3; ++s) {
       const KArgs a = make_args(ctx, s, s == 0 ? 1 : 0);
       CK(cudaEventRecord(ev[2 * s], ctx->stream));
-      launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, ctx->recon_block, ctx->stream);
+      CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, ctx->recon_block, ctx->stream));
       CK(cudaEventRecord(ev[2 * s + 1], ctx->stream));
       launch_flux(ctx->d, ctx->fp32, a, ctx->flux_block, ctx->stream);
     }
@@ -1005,6 +1052,14 @@ int cteno_last_kernel_ms(cteno_ctx *ctx, double *ms_out) {
   }
   ms_out[0] = r;
   ms_out[1] = f;
+  return CTENO_OK;
+}
+
+int cteno_test_wait_timeout(cteno_ctx *ctx, int64_t limit_ns) {
+  if (!ctx) return CTENO_ERR_ARG;
+  if (limit_ns < 0 || limit_ns > 1000000000LL) return fail(ctx, CTENO_ERR_ARG, "limit_ns must be in [0, 1e9]");
+  ctx->test_wait_ns = (unsigned long long)limit_ns;
+  drop_graph(ctx);
   return CTENO_OK;
 }
 

@@ -91,7 +91,7 @@ struct KArgs {
   unsigned long long *guard;
   // parameters
   double C_T, lambda1p, eps, gamma, cfl;
-  int lam_gamma, guard_on;
+  int lam_gamma, guard_on, ctenoz_form;
   // linear coefficients of eq. 18, evaluated once on the host in FP64:
   // lam1 = 1 - 1/lambda_1', 1/lam1, 1 - lam1 (lambda_s = (1 - lam1) / (s_t - 1)) and base-2 logs
   double lam1, inv_lam1, one_m_lam1;
@@ -118,6 +118,9 @@ struct KArgs {
   void *Ff;
   int64_t nfaces;
   int pdl;                  // launched with programmatic dependent launch (see pdl_wait)
+  // test hook of the bounded waits (0 = off): the staged schedules first wait at most this many
+  // nanoseconds on a barrier that nothing completes, then take their timeout path
+  unsigned long long test_wait_ns;
   int stage;                // 0, 1, 2
   int dt_swap;              // stage 0 of a CFL step: move dt[next] to dt[cur] first
 };
@@ -155,6 +158,21 @@ constexpr int kHaloLanes = 4096;
 // gather and update), b threads per block.
 constexpr int kFaceFlux = 8192;
 constexpr int kHaloWarps = 4;
+// kStreamLanes + w (w warps per block, 1..16): the streamed lane schedule (mixed path): every warp
+// streams its tiles' operator records through its own ring of shared-memory stages.
+constexpr int kStreamLanes = 5120;
+constexpr int kStreamStages = 4;
+constexpr int kMaxStreamSmem = 227 * 1024;  // the per-block limit of the GPU
+// Dynamic shared memory of the streamed schedule with `warps` warps (see StreamShape).
+inline long long recon_stream_smem(int d, int degree, int warps) {
+  const int nk = (d == 2 ? (degree + 1) * (degree + 2) / 2 : (degree + 1) * (degree + 2) * (degree + 3) / 6) - 1;
+  const int M = 2 * (nk + 1), nv = d + 2, cpw = 32 / nv, mc = (M % 8 == 0) ? 8 : 4;
+  const long long stage = (long long)cpw * mc * nk * 4;
+  const long long hdr = (long long)cpw * (d + 1) * lay_pds(d) * 4 + (long long)cpw * M * 4;
+  const long long nphi = d == 3 ? (long long)(d + 1) * 6 * 4 * nk : 1;
+  const long long phi = (nphi * 4 + 15) / 16 * 16;
+  return phi + (long long)warps * (2 * hdr + kStreamStages * stage) + (long long)warps * (2 + kStreamStages) * 8 + 8;
+}
 inline int halo_tile(int d) { return kHaloWarps * (32 / (d + 2)); }
 inline int halo_ms(int M) { return (M + 1 + 7) / 8 * 8; }
 // Dynamic shared memory of the gather-staged launch for a tile record of hrec words.
@@ -181,12 +199,14 @@ void launch_setup(int dim, int degree, const SetupArgs &a, cudaStream_t s);
 // reconstruction kernels.
 cudaError_t upload_recon_tables_2d(int degree, const Tables &t, cudaStream_t s);
 cudaError_t upload_recon_tables_3d(int degree, const Tables &t, cudaStream_t s);
-void launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s);
-void launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s);
-inline void launch_recon(int dim, int degree, int fp32, int scheme, const KArgs &a, int block,
-                         cudaStream_t s) {
-  if (dim == 2) launch_recon_2d(degree, fp32, scheme, a, block, s);
-  else launch_recon_3d(degree, fp32, scheme, a, block, s);
+// cudaErrorInvalidValue (and no launch) for a launch value the path does not have (a staged,
+// gather-staged or streamed schedule on the FP64 path).
+cudaError_t launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s);
+cudaError_t launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s);
+inline cudaError_t launch_recon(int dim, int degree, int fp32, int scheme, const KArgs &a, int block,
+                                cudaStream_t s) {
+  return dim == 2 ? launch_recon_2d(degree, fp32, scheme, a, block, s)
+                  : launch_recon_3d(degree, fp32, scheme, a, block, s);
 }
 void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s);
 void launch_dt(int dim, const KArgs &a, cudaStream_t s);
@@ -204,6 +224,11 @@ void launch_permute_in(int nv, int nvp, int64_t n, int64_t off, const int32_t *r
                        const double *src, double *U, float *U32, cudaStream_t s);
 void launch_permute_out(int nv, int nvp, int64_t n, int64_t off, const int32_t *rank,
                         const double *U, double *dst, cudaStream_t s);
+// Load the kernel of launch_permute_out on the current device (lazy module loading).
+cudaError_t preload_permute_out();
+// Device address, on the current device, of the staging array of the allocation-free read-back
+// (noalloc.cu) and its capacity in doubles.
+cudaError_t noalloc_stage_address(double **out, int64_t *capacity);
 
 // 16-byte vector access to records (the records are 16-byte aligned by construction).
 template <typename T>

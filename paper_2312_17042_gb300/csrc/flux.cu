@@ -755,4 +755,9 @@ void launch_permute_out(int nv, int nvp, int64_t n, int64_t off, const int32_t *
   permute_out_kernel<<<grid_for(n, 256), 256, 0, s>>>(nv, nvp, n, off, rank, U, dst);
 }
 
+cudaError_t preload_permute_out() {
+  cudaFuncAttributes attr;
+  return cudaFuncGetAttributes(&attr, permute_out_kernel);
+}
+
 }  // namespace cteno

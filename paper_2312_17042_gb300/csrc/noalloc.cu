@@ -22,10 +22,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_lock;
 double *g_stage_addr[kMaxDevices] = {};
 
-// Device address of the staging array on the current device, looked up once per device. In
-// host code the array's name is only a host-side stand-in, so the kernel must be given this
-// address, never the symbol.
-cudaError_t stage_address(double **out) {
+}  // namespace
+
+namespace cteno {
+
+// Device address of the staging array on the current device, looked up once per device. In host
+// code the array's name is only a host-side stand-in, so a kernel must be given this address,
+// never the symbol. Under lazy module loading the lookup also loads the module that holds the
+// array (which allocates it); cteno_lsq_build calls this on the context's device for that reason.
+cudaError_t noalloc_stage_address(double **out, int64_t *capacity) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -38,21 +43,15 @@ cudaError_t stage_address(double **out) {
     g_stage_addr[dev] = static_cast<double *>(p);
   }
   *out = g_stage_addr[dev];
+  *capacity = kStageValues;
   return cudaSuccess;
 }
 
-}  // namespace
-
-namespace cteno {
-
-// Implemented in api.cpp: everything cteno_get_state needs, with the staging buffer supplied.
-int get_state_staged(cteno_ctx *ctx, int32_t mesh_id, double *U_out, double *stage, int64_t capacity);
+// Implemented in api.cpp: everything cteno_get_state needs, through the context's staging address.
+int get_state_noalloc(cteno_ctx *ctx, int32_t mesh_id, double *U_out);
 
 }  // namespace cteno
 
 extern "C" int cteno_get_state_noalloc(cteno_ctx *ctx, int32_t mesh_id, double *U_out) {
-  double *stage = nullptr;
-  const cudaError_t e = stage_address(&stage);
-  if (e != cudaSuccess) return CTENO_ERR_CUDA;
-  return cteno::get_state_staged(ctx, mesh_id, U_out, stage, kStageValues);
+  return cteno::get_state_noalloc(ctx, mesh_id, U_out);
 }

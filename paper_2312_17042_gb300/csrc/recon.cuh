@@ -100,10 +100,12 @@ __device__ __forceinline__ T pow6(T x) {
 
 // Selection of eqs. 19-23 / Alg. 1-2 in FP64, as printed (gamma_s times lambda_s when
 // lam_gamma). SI0: central; SId[f]: directional stencil of face f, used where bit f of adm is
-// set. Returns delta bits: bit 0 central, bit 1 + f directional f.
+// set. CTENOZ form 0: tau = (mean |SI_s - SI_1|)^6, gamma = 1 + tau / (SI + eps) (as printed);
+// form 1: tau = mean |SI_s - SI_1|, gamma = 1 + (tau / (SI + eps))^6 (the WENO-Z arrangement).
+// Returns delta bits: bit 0 central, bit 1 + f directional f.
 template <int NF>
 __device__ __forceinline__ uint32_t select_fp64(double SI0, const double *SId, uint32_t adm, int st,
-                                                int scheme, int lam_gamma, double lam1, double lams,
+                                                int scheme, int form, int lam_gamma, double lam1, double lams,
                                                 double eps, double C_T) {
   double g0, gd[NF];
   if (scheme == 0) {
@@ -117,11 +119,18 @@ __device__ __forceinline__ uint32_t select_fp64(double SI0, const double *SId, u
 #pragma unroll
       for (int f = 0; f < NF; ++f)
         if ((adm >> f) & 1u) acc += fabs(SId[f] - SI0);
-      tau = pow6(acc / (st - 1));
+      tau = acc / (st - 1);
+      if (form == 0) tau = pow6(tau);
     }
-    g0 = 1.0 + tau / (SI0 + eps);
+    if (form == 0) {
+      g0 = 1.0 + tau / (SI0 + eps);
 #pragma unroll
-    for (int f = 0; f < NF; ++f) gd[f] = 1.0 + tau / (SId[f] + eps);
+      for (int f = 0; f < NF; ++f) gd[f] = 1.0 + tau / (SId[f] + eps);
+    } else {
+      g0 = 1.0 + pow6(tau / (SI0 + eps));
+#pragma unroll
+      for (int f = 0; f < NF; ++f) gd[f] = 1.0 + pow6(tau / (SId[f] + eps));
+    }
   }
   if (lam_gamma) {
     g0 *= lam1;
@@ -169,7 +178,7 @@ __device__ __forceinline__ X pick(const X *tab, int k) {
 // 2^(L_s - Lmax) < C_T sum_t 2^(L_t - Lmax) (no division). inv_stm1 = 1 / (st - 1).
 template <int NF>
 __device__ __forceinline__ uint32_t select_fp32(float SI0, const float *SId, uint32_t adm, int st,
-                                                int scheme, int lam_gamma, float log2lam1,
+                                                int scheme, int form, int lam_gamma, float log2lam1,
                                                 float log2lams, float inv_stm1, float eps, float C_T) {
   float L0, Ld[NF];
   if (scheme == 0) {
@@ -177,21 +186,29 @@ __device__ __forceinline__ uint32_t select_fp32(float SI0, const float *SId, uin
 #pragma unroll
     for (int f = 0; f < NF; ++f) Ld[f] = -6.0f * lg2_approx(SId[f] + eps);
   } else {
-    float lt = -INFINITY;  // log2 tau
+    float lt = -INFINITY;  // log2 of the mean |SI_s - SI_1|
     if (st > 1) {
       float acc = 0.0f;
 #pragma unroll
       for (int f = 0; f < NF; ++f)
         if ((adm >> f) & 1u) acc += fabsf(SId[f] - SI0);
-      lt = 6.0f * lg2_approx(acc * inv_stm1);
+      lt = lg2_approx(acc * inv_stm1);
     }
-    // log2(1 + 2^x) with x = log2(tau / (SI + eps)), split to stay accurate for any x
+    // log2(1 + 2^x), split to stay accurate for any x; x = log2 of the term added to 1:
+    // form 0 tau / (SI + eps) with tau = mean^6, form 1 (mean / (SI + eps))^6
     auto l1p = [](float x) {
       return (x > 0.0f) ? x + lg2_approx(1.0f + ex2_approx(-x)) : lg2_approx(1.0f + ex2_approx(x));
     };
-    L0 = l1p(lt - lg2_approx(SI0 + eps));
+    if (form == 0) {
+      const float lt6 = 6.0f * lt;
+      L0 = l1p(lt6 - lg2_approx(SI0 + eps));
 #pragma unroll
-    for (int f = 0; f < NF; ++f) Ld[f] = l1p(lt - lg2_approx(SId[f] + eps));
+      for (int f = 0; f < NF; ++f) Ld[f] = l1p(lt6 - lg2_approx(SId[f] + eps));
+    } else {
+      L0 = l1p(6.0f * (lt - lg2_approx(SI0 + eps)));
+#pragma unroll
+      for (int f = 0; f < NF; ++f) Ld[f] = l1p(6.0f * (lt - lg2_approx(SId[f] + eps)));
+    }
   }
   if (lam_gamma) {
     L0 += log2lam1;
@@ -384,10 +401,10 @@ __device__ __forceinline__ void recon_cell(const KArgs &a, const int64_t i, cons
     // 5: selection
     uint32_t bits;
     if constexpr (F32) {
-      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, log2lam1, log2lams, inv_stm1, a.eps32,
-                             a.C_T32);
+      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, log2lam1, log2lams,
+                             inv_stm1, a.eps32, a.C_T32);
     } else {
-      bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
+      bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
     }
     // final coefficients, written over a_opt
     if (bits & 1u) {
@@ -511,6 +528,155 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
 // neighbour's record are split over the group. A warp holds floor(32 / NV) cells; spare lanes
 // and lanes past the last cell work on a clamped cell and store nothing.
 // ---------------------------------------------------------------------------------------------
+// The second half of the variable-per-lane schedule, from the central coefficients ao and the
+// directional coefficients ad of variable v (inadmissible stencils hold zeros): p_1 (eq. 17), the
+// smoothness indicators (eq. 15), the selection (eqs. 19-23, Alg. 1 / 2), the final coefficients,
+// and the values at the face Gauss points with the positivity guard (every lane of the warp calls
+// it: the guard exchanges rho, momentum and E of each point by shuffles).
+template <int D, int R, typename T, int SCHEME>
+__device__ __forceinline__ void lane_finish(const KArgs &a, const int64_t i, const bool active, const int v,
+                                            const int base, T (&ao)[Shape<D, R>::NK],
+                                            const T (&ad)[Lay<D>::NF][D], const uint32_t info, const T U0,
+                                            const float L0, const T *__restrict__ sPhi) {
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  constexpr int NV = L::NV, NF = L::NF, NQ = L::NQ;
+  constexpr int NK = S::NK, NP = S::NP;
+  constexpr bool F32 = sizeof(T) == 4;
+  const int64_t N = a.N;
+  const uint32_t adm = (info >> kInfoAdmShift) & 0xFu;
+  // p_1, smoothness indicators, selection (eqs. 15-23), final coefficients in ao
+  const int stn = 1 + __popc(adm);
+  T lams;
+  double lamsd = 0.0;
+  float log2lams = 0.0f, inv_stm1 = 0.0f;
+  if constexpr (F32) {
+    lams = pick<NF>(a.lams_f, stn - 1);
+    log2lams = pick<NF>(a.log2_lams_f, stn - 1);
+    inv_stm1 = pick<NF>(a.inv_stm1_f, stn - 1);
+  } else {
+    lamsd = pick<NF>(a.lams_d, stn - 1);
+    lams = lamsd;
+  }
+  constexpr T INV_FACT = (D == 2) ? (T)0.5 : (T)(1.0 / 6.0);
+  {
+    T a1[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) a1[k] = ao[k];
+    if (stn > 1) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        T s = (T)0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) s += ad[f][k];
+        a1[k] -= lams * s;
+      }
+      T inv_lam1;
+      if constexpr (F32) inv_lam1 = a.inv_lam1_32; else inv_lam1 = a.inv_lam1;
+#pragma unroll
+      for (int k = 0; k < NK; ++k) a1[k] *= inv_lam1;
+    }
+    T SI0 = (T)0;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      T rr = (T)0;
+#pragma unroll
+      for (int l = k; l < NK; ++l) rr += cO<T, R>(k * NK + l) * a1[l];
+      SI0 += a1[k] * rr;
+    }
+    T SId[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T s = (T)0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += ad[f][k] * ad[f][k];
+      SId[f] = s * INV_FACT;
+    }
+    uint32_t bits;
+    if constexpr (F32) {
+      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.log2_lam1, log2lams,
+                             inv_stm1, a.eps32, a.C_T32);
+    } else {
+      bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
+    }
+    if (bits & 1u) {
+#pragma unroll
+      for (int k = 0; k < NK; ++k) ao[k] = a1[k];
+    } else {
+      const T w = (T)1 / (T)__popc(bits >> 1);
+#pragma unroll
+      for (int k = 0; k < NK; ++k) ao[k] = (T)0;
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        if ((bits >> (1 + f)) & 1u) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) ao[k] += w * ad[f][k];
+        }
+    }
+    if (a.flags && active) a.flags[v * N + i] = (uint8_t)((bits & 1u) ? 1u : bits);
+  }
+
+  // face values of variable v; the positivity guard gathers rho, momentum and E of each point
+  // from the group's lanes
+  T *__restrict__ Ufi = (T *)a.Uf + i * (int64_t)(NF * NQ * NV);
+  const uint32_t perm = info >> kInfoPermShift;
+  T gm1;
+  if constexpr (F32) gm1 = a.gm1_32; else gm1 = a.gamma - 1.0;
+  bool bad = false;
+  T fv[NF][NQ];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int p = (perm >> (3 * f)) & 7u;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      T val = (T)L0;
+      if constexpr (D == 2) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) val += cPhi2<T, R>((f * 2 + q) * NK + k) * ao[k];
+      } else {
+        const T *ph = &sPhi[((f * NP + p) * NQ + q) * NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) val += ph[k] * ao[k];
+      }
+      val += U0;
+      fv[f][q] = val;
+      const T rho = __shfl_sync(0xffffffffu, val, base);
+      const T E = __shfl_sync(0xffffffffu, val, base + NV - 1);
+      T ke = (T)0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const T m = __shfl_sync(0xffffffffu, val, base + 1 + j);
+        ke += m * m;
+      }
+      if constexpr (F32) {  // rho > 0 and p > 0, the latter as rho E - |m|^2 / 2 > 0 (no division)
+        bad = bad || !(rho > 0.0f) || !(rho * E - 0.5f * ke > 0.0f);
+      } else {
+        const T pr = gm1 * (E - (T)0.5 * ke / rho);
+        bad = bad || !(rho > (T)0) || !(pr > (T)0);
+      }
+    }
+  }
+  if (a.guard_on && bad) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) fv[f][q] = U0 + (T)L0;
+    if (active && v == 0) atomicAdd(a.guard, 1ull);
+  }
+  if (active) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int p = (perm >> (3 * f)) & 7u;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        // 2D: an edge is stored in sorted-vertex order, the swapped orientation reverses its points
+        const int qq = (D == 2 && p) ? (NQ - 1 - q) : q;
+        Ufi[(f * NQ + qq) * NV + v] = fv[f][q];
+      }
+    }
+  }
+}
+
 // One cell of the variable-per-lane schedule, seen from lane v of its group (first lane base);
 // every lane of the warp calls it (inactive lanes with a clamped valid cell i) because the
 // positivity guard exchanges values with shuffles. Operator pointers as for recon_cell. HALO:
@@ -526,12 +692,10 @@ __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, cons
   const uint16_t *__restrict__ lid = reinterpret_cast<const uint16_t *>(sti_);
   using S = Shape<D, R>;
   using L = Lay<D>;
-  constexpr int NVP = L::NVP, NF = L::NF, NQ = L::NQ, ND = L::ND, PDS = L::PDS;
-  constexpr int NV = L::NV;
-  constexpr int NK = S::NK, M = S::M, NP = S::NP;
+  constexpr int NVP = L::NVP, NF = L::NF, ND = L::ND, PDS = L::PDS;
+  constexpr int NK = S::NK, M = S::M;
   constexpr int CH = Vec16<T>::n;
   constexpr bool F32 = sizeof(T) == 4;
-  const int64_t N = a.N;
   // own mean of variable v: FP64, or the FP32 pair (hi, lo)
   T U0;
   float L0;
@@ -623,136 +787,7 @@ __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, cons
       off += nm;
     }
   }
-  // p_1, smoothness indicators, selection (eqs. 15-23), final coefficients in ao
-  const int stn = 1 + __popc(adm);
-  T lams;
-  double lamsd = 0.0;
-  float log2lams = 0.0f, inv_stm1 = 0.0f;
-  if constexpr (F32) {
-    lams = pick<NF>(a.lams_f, stn - 1);
-    log2lams = pick<NF>(a.log2_lams_f, stn - 1);
-    inv_stm1 = pick<NF>(a.inv_stm1_f, stn - 1);
-  } else {
-    lamsd = pick<NF>(a.lams_d, stn - 1);
-    lams = lamsd;
-  }
-  constexpr T INV_FACT = (D == 2) ? (T)0.5 : (T)(1.0 / 6.0);
-  {
-    T a1[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) a1[k] = ao[k];
-    if (stn > 1) {
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        T s = (T)0;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) s += ad[f][k];
-        a1[k] -= lams * s;
-      }
-      T inv_lam1;
-      if constexpr (F32) inv_lam1 = a.inv_lam1_32; else inv_lam1 = a.inv_lam1;
-#pragma unroll
-      for (int k = 0; k < NK; ++k) a1[k] *= inv_lam1;
-    }
-    T SI0 = (T)0;
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-      T rr = (T)0;
-#pragma unroll
-      for (int l = k; l < NK; ++l) rr += cO<T, R>(k * NK + l) * a1[l];
-      SI0 += a1[k] * rr;
-    }
-    T SId[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      T s = (T)0;
-#pragma unroll
-      for (int k = 0; k < D; ++k) s += ad[f][k] * ad[f][k];
-      SId[f] = s * INV_FACT;
-    }
-    uint32_t bits;
-    if constexpr (F32) {
-      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.log2_lam1, log2lams, inv_stm1, a.eps32,
-                             a.C_T32);
-    } else {
-      bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
-    }
-    if (bits & 1u) {
-#pragma unroll
-      for (int k = 0; k < NK; ++k) ao[k] = a1[k];
-    } else {
-      const T w = (T)1 / (T)__popc(bits >> 1);
-#pragma unroll
-      for (int k = 0; k < NK; ++k) ao[k] = (T)0;
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-        if ((bits >> (1 + f)) & 1u) {
-#pragma unroll
-          for (int k = 0; k < D; ++k) ao[k] += w * ad[f][k];
-        }
-    }
-    if (a.flags && active) a.flags[v * N + i] = (uint8_t)((bits & 1u) ? 1u : bits);
-  }
-
-  // face values of variable v; the positivity guard gathers rho, momentum and E of each point
-  // from the group's lanes
-  T *__restrict__ Ufi = (T *)a.Uf + i * (int64_t)(NF * NQ * NV);
-  const uint32_t perm = info >> kInfoPermShift;
-  T gm1;
-  if constexpr (F32) gm1 = a.gm1_32; else gm1 = a.gamma - 1.0;
-  bool bad = false;
-  T fv[NF][NQ];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const int p = (perm >> (3 * f)) & 7u;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      T val = (T)L0;
-      if constexpr (D == 2) {
-#pragma unroll
-        for (int k = 0; k < NK; ++k) val += cPhi2<T, R>((f * 2 + q) * NK + k) * ao[k];
-      } else {
-        const T *ph = &sPhi[((f * NP + p) * NQ + q) * NK];
-#pragma unroll
-        for (int k = 0; k < NK; ++k) val += ph[k] * ao[k];
-      }
-      val += U0;
-      fv[f][q] = val;
-      const T rho = __shfl_sync(0xffffffffu, val, base);
-      const T E = __shfl_sync(0xffffffffu, val, base + NV - 1);
-      T ke = (T)0;
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        const T m = __shfl_sync(0xffffffffu, val, base + 1 + j);
-        ke += m * m;
-      }
-      if constexpr (F32) {  // rho > 0 and p > 0, the latter as rho E - |m|^2 / 2 > 0 (no division)
-        bad = bad || !(rho > 0.0f) || !(rho * E - 0.5f * ke > 0.0f);
-      } else {
-        const T pr = gm1 * (E - (T)0.5 * ke / rho);
-        bad = bad || !(rho > (T)0) || !(pr > (T)0);
-      }
-    }
-  }
-  if (a.guard_on && bad) {
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) fv[f][q] = U0 + (T)L0;
-    if (active && v == 0) atomicAdd(a.guard, 1ull);
-  }
-  if (active) {
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const int p = (perm >> (3 * f)) & 7u;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        // 2D: an edge is stored in sorted-vertex order, the swapped orientation reverses its points
-        const int qq = (D == 2 && p) ? (NQ - 1 - q) : q;
-        Ufi[(f * NQ + qq) * NV + v] = fv[f][q];
-      }
-    }
-  }
+  lane_finish<D, R, T, SCHEME>(a, i, active, v, base, ao, ad, info, U0, L0, sPhi);
 }
 
 template <int D, int R, typename T, int SCHEME>
@@ -820,7 +855,7 @@ __global__ void __launch_bounds__(256) recon_staged_kernel(const KArgs a) {
   constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
   constexpr int CPW = 32 / NV;
   __shared__ T sPhi[NPHI];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[3];  // two stages; bar[2] only for the test hook
   extern __shared__ __align__(128) unsigned char stage_mem[];
 
   const int C = LANES ? (int)(blockDim.x >> 5) * CPW : (int)blockDim.x;
@@ -845,6 +880,7 @@ __global__ void __launch_bounds__(256) recon_staged_kernel(const KArgs a) {
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
     fence_barrier_init();
   }
   if constexpr (D == 3) {
@@ -858,6 +894,18 @@ __global__ void __launch_bounds__(256) recon_staged_kernel(const KArgs a) {
   if (threadIdx.x == 0) {
     if ((int64_t)blockIdx.x < tiles) issue(blockIdx.x, 0);
     if ((int64_t)blockIdx.x + gridDim.x < tiles) issue((int64_t)blockIdx.x + gridDim.x, 1);
+  }
+  if (a.test_wait_ns) {  // test hook: a bounded wait on a barrier that nothing completes runs out
+    bool ok = true;
+    if (threadIdx.x == 0) ok = mbar_wait(&bar[2], 0, a.test_wait_ns);
+    if (__syncthreads_or(!ok)) {  // the timeout path: report, let this block's copies land, stop
+      if (threadIdx.x == 0) {
+        atomicOr(a.err, kErrTimeout);
+        if ((int64_t)blockIdx.x < tiles) mbar_wait(&bar[0], 0, kStageWaitNs);
+        if ((int64_t)blockIdx.x + gridDim.x < tiles) mbar_wait(&bar[1], 0, kStageWaitNs);
+      }
+      return;
+    }
   }
   // the operator records do not depend on the previous kernel: their copies were issued above;
   // the states it writes (and the face states it may still read) are touched only after this
@@ -930,7 +978,7 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
   constexpr int HS = NVP * 2 * 4;           // bytes of one member state (FP32 pairs)
   constexpr int LI = MS * 2;                // bytes of one cell's local ids
   __shared__ T sPhi[NPHI];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[3];  // two stages; bar[2] only for the test hook
   extern __shared__ __align__(128) unsigned char stage_mem[];
 
   const int64_t N = a.N;
@@ -987,6 +1035,7 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     if (!ONE) mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
     fence_barrier_init();
   }
   if constexpr (D == 3) {
@@ -1000,6 +1049,17 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
   if (threadIdx.x == 0) {
     if ((int64_t)blockIdx.x < tiles) issue(blockIdx.x, 0);
     if (!ONE && (int64_t)blockIdx.x + gridDim.x < tiles) issue((int64_t)blockIdx.x + gridDim.x, 1);
+  }
+  if (a.test_wait_ns) {  // test hook: a bounded wait on a barrier that nothing completes runs out
+    bool ok = true;
+    if (threadIdx.x == 0) ok = mbar_wait(&bar[2], 0, a.test_wait_ns);
+    if (__syncthreads_or(!ok)) {  // the timeout path: report, let this block's copies land, stop
+      if ((int64_t)blockIdx.x < tiles)
+        give_up(0, 0, !ONE && (int64_t)blockIdx.x + gridDim.x < tiles);
+      else if (threadIdx.x == 0)
+        atomicOr(a.err, kErrTimeout);
+      return;
+    }
   }
   // the operator records and member lists do not depend on the previous kernel: their copies
   // were issued above; member states, face states and dt are touched only after this
@@ -1056,6 +1116,249 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
     }
   }
   cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Streamed lane schedule (mixed path): every warp is an independent pipeline over tiles of CPW
+// consecutive cells (lane v of group g: variable v of cell g). The central pseudo-inverse records
+// of a tile stream through a per-warp ring of NST shared-memory stages in chunks of MC members
+// per cell (one bulk copy per cell and chunk, completion on the stage's mbarrier); the tile's
+// directional operators and stencil ids go to one of two per-warp header buffers. Copies run NST
+// chunks (and two tiles' headers) ahead of the computation, so each SM keeps tens of kilobytes of
+// the dominant stream in flight while its loops stay short (few registers, little code), and no
+// warp waits for another.
+// ---------------------------------------------------------------------------------------------
+template <int D, int R>
+struct StreamShape {
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  static constexpr int CPW = 32 / L::NV;                     // cells per warp
+  static constexpr int MC = (S::M % 8 == 0) ? 8 : 4;          // members per chunk
+  static constexpr int NCH = S::M / MC;                       // chunks per tile
+  static constexpr int NST = kStreamStages;                   // stages of the chunk ring
+  static constexpr int CHUNK_CELL = MC * S::NK * 4;           // bytes of one cell's chunk
+  static constexpr int STAGE = CPW * CHUNK_CELL;
+  static constexpr int HPD = CPW * L::NF * L::PDS * 4;        // header: directional operators,
+  static constexpr int HST = CPW * S::M * 4;                  //   stencil ids
+  static constexpr int HDR = HPD + HST;
+  static constexpr int WARP_BYTES = 2 * HDR + NST * STAGE;
+  static constexpr int NPHI = (D == 3) ? L::NF * S::NP * L::NQ * S::NK : 1;
+  static constexpr int PHI_BYTES = (NPHI * 4 + 15) / 16 * 16;
+  static_assert(S::M % MC == 0 && CHUNK_CELL % 16 == 0 && HPD % 16 == 0 && HST % 16 == 0,
+                "bulk copies need 16-byte spans");
+};
+
+template <int D, int R, int SCHEME>
+__global__ void __launch_bounds__(512, 1) recon_stream_kernel(const KArgs a) {
+  using T = float;
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  using Q = StreamShape<D, R>;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, ND = L::ND, PDS = L::PDS;
+  constexpr int NK = S::NK, M = S::M, NP = S::NP, NQ = L::NQ;
+  constexpr int CPW = Q::CPW, MC = Q::MC, NCH = Q::NCH, NST = Q::NST;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int W = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  T *const sPhi = reinterpret_cast<T *>(smem);
+  unsigned char *const wbase = smem + Q::PHI_BYTES + (size_t)warp * Q::WARP_BYTES;
+  uint64_t *const bars = reinterpret_cast<uint64_t *>(smem + Q::PHI_BYTES + (size_t)W * Q::WARP_BYTES);
+  uint64_t *const hbar = bars + warp * (2 + NST);  // the two header buffers
+  uint64_t *const pbar = hbar + 2;                 // the NST chunk stages
+  uint64_t *const tbar = bars + W * (2 + NST);     // the test hook (block)
+  auto hdr = [&](int64_t it) { return wbase + (it & 1) * Q::HDR; };
+  auto stage = [&](int64_t q) { return wbase + 2 * Q::HDR + (q % NST) * Q::STAGE; };
+
+  const int64_t N = a.N;
+  const int64_t tiles = (N + CPW - 1) / CPW;
+  const int64_t gw = (int64_t)blockIdx.x * W + warp, TW = (int64_t)gridDim.x * W;
+  auto tile_of = [&](int64_t it) { return gw + it * TW; };
+  // lane 0 only: the header of tile iteration it, chunk q (tile iteration q / NCH, chunk q % NCH)
+  auto issue_hdr = [&](int64_t it) {
+    const int64_t t = tile_of(it);
+    if (t >= tiles) return;
+    const int64_t c0 = t * CPW;
+    const uint32_t n = (uint32_t)min((int64_t)CPW, N - c0);
+    uint64_t *bar = &hbar[it & 1];
+    mbar_arrive_expect_tx(bar, n * (uint32_t)(NF * PDS * 4 + M * 4));
+    bulk_copy_g2s(hdr(it), (const float *)a.Pd + c0 * (NF * PDS), n * (uint32_t)(NF * PDS * 4), bar);
+    bulk_copy_g2s(hdr(it) + Q::HPD, a.st + c0 * M, n * (uint32_t)(M * 4), bar);
+  };
+  auto issue_chunk = [&](int64_t q) {
+    const int64_t t = tile_of(q / NCH);
+    if (t >= tiles) return;
+    const int c = (int)(q % NCH);
+    const int64_t c0 = t * CPW;
+    const int n = (int)min((int64_t)CPW, N - c0);
+    uint64_t *bar = &pbar[q % NST];
+    mbar_arrive_expect_tx(bar, (uint32_t)(n * Q::CHUNK_CELL));
+    for (int g = 0; g < n; ++g)
+      bulk_copy_g2s(stage(q) + g * Q::CHUNK_CELL,
+                    (const float *)a.Pc + (c0 + g) * (int64_t)(M * NK) + c * (MC * NK), Q::CHUNK_CELL, bar);
+  };
+  // a bounded wait of the whole warp; false (in every lane) when any lane's wait ran out
+  auto wait_all = [&](uint64_t *bar, uint32_t parity) {
+    const bool ok = mbar_wait(bar, parity, kStageWaitNs);
+    return !__any_sync(0xffffffffu, !ok);
+  };
+  // timeout path: report it, let this warp's copies in flight land (bounded), then stop
+  auto give_up = [&](int64_t it, int64_t q, int64_t qi) {
+    if (lane == 0) {
+      atomicOr(a.err, kErrTimeout);
+      for (int64_t h = it; h < it + 2; ++h)
+        if (tile_of(h) < tiles) mbar_wait(&hbar[h & 1], (uint32_t)((h >> 1) & 1), kStageWaitNs);
+      for (int64_t c = q; c < qi; ++c)
+        if (tile_of(c / NCH) < tiles) mbar_wait(&pbar[c % NST], (uint32_t)((c / NST) & 1), kStageWaitNs);
+    }
+    __syncwarp();
+  };
+
+  if (lane == 0) {
+    for (int b = 0; b < 2 + NST; ++b) mbar_init(&hbar[b], 1);
+    if (threadIdx.x == 0) mbar_init(tbar, 1);
+    fence_barrier_init();
+  }
+  if constexpr (D == 3) {
+    const DevTables &tb = *a.tab;
+    for (int t = threadIdx.x; t < Q::NPHI; t += blockDim.x) {
+      const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
+      sPhi[t] = (T)tb.Phi[f][p][q][k];
+    }
+  }
+  __syncthreads();
+  // the operator records do not depend on the previous kernel: their copies start now
+  if (lane == 0) {
+    issue_hdr(0);
+    issue_hdr(1);
+    for (int64_t q = 0; q < NST; ++q) issue_chunk(q);
+  }
+  if (a.test_wait_ns) {  // test hook: a bounded wait on a barrier that nothing completes runs out
+    bool ok = true;
+    if (threadIdx.x == 0) ok = mbar_wait(tbar, 0, a.test_wait_ns);
+    if (__syncthreads_or(!ok)) {
+      give_up(0, 0, NST);
+      return;
+    }
+  }
+  pdl_wait(a);  // states written by the previous stage's update
+  if (a.dt_swap && blockIdx.x == 0)
+    for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {
+      a.dt[t] = a.dt[a.nmesh + t];
+      a.dt[a.nmesh + t] = 1e300;
+    }
+
+  const int grp = lane / NV, v = lane - grp * NV;
+  int64_t q = 0, qi = NST;  // next chunk to consume / to issue
+  for (int64_t it = 0; tile_of(it) < tiles; ++it) {
+    const int64_t c0 = tile_of(it) * CPW;
+    const int nvalid = (int)min((int64_t)CPW, N - c0);
+    const bool active = grp < CPW && grp < nvalid;
+    const int g = active ? grp : nvalid - 1;  // spare lanes shadow a valid cell of the tile
+    const int64_t i = c0 + g;
+    const float2 own = __ldg(reinterpret_cast<const float2 *>(a.U32) + i * NVP + v);
+    const T U0 = own.x;
+    const float L0 = own.y;
+    const uint32_t info = __ldg(a.cinfo + i);
+    if (!wait_all(&hbar[it & 1], (uint32_t)((it >> 1) & 1))) {
+      give_up(it, q, qi);
+      return;
+    }
+    const T *__restrict__ Pd_s = reinterpret_cast<const T *>(hdr(it)) + g * (NF * PDS);
+    const int32_t *__restrict__ st_s = reinterpret_cast<const int32_t *>(hdr(it) + Q::HPD) + g * M;
+    auto delta = [&](int32_t j) -> T {
+      const float2 h = __ldg(reinterpret_cast<const float2 *>(a.U32) + (int64_t)j * NVP + v);
+      return (h.x - U0) + (h.y - L0);
+    };
+
+    // central coefficients of variable v, chunk after chunk
+    T ao[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) ao[k] = (T)0;
+#pragma unroll 1
+    for (int c = 0; c < NCH; ++c, ++q) {
+      T du[MC];
+#pragma unroll
+      for (int mm = 0; mm < MC; mm += 4) {
+        const int4 j4 = *reinterpret_cast<const int4 *>(st_s + c * MC + mm);
+        du[mm] = delta(j4.x);
+        du[mm + 1] = delta(j4.y);
+        du[mm + 2] = delta(j4.z);
+        du[mm + 3] = delta(j4.w);
+      }
+      if (!wait_all(&pbar[q % NST], (uint32_t)((q / NST) & 1))) {
+        give_up(it, q, qi);
+        return;
+      }
+      const T *__restrict__ P_s = reinterpret_cast<const T *>(stage(q)) + g * (MC * NK);
+      T pb[4];
+#pragma unroll
+      for (int e = 0; e < MC * NK; ++e) {
+        if (e % 4 == 0) load16<T, 4, true>(P_s + e, pb);
+        ao[e % NK] += pb[e % 4] * du[e / NK];
+      }
+      __syncwarp();  // every lane is done with this stage
+      if (lane == 0) {
+        fence_proxy_async_shared();
+        issue_chunk(qi);
+      }
+      ++qi;
+    }
+
+    // directional coefficients (degree 1): members of face f are the next slots of the list
+    const uint32_t adm = (info >> kInfoAdmShift) & 0xFu;
+    T ad[NF][D];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int k = 0; k < D; ++k) ad[f][k] = (T)0;
+    {
+      int off = 0;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const int nm = (info >> (4 * f)) & 15u;
+        if ((adm >> f) & 1u) {
+          T pf[PDS];
+          load16<T, PDS, true>(Pd_s + f * PDS, pf);
+#pragma unroll
+          for (int jj = 0; jj < ND; ++jj) {
+            if (jj < nm) {
+              const T du = delta(st_s[off + jj]);
+#pragma unroll
+              for (int k = 0; k < D; ++k) ad[f][k] += pf[jj * D + k] * du;
+            }
+          }
+        }
+        off += nm;
+      }
+    }
+    lane_finish<D, R, T, SCHEME>(a, i, active, v, grp * NV, ao, ad, info, U0, L0, sPhi);
+    __syncwarp();  // every lane is done with this header
+    if (lane == 0) {
+      fence_proxy_async_shared();
+      issue_hdr(it + 2);
+    }
+  }
+}
+
+template <int D, int R, int SCHEME>
+void launch_recon_stream(const KArgs &a, int warps, cudaStream_t s) {
+  using Q = StreamShape<D, R>;
+  const int threads = 32 * warps;
+  const size_t smem = (size_t)recon_stream_smem(D, R, warps);
+  auto kern = recon_stream_kernel<D, R, SCHEME>;
+  static int resident[17] = {}, sms = 0;
+  int &nb = resident[warps];
+  if (!nb) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStreamSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+    if (nb < 1) nb = 1;  // a launch that cannot fit fails loudly below
+  }
+  const int64_t tiles = (a.N + Q::CPW - 1) / Q::CPW;
+  const int64_t blocks = (tiles + warps - 1) / warps;
+  const unsigned grid = (unsigned)std::min<int64_t>(blocks, (int64_t)nb * sms);
+  launch_stage_kernel(kern, grid, threads, smem, s, a);
 }
 
 template <int D, int R, int SCHEME, bool ONE>

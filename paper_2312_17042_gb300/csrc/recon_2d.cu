@@ -3,9 +3,9 @@
 
 namespace cteno {
 
-void launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s) {
+cudaError_t launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s) {
   if (block == kHaloLanes || block == kHaloLanes + 1) {  // gather-staged lane schedule (mixed)
-    if (!fp32) return;
+    if (!fp32) return cudaErrorInvalidValue;  // mixed path only
     const bool one = block == kHaloLanes + 1;  // one tile per block, single stage
 #define CTENO_HALO(R, SC) \
   (one ? launch_recon_halo<2, R, SC, true>(a, s) : launch_recon_halo<2, R, SC, false>(a, s))
@@ -14,13 +14,22 @@ void launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, int block
     if (degree == 3 && scheme == 0) CTENO_HALO(3, 0);
     if (degree == 3 && scheme == 1) CTENO_HALO(3, 1);
 #undef CTENO_HALO
-    return;
+    return cudaSuccess;
+  }
+  if (block > kStreamLanes && block <= kStreamLanes + 16) {  // streamed lane schedule (mixed)
+    if (!fp32) return cudaErrorInvalidValue;  // mixed path only
+    const int warps = block - kStreamLanes;
+    if (degree == 2 && scheme == 0) launch_recon_stream<2, 2, 0>(a, warps, s);
+    if (degree == 2 && scheme == 1) launch_recon_stream<2, 2, 1>(a, warps, s);
+    if (degree == 3 && scheme == 0) launch_recon_stream<2, 3, 0>(a, warps, s);
+    if (degree == 3 && scheme == 1) launch_recon_stream<2, 3, 1>(a, warps, s);
+    return cudaSuccess;
   }
   if (block >= kStagedCells) {  // staged persistent schedules (mixed path; the launch value is
                                 // validated by the caller)
     const bool lanes = block >= kStagedLanes;
     const int threads = block - (lanes ? kStagedLanes : kStagedCells);
-    if (!fp32) return;
+    if (!fp32) return cudaErrorInvalidValue;  // mixed path only
 #define CTENO_STAGED(R, SC) \
   (lanes ? launch_recon_staged<2, R, float, SC, true>(a, threads, s) : launch_recon_staged<2, R, float, SC, false>(a, threads, s))
     if (degree == 2 && scheme == 0) CTENO_STAGED(2, 0);
@@ -28,7 +37,7 @@ void launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, int block
     if (degree == 3 && scheme == 0) CTENO_STAGED(3, 0);
     if (degree == 3 && scheme == 1) CTENO_STAGED(3, 1);
 #undef CTENO_STAGED
-    return;
+    return cudaSuccess;
   }
   if (block >= kLaneSchedule) {  // variable-per-lane schedule, block - kLaneSchedule threads
     const int threads = block - kLaneSchedule, cpw = 32 / (2 + 2);
@@ -44,7 +53,7 @@ void launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, int block
     if (degree == 3 && !fp32 && scheme == 0) CTENO_LANES(3, double, 0);
     if (degree == 3 && !fp32 && scheme == 1) CTENO_LANES(3, double, 1);
 #undef CTENO_LANES
-    return;
+    return cudaSuccess;
   }
   const bool capped = block < 0;  // register-capped variant (FP32 only)
   if (capped) block = -block;
@@ -59,6 +68,7 @@ void launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, int block
   if (degree == 3 && !fp32 && scheme == 0) CTENO_RECON(3, double, 0, 0);
   if (degree == 3 && !fp32 && scheme == 1) CTENO_RECON(3, double, 1, 0);
 #undef CTENO_RECON
+  return cudaSuccess;
 }
 
 cudaError_t upload_recon_tables_2d(int degree, const Tables &t, cudaStream_t s) {

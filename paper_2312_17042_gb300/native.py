@@ -25,7 +25,7 @@ class CtenoError(RuntimeError):
 
 class cteno_params(C.Structure):
     _fields_ = [("dim", C.c_int), ("degree", C.c_int), ("scheme", C.c_int), ("precision", C.c_int),
-                ("lam_gamma", C.c_int), ("positivity_guard", C.c_int), ("C_T", C.c_double),
+                ("lam_gamma", C.c_int), ("positivity_guard", C.c_int), ("ctenoz_form", C.c_int), ("C_T", C.c_double),
                 ("lambda1p", C.c_double), ("eps", C.c_double), ("cfl", C.c_double),
                 ("gamma", C.c_double)]
 
@@ -71,6 +71,7 @@ def load_library():
         "cteno_set_timing": (I, [V, I]),
         "cteno_last_kernel_ms": (I, [V, V]),
         "cteno_measure_alu_peak": (I, [P(D), P(D)]),
+        "cteno_test_wait_timeout": (I, [V, I64]),
         "cteno_last_error": (C.c_char_p, [V]),
         "cteno_destroy": (None, [V]),
     }
@@ -135,7 +136,11 @@ def cteno_set_state(ctx, mesh_id: int, U, is_device: bool = False):
         _check(ctx, load_library().cteno_set_state(ctx, mesh_id, _ptr(U), 0))
 
 
-def cteno_rk_stage(ctx, stage: int, dt):
+def cteno_rk_stage(ctx, stage: int, dt=None):
+    """dt: the time step of each mesh, or None for the CFL step of the current state (stage 0)."""
+    if dt is None:
+        _check(ctx, load_library().cteno_rk_stage(ctx, stage, None))
+        return
     dt = np.ascontiguousarray(np.atleast_1d(dt), np.float64)
     _check(ctx, load_library().cteno_rk_stage(ctx, stage, _ptr(dt)))
 
@@ -275,6 +280,10 @@ def cteno_measure_alu_peak():
     return a.value, b.value
 
 
+def cteno_test_wait_timeout(ctx, limit_ns: int):
+    _check(ctx, load_library().cteno_test_wait_timeout(ctx, int(limit_ns)))
+
+
 def cteno_last_error(ctx) -> str:
     m = load_library().cteno_last_error(ctx)
     return m.decode() if m else ""
@@ -323,10 +332,10 @@ class Solver:
     def get_state(self, mesh_id: int = 0):
         return cteno_get_state(self.ctx, mesh_id)
 
-    def stage(self, s: int, dt):
+    def stage(self, s: int, dt=None):
         cteno_rk_stage(self.ctx, s, dt)
 
-    def step(self, dt):
+    def step(self, dt=None):
         for s in range(3):
             cteno_rk_stage(self.ctx, s, dt)
 

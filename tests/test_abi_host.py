@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 def test_parameter_validation_without_gpu():
     native = _lib()
     p = native.cteno_default_params()
-    assert (p.dim, p.degree, p.C_T, p.lambda1p, p.eps) == (2, 2, 1e-6, 1e15, 1e-40)
+    assert (p.dim, p.degree, p.C_T, p.lambda1p, p.eps, p.ctenoz_form) == (2, 2, 1e-6, 1e15, 1e-24, 0)
     p.degree = 5
     with pytest.raises(native.CtenoError):
         native.cteno_create(p)

@@ -4,15 +4,12 @@ seeded inputs.
 Tolerances: the FP64 path must match the oracle to max relative 1e-12 (per state component,
 relative to the component's max magnitude) after 10 steps; reconstructed face states of one stage
 to 1e-12; selection flags exactly. The mixed path (FP32 reconstruction and flux, FP64
-accumulation) keeps flags equal except where the oracle's decision is ambiguous (chi within 1e-4
-of the cut-off, or a decision that changes when the smoothness indicators move by the rounding
-floor of the data), and its L1 density error within 1.05x of the FP64 path's on smooth problems.
+accumulation) keeps flags equal except in (cell, variable) pairs where one of the oracle's chi_s
+lies within 1e-4 (relative) of the cut-off C_T, and its L1 density error within 1.05x of the FP64
+path's on smooth problems.
 
-Multi-step FP64 comparisons of CTENOZ on discontinuous data use eps = 1e-24. With eps = 1e-40 the
-CTENOZ decision in a cell whose directional stencil is flat to rounding compares tau with that
-stencil's rounding-noise indicator (~1e-35); two correct FP64 evaluations can then choose
-differently (the oracle's own choice depends on its rounding). eps = 1e-24 lies above the FP64
-rounding floor of the indicators for |U| <= 25, so the decision depends on resolved data only.
+All cases run at the library's default eps = 1e-24 (the oracle's too): above the rounding floor of
+the smoothness indicators of both paths, so no decision of either side depends on rounding.
 """
 from __future__ import annotations
 
@@ -59,17 +56,17 @@ SCHEDULES = [(128, 128), (1024 + 256, 1024 + 128)]
 
 
 @pytest.mark.parametrize("launch", SCHEDULES, ids=["cell-thread", "var-lanes"])
-@pytest.mark.parametrize("scheme", [0, 1], ids=["CTENO", "CTENOZ"])
+@pytest.mark.parametrize("scheme,form", [(0, 0), (1, 0), (1, 1)], ids=["CTENO", "CTENOZ", "CTENOZ-wenoz"])
 @pytest.mark.parametrize("name,make,degree", CASES, ids=[c[0] for c in CASES])
-def test_one_stage_face_states_flags_and_update(name, make, degree, scheme, launch):
+def test_one_stage_face_states_flags_and_update(name, make, degree, scheme, form, launch):
     native = _native()
     from oracle import Oracle
     wl = make()
     d = wl.mesh.dim
-    o = Oracle(wl.mesh, degree=degree, scheme=scheme)
+    o = Oracle(wl.mesh, degree=degree, scheme=scheme, ctenoz_form=form)
     o.set_state(wl.U0)
     dt = 0.5 * o.dt()
-    s = _solver(native, [wl.mesh], d, degree=degree, scheme=scheme)
+    s = _solver(native, [wl.mesh], d, degree=degree, scheme=scheme, ctenoz_form=form)
     native.cteno_set_launch(s.ctx, *launch)
     native.cteno_record_flags(s.ctx, True)
     s.set_state(wl.U0)
@@ -114,11 +111,10 @@ def test_shock_tube_fp64_matches_oracle(scheme, degree):
     native = _native()
     from oracle import Oracle
     wl = W.shock_tube_2d(64, 16)
-    eps = 1e-40 if scheme == 0 else 1e-24
-    o = Oracle(wl.mesh, degree=degree, scheme=scheme, cfl=0.4, eps=eps)
+    o = Oracle(wl.mesh, degree=degree, scheme=scheme, cfl=0.4)
     o.set_state(wl.U0)
     o.run(10)
-    s = _solver(native, [wl.mesh], 2, degree=degree, scheme=scheme, cfl=0.4, eps=eps)
+    s = _solver(native, [wl.mesh], 2, degree=degree, scheme=scheme, cfl=0.4)
     s.set_state(wl.U0)
     s.run(10)
     assert _relerr(s.get_state(), o.get_state()) < FP64_TOL
@@ -175,13 +171,13 @@ def test_batched_meshes_match_independent_oracles():
     native = _native()
     from oracle import Oracle
     wls = W.quadrants_batch(n_meshes=4, seed=3, nmin=8, nmax=20)
-    s = _solver(native, [w.mesh for w in wls], 2, degree=2, scheme=1, cfl=0.4, eps=1e-24)
+    s = _solver(native, [w.mesh for w in wls], 2, degree=2, scheme=1, cfl=0.4)
     for k, w in enumerate(wls):
         s.set_state(w.U0, k)
     s.run(5)
     dts = s.dt()
     for k, w in enumerate(wls):
-        o = Oracle(w.mesh, degree=2, scheme=1, cfl=0.4, eps=1e-24)
+        o = Oracle(w.mesh, degree=2, scheme=1, cfl=0.4)
         o.set_state(w.U0)
         d_o = o.run(5)
         assert abs(dts[k] - d_o[-1]) < 1e-13 * d_o[-1]
@@ -200,14 +196,29 @@ def _staged_smem(d, degree, launch):
 
 
 STAGED_SMEM_MAX = 200 * 1024
+STREAM_SMEM_MAX = 227 * 1024
+
+
+def _stream_smem(d, degree, warps):
+    """Shared memory of the streamed lane schedule: per warp two tile headers (directional
+    operators, stencil ids) and four chunk stages of 8 (or 4) members' operator rows per cell."""
+    nk = ((degree + 1) * (degree + 2) // 2 if d == 2 else (degree + 1) * (degree + 2) * (degree + 3) // 6) - 1
+    M = 2 * (nk + 1)
+    cpw = 32 // (d + 2)
+    mc = 8 if M % 8 == 0 else 4
+    hdr = cpw * (d + 1) * (8 if d == 2 else 20) * 4 + cpw * M * 4
+    phi = (((d + 1) * 6 * 4 * nk if d == 3 else 1) * 4 + 15) // 16 * 16
+    return phi + warps * (2 * hdr + 4 * cpw * mc * nk * 4) + warps * 6 * 8 + 8
 
 
 @pytest.mark.parametrize("launch", [(128, 128), (-128, -128), (1024 + 128, 1024 + 256), (1024 + 256, 256),
                                     (2048 + 32, 128), (2048 + 64, -128), (3072 + 64, 1024 + 128),
-                                    (3072 + 128, 256), (3072 + 256, 128), (4096, 128), (4097, 8192 + 128)],
+                                    (3072 + 128, 256), (3072 + 256, 128), (4096, 128), (4097, 8192 + 128),
+                                    (5120 + 1, 128), (5120 + 4, 8192 + 128), (5120 + 10, 128), (5120 + 16, 128)],
                          ids=["cell-thread", "capped", "var-lanes-128", "var-lanes-256", "staged-cells-32",
                               "staged-cells-64", "staged-lanes-64", "staged-lanes-128", "staged-lanes-256",
-                              "gather-staged", "gather-staged-one-tile"])
+                              "gather-staged", "gather-staged-one-tile", "streamed-1", "streamed-4",
+                              "streamed-10", "streamed-16"])
 def test_mixed_schedules_agree(launch):
     """Every launch schedule of the mixed path gives the same face states and update on a 2D and a
     3D mesh (the arithmetic per variable is the same in each schedule). A staged schedule whose two
@@ -225,6 +236,11 @@ def test_mixed_schedules_agree(launch):
                 s.close()
                 continue
         if launch[0] in range(2048, 4096) and _staged_smem(d, deg, launch[0]) > STAGED_SMEM_MAX:
+            with pytest.raises(native.CtenoError):
+                native.cteno_set_launch(s.ctx, *launch)
+            s.close()
+            continue
+        if launch[0] > 5120 and _stream_smem(d, deg, launch[0] - 5120) > STREAM_SMEM_MAX:
             with pytest.raises(native.CtenoError):
                 native.cteno_set_launch(s.ctx, *launch)
             s.close()
@@ -274,10 +290,30 @@ def test_mixed_precision_flags_and_accuracy_on_density_wave():
     s.close()
 
 
+def flag_band(o, rel=1e-4):
+    """(cell, variable) pairs whose oracle decision lies in the contract's band: some admissible
+    chi_s (eq. 22, from the oracle's last reconstruction) within rel * C_T of the cut-off."""
+    chi = o.chi()
+    mask = o.stencil_mask()
+    adm = np.stack([np.ones_like(mask, bool)] + [(mask >> (1 + f)) & 1 == 1 for f in range(o.nf)], axis=1)
+    near = np.abs(chi - o.p["C_T"]) <= rel * o.p["C_T"]
+    return (near & adm[:, None, :]).any(axis=2)
+
+
+def assert_flags_within_contract(fl, o, min_compared=1):
+    """Mixed-path flags equal the oracle's outside the 1e-4 band; returns (#in band, #compared)."""
+    ref = o.flags()
+    band = flag_band(o)
+    bad = (fl != ref) & ~band
+    assert not bad.any(), (int(bad.sum()), np.argwhere(bad)[:10])
+    assert (~band).sum() >= min_compared
+    return int(band.sum()), int((~band).sum())
+
+
 @pytest.mark.parametrize("scheme", [0, 1], ids=["CTENO", "CTENOZ"])
 def test_mixed_precision_flags_at_shocks(scheme):
-    """Sod: mixed-path flags equal the oracle's except where the oracle's chi_1 lies within 1e-4
-    (relative) of the cut-off."""
+    """Sod after 5 oracle steps: one mixed-path reconstruction from the oracle's state. Its flags
+    equal the oracle's except where some chi_s lies within 1e-4 (relative) of the cut-off."""
     native = _native()
     from oracle import Oracle
     wl = W.shock_tube_2d(64, 16)
@@ -291,70 +327,28 @@ def test_mixed_precision_flags_at_shocks(scheme):
     s.set_state(U)
     s.stage(0, 1e-5)
     fl = native.cteno_get_flags(s.ctx, 0)
-    ref = o.flags()
-    diff = fl != ref
-    amb = _ambiguous(o, scheme, U)
-    assert not (diff & ~amb).any(), np.argwhere(diff & ~amb)[:10]
-    # not vacuous. CTENO: resolved decisions that drop the central stencil are compared. CTENOZ
-    # at eps = 1e-40: every such decision on this problem is rounding-driven (see the module
-    # docstring), so the check is that most decisions are resolved and compared.
-    if scheme == 0:
-        assert (~amb & ((ref & 1) == 0)).sum() >= 20
-    else:
-        assert (~amb).mean() > 0.5
+    nband, ncmp = assert_flags_within_contract(fl, o, min_compared=1000)
+    # not vacuous: resolved decisions that drop the central stencil are among those compared
+    assert (((o.flags() & 1) == 0) & ~flag_band(o)).sum() >= 20
+    print(f"flags in the 1e-4 band: {nband}, compared: {ncmp}")
     s.close()
-
-
-def _chi(si, st, scheme, eps, lam1):
-    lams = (1 - lam1) / (st - 1) if st > 1 else 0.0
-    if scheme == 0:
-        g = 1.0 / (si + eps) ** 6
-    else:
-        tau = (np.abs(si[1:] - si[0]).sum() / (st - 1)) ** 6 if st > 1 else 0.0
-        g = 1 + tau / (si + eps)
-    g = g * np.array([lam1] + [lams] * (st - 1))
-    return g / g.sum()
-
-
-def _ambiguous(o, scheme, U, rel=1e-4, noise=1e-12):
-    """Cells/variables whose oracle decision is not resolved: some chi_s within rel of C_T, or a
-    delta that changes when the indicators move by the rounding floor (noise * max|U_v|)^2."""
-    SI = o.smoothness_indicators()
-    mask = o.stencil_mask()
-    out = np.zeros(SI.shape[:2], bool)
-    C_T, eps = o.p["C_T"], o.p["eps"]
-    lam1 = 1 - 1 / o.p["lambda1p"]
-    floor = (noise * np.abs(U).max(axis=1)) ** 2
-    for i in range(SI.shape[0]):
-        adm = [0] + [1 + f for f in range(o.nf) if mask[i] >> (1 + f) & 1]
-        st = len(adm)
-        for v in range(SI.shape[1]):
-            si = SI[i, v, adm]
-            chi = _chi(si, st, scheme, eps, lam1)
-            base = chi >= C_T
-            amb = bool(np.any(np.abs(chi - C_T) <= rel * C_T))
-            for sc, sd in ((1, 1), (-1, -1), (1, -1), (-1, 1)):
-                pert = si.copy()
-                pert[0] = max(pert[0] + sc * floor[v], 0.0)
-                pert[1:] = np.maximum(pert[1:] + sd * floor[v], 0.0)
-                amb = amb or bool(np.any((_chi(pert, st, scheme, eps, lam1) >= C_T) != base))
-            out[i, v] = amb
-    return out
 
 
 def test_full_size_shock_tube_sampled_residual():
     """512x128 shock tube (131072 cells), the launch configuration the benchmark times: one
-    FP64 stage on the GPU against the oracle's residual at sampled cells near the discontinuity
-    and elsewhere."""
+    FP64 stage on the GPU against U + dt R with the oracle's residual R at sampled cells near the
+    discontinuity and elsewhere, relative to each component's max magnitude."""
     native = _native()
     from oracle import Oracle
     wl = W.shock_tube_2d(512, 128)
     for scheme, degree in ((0, 2), (1, 3)):
         s = _solver(native, [wl.mesh], 2, degree=degree, scheme=scheme, cfl=0.4)
         s.set_state(wl.U0)
-        dt = 1e-4
+        native.cteno_autotune(s.ctx)   # times kernels on the current state
+        s.set_state(wl.U0)
+        dt = 5e-4
         s.stage(0, dt)
-        R_gpu = (s.get_state() - wl.U0) / dt
+        U1 = s.get_state()
         o = Oracle(wl.mesh, setup=False, degree=degree, scheme=scheme)
         o.set_state(wl.U0)
         cen = W.cell_centroids(wl.mesh)
@@ -363,8 +357,8 @@ def test_full_size_shock_tube_sampled_residual():
         ids = np.concatenate([rng.choice(near, 40, replace=False),
                               rng.choice(wl.mesh.ncells, 40, replace=False)])
         R_orc = o.residual_cells(ids)
-        scale = np.abs(R_orc).max(axis=0) + 1e-300
-        assert (np.abs(R_gpu[:, ids].T - R_orc) / scale).max() < 1e-11
+        ref = wl.U0[:, ids].T + dt * R_orc
+        assert (np.abs(U1[:, ids].T - ref) / np.abs(wl.U0).max(axis=1)).max() < FP64_TOL
         s.close()
 
 
@@ -485,6 +479,35 @@ def test_launch_and_host_access_switches_do_not_change_results(monkeypatch):
     assert np.array_equal(results[0], results[1]) and np.array_equal(results[0], results[2])
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_rk_stage_with_cfl_time_step(precision):
+    """cteno_rk_stage(ctx, s, NULL): stage 0 takes each mesh's CFL step of the current state and
+    stages 1, 2 keep it, which is what cteno_run does: three such stages equal cteno_run(1) bit for
+    bit, and the step equals the oracle's (FP64)."""
+    native = _native()
+    from oracle import Oracle
+    wls = W.quadrants_batch(3, seed=2, nmin=12, nmax=20)
+    meshes = [w.mesh for w in wls]
+    a = _solver(native, meshes, 2, degree=2, scheme=1, precision=precision, cfl=0.4)
+    b = _solver(native, meshes, 2, degree=2, scheme=1, precision=precision, cfl=0.4)
+    for k, w in enumerate(wls):
+        a.set_state(w.U0, k)
+        b.set_state(w.U0, k)
+    for _ in range(3):
+        a.step(None)
+        b.run(1)
+    for k in range(3):
+        assert np.array_equal(a.get_state(k), b.get_state(k))
+    assert np.array_equal(a.dt(), b.dt())
+    if precision == 0:
+        o = Oracle(wls[1].mesh, degree=2, scheme=1, cfl=0.4)
+        o.set_state(wls[1].U0)
+        d_o = o.run(3)
+        assert abs(a.dt()[1] - d_o[-1]) < 1e-13 * d_o[-1]
+    a.close()
+    b.close()
+
+
 def test_rejects_bad_calls_without_faulting():
     native = _native()
     wl = W.density_wave_2d(8)
@@ -503,6 +526,10 @@ def test_rejects_bad_calls_without_faulting():
         native.cteno_set_launch(s.ctx, 4096, 0)          # gather staging: mixed path only
     with pytest.raises(native.CtenoError):
         native.cteno_set_launch(s.ctx, 8192 + 128, 0)    # the face-based schedule is a flux schedule
+    with pytest.raises(native.CtenoError):
+        native.cteno_set_launch(s.ctx, 5120 + 8, 0)      # streamed lanes: mixed path only
+    with pytest.raises(native.CtenoError):
+        native.cteno_set_launch(s.ctx, 5120 + 17, 0)     # at most 16 warps
     s.set_state(wl.U0)
     s.run(1)
     assert s.sync() == 0
