@@ -230,6 +230,8 @@ def alu_peak(native):
 def recon_kernel_name(dim, degree, scheme, precision, launch):
     """Name of the reconstruction kernel a launch value selects."""
     args = f"{dim},{degree},{'float' if precision else 'double'},{SCHEMES[scheme]}"
+    if 5120 < launch <= 5136:
+        return f"recon_stream_kernel<{args}> x{32 * (launch - 5120)}"
     if launch in (4096, 4097):
         return f"recon_halo_kernel<{args},{'one-tile' if launch == 4097 else 'persistent'}> x128"
     if launch >= 3072:

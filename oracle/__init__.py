@@ -58,6 +58,7 @@ def _load():
     lib.orc_get_flags.argtypes = [V, _u8]
     lib.orc_get_si.argtypes = [V, _dp]
     lib.orc_get_stmask.argtypes = [V, _ip]
+    lib.orc_get_guarded.argtypes = [V, _u8]
     lib.orc_get_coeffs.argtypes = [V, _dp]
     lib.orc_get_refmap.argtypes = [V, C.c_int, _dp, _dp]
     lib.orc_get_exponents.argtypes = [V, _ip]
@@ -266,6 +267,12 @@ class Oracle:
 
     def psibar(self):
         return np.array([self.lib.orc_psibar(self.h, k) for k in range(self.nk)])
+
+    def guarded(self):
+        """Cells whose last reconstruction fell back to the cell mean (positivity guard)."""
+        out = np.empty(self.ncells, np.uint8)
+        self.lib.orc_get_guarded(self.h, out)
+        return out.astype(bool)
 
     def nguard(self) -> int:
         info = np.zeros(8, np.int32)

@@ -95,6 +95,7 @@ typedef struct {
   double *chi;                  /* [ncells][nv][1+nf] chi_s of eq. 22, 0 where inadmissible (debug) */
   double *coef;                 /* [ncells][nv][nk] final polynomial coefficients (debug) */
   int *stmask;                  /* [ncells]: bit 0 central, bit 1+f admissible directional f */
+  uint8_t *guarded;             /* [ncells]: the last reconstruction fell back to the mean (debug) */
   int nguard;
   int err;
 } orc;
@@ -903,6 +904,7 @@ static void recon_cell(orc *o, int i, const double *U) {
     for (int q = 0; q < nq; ++q)
       for (int v = 0; v < nv; ++v)
         o->face[(((size_t)i * nf + f) * nq + q) * nv + v] = fout[f][q][v];
+  o->guarded[i] = (uint8_t)guard_hit;
   if (guard_hit) {
 #pragma omp atomic
     o->nguard++;
@@ -1105,6 +1107,7 @@ orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form,
   o->SI = (double *)calloc(n * o->nv * (1 + o->nf), sizeof(double));
   o->chi = (double *)calloc(n * o->nv * (1 + o->nf), sizeof(double));
   o->stmask = (int *)calloc(n, sizeof(int));
+  o->guarded = (uint8_t *)calloc(n, 1);
   o->coef = (double *)calloc(n * o->nv * o->nk, sizeof(double));
   return o;
 }
@@ -1158,6 +1161,7 @@ void orc_destroy(orc *o) {
   free(o->v2c_off); free(o->v2c); free(o->qlam); free(o->qw);
   free(o->U); free(o->Un); free(o->Rres); free(o->face); free(o->flags); free(o->SI); free(o->chi);
   free(o->stmask);
+  free(o->guarded);
   free(o->coef);
   free(o);
 }
@@ -1308,6 +1312,7 @@ void orc_get_refmap(const orc *o, int i, double *X, double *Jinv) {
   memcpy(Jinv, o->Jinv + (size_t)i * d * d, sizeof(double) * d * d);
 }
 void orc_get_stmask(const orc *o, int *out) { memcpy(out, o->stmask, sizeof(int) * o->ncells); }
+void orc_get_guarded(const orc *o, uint8_t *out) { memcpy(out, o->guarded, (size_t)o->ncells); }
 void orc_get_exponents(const orc *o, int *ex) {
   for (int k = 0; k < o->nk; ++k)
     for (int j = 0; j < 3; ++j) ex[k * 3 + j] = o->ex[k][j];

@@ -310,26 +310,28 @@ def assert_flags_within_contract(fl, o, min_compared=1):
     return int(band.sum()), int((~band).sum())
 
 
-@pytest.mark.parametrize("scheme", [0, 1], ids=["CTENO", "CTENOZ"])
-def test_mixed_precision_flags_at_shocks(scheme):
+@pytest.mark.parametrize("scheme,form", [(0, 0), (1, 0), (1, 1)], ids=["CTENO", "CTENOZ", "CTENOZ-wenoz"])
+def test_mixed_precision_flags_at_shocks(scheme, form):
     """Sod after 5 oracle steps: one mixed-path reconstruction from the oracle's state. Its flags
     equal the oracle's except where some chi_s lies within 1e-4 (relative) of the cut-off."""
     native = _native()
     from oracle import Oracle
     wl = W.shock_tube_2d(64, 16)
-    o = Oracle(wl.mesh, degree=2, scheme=scheme)
+    o = Oracle(wl.mesh, degree=2, scheme=scheme, ctenoz_form=form)
     o.set_state(wl.U0)
     o.run(5)
     U = o.get_state()
     o.residual()
-    s = _solver(native, [wl.mesh], 2, degree=2, scheme=scheme, precision=1)
+    s = _solver(native, [wl.mesh], 2, degree=2, scheme=scheme, ctenoz_form=form, precision=1)
     native.cteno_record_flags(s.ctx, True)
     s.set_state(U)
     s.stage(0, 1e-5)
     fl = native.cteno_get_flags(s.ctx, 0)
     nband, ncmp = assert_flags_within_contract(fl, o, min_compared=1000)
-    # not vacuous: resolved decisions that drop the central stencil are among those compared
-    assert (((o.flags() & 1) == 0) & ~flag_band(o)).sum() >= 20
+    # not vacuous: resolved decisions that drop the central stencil are among those compared (the
+    # printed CTENOZ measure at eps = 1e-24 drops it only for jumps larger than this smeared one)
+    if (scheme, form) != (1, 0):
+        assert (((o.flags() & 1) == 0) & ~flag_band(o)).sum() >= 20
     print(f"flags in the 1e-4 band: {nband}, compared: {ncmp}")
     s.close()
 
