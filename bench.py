@@ -230,8 +230,12 @@ def alu_peak(native):
 def recon_kernel_name(dim, degree, scheme, precision, launch):
     """Name of the reconstruction kernel a launch value selects."""
     args = f"{dim},{degree},{'float' if precision else 'double'},{SCHEMES[scheme]}"
+    if 6144 < launch <= 6152:
+        return f"recon_stream_cells_kernel<{args}> x{32 * (launch - 6144)}"
     if 5120 < launch <= 5136:
-        return f"recon_stream_kernel<{args}> x{32 * (launch - 5120)}"
+        return f"recon_stream_kernel<{args},3 stages> x{32 * (launch - 5120)}"
+    if 5152 < launch <= 5168:
+        return f"recon_stream_kernel<{args},2 stages> x{32 * (launch - 5152)}"
     if launch in (4096, 4097):
         return f"recon_halo_kernel<{args},{'one-tile' if launch == 4097 else 'persistent'}> x128"
     if launch >= 3072:

@@ -220,9 +220,14 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
  * 4097 the same with one tile per block and a single stage (half the shared memory); both refused
  * like the staged values when they do not fit. 5120 + w (mixed path, w warps per block, 1..16)
  * selects the streamed lane schedule: every warp walks its own tiles of floor(32/(d+2)) cells and
- * streams their operator records through its own ring of shared-memory stages, in chunks of 4 or 8
- * stencil members per cell, several chunks ahead of the arithmetic (bounded waits as above);
- * refused when w warps' rings do not fit in the 227 KiB of shared memory of a block. Flux only:
+ * streams their operator records through its own ring of three shared-memory stages, in chunks of
+ * 8 (or 4) stencil members per cell, ahead of the arithmetic (bounded waits as above); 5152 + w the
+ * same with a two-stage ring; refused when w warps' rings do not fit in the 227 KiB of shared
+ * memory of a block. 6144 + w
+ * (mixed path, w warps per block, 1..8) selects the streamed thread-per-cell schedule: every warp
+ * walks tiles of 32 cells, one thread per cell, and each lane streams its own cell's operator
+ * record through the warp's ring of shared-memory stages four stencil members at a time; refused
+ * likewise when it does not fit. Flux only:
  * 8192 + b (b a multiple of 32 in
  * [32, 256]) selects the face-based schedule: HLLC once per face, in its owner's orientation, into
  * a face-flux array, then a per-cell gather and update (results bit-identical to the per-cell

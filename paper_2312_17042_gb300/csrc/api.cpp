@@ -848,8 +848,15 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
     if (b == 0) return true;
     if (b >= kFaceFlux)  // face-based flux schedule
       return !recon && b - kFaceFlux >= 32 && b - kFaceFlux <= 256 && b % 32 == 0;
-    if (b > kStreamLanes && b <= kStreamLanes + 16)  // streamed lanes: reconstruction, mixed, fits
-      return recon && ctx->fp32 && recon_stream_smem(ctx->d, ctx->p.degree, b - kStreamLanes) <= kMaxStreamSmem;
+    if (b > kStreamCells && b <= kStreamCells + 8)  // streamed cells: reconstruction, mixed, fits
+      return recon && ctx->fp32 &&
+             recon_stream_cells_smem(ctx->d, ctx->p.degree, b - kStreamCells) <= kMaxStreamSmem;
+    {
+      int w = 0, st = 0;
+      stream_launch(b, &w, &st);
+      if (w)  // streamed lanes: reconstruction, mixed, fits
+        return recon && ctx->fp32 && recon_stream_smem(ctx->d, ctx->p.degree, w, st) <= kMaxStreamSmem;
+    }
     if (b == kHaloLanes || b == kHaloLanes + 1)  // gather-staged: reconstruction, mixed, lists built, fits
       return recon && ctx->fp32 && ctx->hl &&
              recon_halo_smem(ctx->d, ctx->p.degree, ctx->hrec) / (b == kHaloLanes ? 1 : 2) <= kMaxStagedSmem;
@@ -920,9 +927,14 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
     if (hs / 2 <= kMaxStagedSmem) rcand.push_back(kHaloLanes + 1);
   }
   // the streamed lane schedule (mixed path) at the block sizes that fit
-  if (ctx->fp32)
-    for (int w : {4, 8, 10, 12, 16})
-      if (recon_stream_smem(ctx->d, ctx->p.degree, w) <= kMaxStreamSmem) rcand.push_back(kStreamLanes + w);
+  if (ctx->fp32) {
+    for (int w : {8, 12, 16}) {
+      if (recon_stream_smem(ctx->d, ctx->p.degree, w, 3) <= kMaxStreamSmem) rcand.push_back(kStreamLanes + w);
+      if (recon_stream_smem(ctx->d, ctx->p.degree, w, 2) <= kMaxStreamSmem) rcand.push_back(kStreamLanes2 + w);
+    }
+    for (int w : {2, 4, 6, 7, 8})
+      if (recon_stream_cells_smem(ctx->d, ctx->p.degree, w) <= kMaxStreamSmem) rcand.push_back(kStreamCells + w);
+  }
   const int reps = 5;
   float best_r = 1e30f, best_f = 1e30f;
   int br = ctx->recon_block, bf = ctx->flux_block;

@@ -159,19 +159,40 @@ constexpr int kHaloLanes = 4096;
 constexpr int kFaceFlux = 8192;
 constexpr int kHaloWarps = 4;
 // kStreamLanes + w (w warps per block, 1..16): the streamed lane schedule (mixed path): every warp
-// streams its tiles' operator records through its own ring of shared-memory stages.
+// streams its tiles' operator records through its own ring of three shared-memory stages;
+// kStreamLanes2 + w the same with two stages (a smaller ring, more warps).
 constexpr int kStreamLanes = 5120;
-constexpr int kStreamStages = 4;
+constexpr int kStreamLanes2 = 5152;
 constexpr int kMaxStreamSmem = 227 * 1024;  // the per-block limit of the GPU
-// Dynamic shared memory of the streamed schedule with `warps` warps (see StreamShape).
-inline long long recon_stream_smem(int d, int degree, int warps) {
+// kStreamCells + w (w warps per block, 1..8): the streamed thread-per-cell schedule (mixed path):
+// every warp walks tiles of 32 cells and each lane streams its own cell's operator record through
+// the warp's ring of shared-memory stages, four stencil members at a time.
+constexpr int kStreamCells = 6144;
+constexpr int kStreamCellStages = 3;
+inline long long recon_stream_cells_smem(int d, int degree, int warps) {
+  const int nk = (d == 2 ? (degree + 1) * (degree + 2) / 2 : (degree + 1) * (degree + 2) * (degree + 3) / 6) - 1;
+  const long long stage = 32LL * 4 * nk * 4;
+  const long long nphi = d == 3 ? (long long)(d + 1) * 6 * 4 * nk : 1;
+  const long long phi = (nphi * 4 + 15) / 16 * 16;
+  return phi + (long long)warps * kStreamCellStages * stage + (long long)warps * kStreamCellStages * 8 + 8;
+}
+// Dynamic shared memory of the streamed lane schedule with `warps` warps and `stages` stages (see
+// StreamShape).
+inline long long recon_stream_smem(int d, int degree, int warps, int stages) {
   const int nk = (d == 2 ? (degree + 1) * (degree + 2) / 2 : (degree + 1) * (degree + 2) * (degree + 3) / 6) - 1;
   const int M = 2 * (nk + 1), nv = d + 2, cpw = 32 / nv, mc = (M % 8 == 0) ? 8 : 4;
   const long long stage = (long long)cpw * mc * nk * 4;
   const long long hdr = (long long)cpw * (d + 1) * lay_pds(d) * 4 + (long long)cpw * M * 4;
   const long long nphi = d == 3 ? (long long)(d + 1) * 6 * 4 * nk : 1;
   const long long phi = (nphi * 4 + 15) / 16 * 16;
-  return phi + (long long)warps * (2 * hdr + kStreamStages * stage) + (long long)warps * (2 + kStreamStages) * 8 + 8;
+  return phi + (long long)warps * (2 * hdr + stages * stage) + (long long)warps * (2 + stages) * 8 + 8;
+}
+// Launch value -> (warps, stages) of the streamed lane schedule, or warps = 0.
+inline void stream_launch(int b, int *warps, int *stages) {
+  *warps = 0;
+  *stages = 0;
+  if (b > kStreamLanes && b <= kStreamLanes + 16) *warps = b - kStreamLanes, *stages = 3;
+  if (b > kStreamLanes2 && b <= kStreamLanes2 + 16) *warps = b - kStreamLanes2, *stages = 2;
 }
 inline int halo_tile(int d) { return kHaloWarps * (32 / (d + 2)); }
 inline int halo_ms(int M) { return (M + 1 + 7) / 8 * 8; }

@@ -237,22 +237,13 @@ __device__ __forceinline__ uint32_t select_fp32(float SI0, const float *SId, uin
 // One cell of the thread-per-cell schedule. Pci, Pdi, sti: the cell's central pseudo-inverse,
 // directional operators and stencil ids, in global memory (SH = false) or in a shared-memory copy
 // (SH = true); sPhi: 3D face-point basis values in shared memory.
-template <int D, int R, typename T, int SCHEME, bool SH>
-__device__ __forceinline__ void recon_cell(const KArgs &a, const int64_t i, const T *__restrict__ Pci,
-                                           const T *__restrict__ Pdi, const int32_t *__restrict__ sti,
-                                           const T *__restrict__ sPhi) {
-  using S = Shape<D, R>;
-  using L = Lay<D>;
-  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, ND = L::ND, PDS = L::PDS;
-  constexpr int NK = S::NK, M = S::M, NP = S::NP;
-  constexpr int CH = Vec16<T>::n;
-  constexpr bool F32 = sizeof(T) == 4;
-  const int64_t N = a.N;
-  // own cell means: FP64, or (mixed path) the FP32 pair hi + lo of every FP64 value, so that
-  // U_m - U_0 = (hi_m - hi_0) + (lo_m - lo_0) keeps FP64 accuracy in FP32 arithmetic
-  T U0[NV];
-  float L0[NV];
-  if constexpr (F32) {
+// Own cell means of cell i: FP64, or (mixed path) the FP32 pair hi + lo of every FP64 value, so
+// that U_m - U_0 = (hi_m - hi_0) + (lo_m - lo_0) keeps FP64 accuracy in FP32 arithmetic.
+template <int D, typename T>
+__device__ __forceinline__ void cell_own(const KArgs &a, const int64_t i, T (&U0)[Lay<D>::NV],
+                                         float (&L0)[Lay<D>::NV]) {
+  constexpr int NV = Lay<D>::NV, NVP = Lay<D>::NVP;
+  if constexpr (sizeof(T) == 4) {
     float hl[2 * NVP];
     load16<float, 2 * NVP>(a.U32 + i * 2 * NVP, hl);
 #pragma unroll
@@ -269,47 +260,43 @@ __device__ __forceinline__ void recon_cell(const KArgs &a, const int64_t i, cons
       L0[v] = 0.0f;
     }
   }
-  auto delta = [&](int64_t j, T *du) {
-    if constexpr (F32) {
-      float hl[2 * NVP];
-      load16<float, 2 * NVP>(a.U32 + j * 2 * NVP, hl);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) du[v] = (T)((hl[2 * v] - (float)U0[v]) + (hl[2 * v + 1] - L0[v]));
-    } else {
-      double u[NVP];
-      load16<double, NVP>(a.U + j * NVP, u);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) du[v] = (T)(u[v] - (double)U0[v]);
-    }
-  };
+}
 
-  // 1-2: central coefficients a_opt = P_c (U_m - U_0), streaming the member-major record
-  T ao[NK][NV];
+// U_j - U_0 for every variable (eq. 10), from member j's record.
+template <int D, typename T>
+__device__ __forceinline__ void cell_delta(const KArgs &a, const int64_t j, const T (&U0)[Lay<D>::NV],
+                                           const float (&L0)[Lay<D>::NV], T *du) {
+  constexpr int NV = Lay<D>::NV, NVP = Lay<D>::NVP;
+  if constexpr (sizeof(T) == 4) {
+    float hl[2 * NVP];
+    load16<float, 2 * NVP>(a.U32 + j * 2 * NVP, hl);
 #pragma unroll
-  for (int k = 0; k < NK; ++k)
+    for (int v = 0; v < NV; ++v) du[v] = (T)((hl[2 * v] - (float)U0[v]) + (hl[2 * v + 1] - L0[v]));
+  } else {
+    double u[NVP];
+    load16<double, NVP>(a.U + j * NVP, u);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) ao[k][v] = (T)0;
-  {
-    T pb[CH], du[NV];
-    int ids[4];
-#pragma unroll
-    for (int e = 0; e < M * NK; ++e) {
-      const int m = e / NK, k = e % NK;
-      if (e % CH == 0) {
-        if constexpr (SH) load16<T, CH, true>(Pci + e, pb);
-        else load16_stream<T, CH>(Pci + e, pb);
-      }
-      if (k == 0) {
-        if (m % 4 == 0) {
-          const int4 t4 = load_i4<SH>(sti + m);
-          ids[0] = t4.x; ids[1] = t4.y; ids[2] = t4.z; ids[3] = t4.w;
-        }
-        delta(ids[m % 4], du);
-      }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) ao[k][v] += pb[e % CH] * du[v];
-    }
+    for (int v = 0; v < NV; ++v) du[v] = (T)(u[v] - (double)U0[v]);
   }
+}
+
+// The second half of the thread-per-cell schedule, from the central coefficients ao of every
+// variable: the directional coefficients, p_1 (eq. 17), the smoothness indicators (eq. 15), the
+// selection (eqs. 19-23, Alg. 1 / 2), the final coefficients and the values at the face Gauss
+// points with the positivity guard. Pdi, sti: the cell's directional operators and stencil ids in
+// global memory (SH = false) or in a shared-memory copy (SH = true).
+template <int D, int R, typename T, int SCHEME, bool SH>
+__device__ __forceinline__ void cell_finish(const KArgs &a, const int64_t i,
+                                            T (&ao)[Shape<D, R>::NK][Lay<D>::NV], const T (&U0)[Lay<D>::NV],
+                                            const float (&L0)[Lay<D>::NV], const T *__restrict__ Pdi,
+                                            const int32_t *__restrict__ sti, const T *__restrict__ sPhi) {
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  constexpr int NV = L::NV, NF = L::NF, NQ = L::NQ, ND = L::ND, PDS = L::PDS;
+  constexpr int NK = S::NK, NP = S::NP;
+  constexpr bool F32 = sizeof(T) == 4;
+  const int64_t N = a.N;
+  auto delta = [&](int64_t j, T *du) { cell_delta<D, T>(a, j, U0, L0, du); };
 
   // directional coefficients (degree 1): members of face f are the next slots of the list
   const uint32_t info = __ldg(a.cinfo + i);
@@ -483,6 +470,49 @@ __device__ __forceinline__ void recon_cell(const KArgs &a, const int64_t i, cons
     atomicAdd(a.guard, 1ull);
   }
 
+}
+
+template <int D, int R, typename T, int SCHEME, bool SH>
+__device__ __forceinline__ void recon_cell(const KArgs &a, const int64_t i, const T *__restrict__ Pci,
+                                           const T *__restrict__ Pdi, const int32_t *__restrict__ sti,
+                                           const T *__restrict__ sPhi) {
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  constexpr int NV = L::NV;
+  constexpr int NK = S::NK, M = S::M;
+  constexpr int CH = Vec16<T>::n;
+  T U0[NV];
+  float L0[NV];
+  cell_own<D, T>(a, i, U0, L0);
+
+  // 1-2: central coefficients a_opt = P_c (U_m - U_0), streaming the member-major record
+  T ao[NK][NV];
+#pragma unroll
+  for (int k = 0; k < NK; ++k)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ao[k][v] = (T)0;
+  {
+    T pb[CH], du[NV];
+    int ids[4];
+#pragma unroll
+    for (int e = 0; e < M * NK; ++e) {
+      const int m = e / NK, k = e % NK;
+      if (e % CH == 0) {
+        if constexpr (SH) load16<T, CH, true>(Pci + e, pb);
+        else load16_stream<T, CH>(Pci + e, pb);
+      }
+      if (k == 0) {
+        if (m % 4 == 0) {
+          const int4 t4 = load_i4<SH>(sti + m);
+          ids[0] = t4.x; ids[1] = t4.y; ids[2] = t4.z; ids[3] = t4.w;
+        }
+        cell_delta<D, T>(a, ids[m % 4], U0, L0, du);
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ao[k][v] += pb[e % CH] * du[v];
+    }
+  }
+  cell_finish<D, R, T, SCHEME, SH>(a, i, ao, U0, L0, Pdi, sti, sPhi);
 }
 
 // MINB > 0: register-capped variant (at most 128 threads per block, MINB blocks per SM), which the
@@ -1128,14 +1158,14 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
 // the dominant stream in flight while its loops stay short (few registers, little code), and no
 // warp waits for another.
 // ---------------------------------------------------------------------------------------------
-template <int D, int R>
+template <int D, int R, int STAGES>
 struct StreamShape {
   using S = Shape<D, R>;
   using L = Lay<D>;
   static constexpr int CPW = 32 / L::NV;                     // cells per warp
   static constexpr int MC = (S::M % 8 == 0) ? 8 : 4;          // members per chunk
   static constexpr int NCH = S::M / MC;                       // chunks per tile
-  static constexpr int NST = kStreamStages;                   // stages of the chunk ring
+  static constexpr int NST = STAGES;                          // stages of the chunk ring
   static constexpr int CHUNK_CELL = MC * S::NK * 4;           // bytes of one cell's chunk
   static constexpr int STAGE = CPW * CHUNK_CELL;
   static constexpr int HPD = CPW * L::NF * L::PDS * 4;        // header: directional operators,
@@ -1148,12 +1178,12 @@ struct StreamShape {
                 "bulk copies need 16-byte spans");
 };
 
-template <int D, int R, int SCHEME>
+template <int D, int R, int SCHEME, int STAGES>
 __global__ void __launch_bounds__(512, 1) recon_stream_kernel(const KArgs a) {
   using T = float;
   using S = Shape<D, R>;
   using L = Lay<D>;
-  using Q = StreamShape<D, R>;
+  using Q = StreamShape<D, R, STAGES>;
   constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, ND = L::ND, PDS = L::PDS;
   constexpr int NK = S::NK, M = S::M, NP = S::NP, NQ = L::NQ;
   constexpr int CPW = Q::CPW, MC = Q::MC, NCH = Q::NCH, NST = Q::NST;
@@ -1269,21 +1299,30 @@ __global__ void __launch_bounds__(512, 1) recon_stream_kernel(const KArgs a) {
       return (h.x - U0) + (h.y - L0);
     };
 
-    // central coefficients of variable v, chunk after chunk
+    // central coefficients of variable v, chunk after chunk; the member states of chunk c + 1
+    // are loaded while chunk c is multiplied
     T ao[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) ao[k] = (T)0;
+    float2 nx[MC];
+    auto fetch = [&](int c) {
+#pragma unroll
+      for (int mm = 0; mm < MC; mm += 4) {
+        const int4 j4 = *reinterpret_cast<const int4 *>(st_s + c * MC + mm);
+        const float2 *u = reinterpret_cast<const float2 *>(a.U32) + v;
+        nx[mm] = __ldg(u + (int64_t)j4.x * NVP);
+        nx[mm + 1] = __ldg(u + (int64_t)j4.y * NVP);
+        nx[mm + 2] = __ldg(u + (int64_t)j4.z * NVP);
+        nx[mm + 3] = __ldg(u + (int64_t)j4.w * NVP);
+      }
+    };
+    fetch(0);
 #pragma unroll 1
     for (int c = 0; c < NCH; ++c, ++q) {
       T du[MC];
 #pragma unroll
-      for (int mm = 0; mm < MC; mm += 4) {
-        const int4 j4 = *reinterpret_cast<const int4 *>(st_s + c * MC + mm);
-        du[mm] = delta(j4.x);
-        du[mm + 1] = delta(j4.y);
-        du[mm + 2] = delta(j4.z);
-        du[mm + 3] = delta(j4.w);
-      }
+      for (int mm = 0; mm < MC; ++mm) du[mm] = (nx[mm].x - U0) + (nx[mm].y - L0);
+      if (c + 1 < NCH) fetch(c + 1);
       if (!wait_all(&pbar[q % NST], (uint32_t)((q / NST) & 1))) {
         give_up(it, q, qi);
         return;
@@ -1339,12 +1378,180 @@ __global__ void __launch_bounds__(512, 1) recon_stream_kernel(const KArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Streamed thread-per-cell schedule (mixed path): every warp walks tiles of 32 consecutive cells,
+// one thread per cell with all its variables, and each lane streams its own cell's central
+// pseudo-inverse record through the warp's ring of NST shared-memory stages, four stencil members
+// (one row of MC * NK values) at a time: each lane announces and issues the bulk copy of its row,
+// lane 0 arrives on the stage's mbarrier. The arithmetic is the thread-per-cell schedule's, in the
+// same order; the rows are read back with conflict-free 16-byte shared loads.
+// ---------------------------------------------------------------------------------------------
+template <int D, int R>
+struct StreamCellShape {
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  static constexpr int MC = 4;                                // members per chunk
+  static constexpr int NCH = S::M / MC;                       // chunks per cell
+  static constexpr int NST = kStreamCellStages;
+  static constexpr int ROW = MC * S::NK * 4;                  // bytes of one cell's chunk
+  static constexpr int STAGE = 32 * ROW;
+  static constexpr int WARP_BYTES = NST * STAGE;
+  static constexpr int NPHI = (D == 3) ? L::NF * S::NP * L::NQ * S::NK : 1;
+  static constexpr int PHI_BYTES = (NPHI * 4 + 15) / 16 * 16;
+  static_assert(S::M % MC == 0 && ROW % 16 == 0, "bulk copies need 16-byte rows");
+};
+
 template <int D, int R, int SCHEME>
-void launch_recon_stream(const KArgs &a, int warps, cudaStream_t s) {
-  using Q = StreamShape<D, R>;
+__global__ void __launch_bounds__(256, 1) recon_stream_cells_kernel(const KArgs a) {
+  using T = float;
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  using Q = StreamCellShape<D, R>;
+  constexpr int NV = L::NV, NF = L::NF, PDS = L::PDS, NQ = L::NQ;
+  constexpr int NK = S::NK, M = S::M, NP = S::NP;
+  constexpr int MC = Q::MC, NCH = Q::NCH, NST = Q::NST;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int W = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  T *const sPhi = reinterpret_cast<T *>(smem);
+  unsigned char *const wbase = smem + Q::PHI_BYTES + (size_t)warp * Q::WARP_BYTES;
+  uint64_t *const bars = reinterpret_cast<uint64_t *>(smem + Q::PHI_BYTES + (size_t)W * Q::WARP_BYTES);
+  uint64_t *const pbar = bars + warp * NST;  // the NST stages of this warp
+  uint64_t *const tbar = bars + W * NST;     // the test hook (block)
+  auto stage = [&](int64_t q) { return wbase + (q % NST) * Q::STAGE; };
+
+  const int64_t N = a.N;
+  const int64_t tiles = (N + 31) / 32;
+  const int64_t gw = (int64_t)blockIdx.x * W + warp, TW = (int64_t)gridDim.x * W;
+  auto tile_of = [&](int64_t it) { return gw + it * TW; };
+  // every lane: its row of chunk q (tile iteration q / NCH, members 4 (q % NCH) ..); the branch is
+  // uniform across the warp
+  auto issue = [&](int64_t q) {
+    const int64_t t = tile_of(q / NCH);
+    if (t >= tiles) return;
+    const int c = (int)(q % NCH);
+    const int64_t cell = t * 32 + lane;
+    uint64_t *bar = &pbar[q % NST];
+    if (cell < N) {
+      mbar_expect_tx(bar, Q::ROW);
+      bulk_copy_g2s(stage(q) + lane * Q::ROW, (const T *)a.Pc + cell * (int64_t)(M * NK) + c * (MC * NK), Q::ROW,
+                    bar);
+    }
+    __syncwarp();  // every announcement precedes the arrival that can complete the phase
+    if (lane == 0) mbar_arrive(bar);
+  };
+  auto wait_all = [&](uint64_t *bar, uint32_t parity) {
+    const bool ok = mbar_wait(bar, parity, kStageWaitNs);
+    return !__any_sync(0xffffffffu, !ok);
+  };
+  auto give_up = [&](int64_t q, int64_t qi) {  // report, let this warp's copies land (bounded), stop
+    if (lane == 0) {
+      atomicOr(a.err, kErrTimeout);
+      for (int64_t c = q; c < qi; ++c)
+        if (tile_of(c / NCH) < tiles) mbar_wait(&pbar[c % NST], (uint32_t)((c / NST) & 1), kStageWaitNs);
+    }
+    __syncwarp();
+  };
+
+  if (lane == 0) {
+    for (int b = 0; b < NST; ++b) mbar_init(&pbar[b], 1);
+    if (threadIdx.x == 0) mbar_init(tbar, 1);
+    fence_barrier_init();
+  }
+  if constexpr (D == 3) {
+    const DevTables &tb = *a.tab;
+    for (int t = threadIdx.x; t < Q::NPHI; t += blockDim.x) {
+      const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
+      sPhi[t] = (T)tb.Phi[f][p][q][k];
+    }
+  }
+  __syncthreads();
+  // the operator records do not depend on the previous kernel: their copies start now
+  for (int64_t q = 0; q < NST; ++q) issue(q);
+  if (a.test_wait_ns) {  // test hook: a bounded wait on a barrier that nothing completes runs out
+    bool ok = true;
+    if (threadIdx.x == 0) ok = mbar_wait(tbar, 0, a.test_wait_ns);
+    if (__syncthreads_or(!ok)) {
+      give_up(0, NST);
+      return;
+    }
+  }
+  pdl_wait(a);  // states written by the previous stage's update
+  if (a.dt_swap && blockIdx.x == 0)
+    for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {
+      a.dt[t] = a.dt[a.nmesh + t];
+      a.dt[a.nmesh + t] = 1e300;
+    }
+
+  int64_t q = 0, qi = NST;  // next chunk to consume / to issue
+  for (int64_t it = 0; tile_of(it) < tiles; ++it) {
+    const int64_t i0 = tile_of(it) * 32 + lane;
+    const bool active = i0 < N;
+    const int64_t i = active ? i0 : N - 1;  // lanes past the last cell shadow it and store nothing
+    T U0[NV];
+    float L0[NV];
+    cell_own<D, T>(a, i, U0, L0);
+    const int32_t *__restrict__ sti = a.st + i * M;
+    T ao[NK][NV];
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ao[k][v] = (T)0;
+#pragma unroll 1
+    for (int c = 0; c < NCH; ++c, ++q) {
+      const int4 j4 = load_i4<false>(sti + c * MC);
+      T du[MC][NV];
+      cell_delta<D, T>(a, j4.x, U0, L0, du[0]);
+      cell_delta<D, T>(a, j4.y, U0, L0, du[1]);
+      cell_delta<D, T>(a, j4.z, U0, L0, du[2]);
+      cell_delta<D, T>(a, j4.w, U0, L0, du[3]);
+      if (!wait_all(&pbar[q % NST], (uint32_t)((q / NST) & 1))) {
+        give_up(q, qi);
+        return;
+      }
+      const T *__restrict__ P = reinterpret_cast<const T *>(stage(q) + lane * Q::ROW);
+      T pb[4];
+#pragma unroll
+      for (int e = 0; e < MC * NK; ++e) {
+        if (e % 4 == 0) load16<T, 4, true>(P + e, pb);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ao[e % NK][v] += pb[e % 4] * du[e / NK][v];
+      }
+      fence_proxy_async_shared();  // this lane's reads of its row precede the copy that refills it
+      issue(qi);
+      ++qi;
+    }
+    if (active)
+      cell_finish<D, R, T, SCHEME, false>(a, i, ao, U0, L0, (const T *)a.Pd + i * (int64_t)(NF * PDS), sti, sPhi);
+  }
+}
+
+template <int D, int R, int SCHEME>
+void launch_recon_stream_cells(const KArgs &a, int warps, cudaStream_t s) {
   const int threads = 32 * warps;
-  const size_t smem = (size_t)recon_stream_smem(D, R, warps);
-  auto kern = recon_stream_kernel<D, R, SCHEME>;
+  const size_t smem = (size_t)recon_stream_cells_smem(D, R, warps);
+  auto kern = recon_stream_cells_kernel<D, R, SCHEME>;
+  static int resident[9] = {}, sms = 0;
+  int &nb = resident[warps];
+  if (!nb) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxStreamSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+    if (nb < 1) nb = 1;  // a launch that cannot fit fails loudly below
+  }
+  const int64_t tiles = (a.N + 31) / 32;
+  const int64_t blocks = (tiles + warps - 1) / warps;
+  const unsigned grid = (unsigned)std::min<int64_t>(blocks, (int64_t)nb * sms);
+  launch_stage_kernel(kern, grid, threads, smem, s, a);
+}
+
+template <int D, int R, int SCHEME, int STAGES>
+void launch_recon_stream(const KArgs &a, int warps, cudaStream_t s) {
+  using Q = StreamShape<D, R, STAGES>;
+  const int threads = 32 * warps;
+  const size_t smem = (size_t)recon_stream_smem(D, R, warps, STAGES);
+  auto kern = recon_stream_kernel<D, R, SCHEME, STAGES>;
   static int resident[17] = {}, sms = 0;
   int &nb = resident[warps];
   if (!nb) {

@@ -16,14 +16,29 @@ cudaError_t launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, in
 #undef CTENO_HALO
     return cudaSuccess;
   }
-  if (block > kStreamLanes && block <= kStreamLanes + 16) {  // streamed lane schedule (mixed)
+  if (block > kStreamCells && block <= kStreamCells + 8) {  // streamed thread-per-cell schedule (mixed)
     if (!fp32) return cudaErrorInvalidValue;  // mixed path only
-    const int warps = block - kStreamLanes;
-    if (degree == 2 && scheme == 0) launch_recon_stream<2, 2, 0>(a, warps, s);
-    if (degree == 2 && scheme == 1) launch_recon_stream<2, 2, 1>(a, warps, s);
-    if (degree == 3 && scheme == 0) launch_recon_stream<2, 3, 0>(a, warps, s);
-    if (degree == 3 && scheme == 1) launch_recon_stream<2, 3, 1>(a, warps, s);
+    const int warps = block - kStreamCells;
+    if (degree == 2 && scheme == 0) launch_recon_stream_cells<2, 2, 0>(a, warps, s);
+    if (degree == 2 && scheme == 1) launch_recon_stream_cells<2, 2, 1>(a, warps, s);
+    if (degree == 3 && scheme == 0) launch_recon_stream_cells<2, 3, 0>(a, warps, s);
+    if (degree == 3 && scheme == 1) launch_recon_stream_cells<2, 3, 1>(a, warps, s);
     return cudaSuccess;
+  }
+  {
+    int warps = 0, stages = 0;
+    stream_launch(block, &warps, &stages);
+    if (warps) {  // streamed lane schedule (mixed)
+      if (!fp32) return cudaErrorInvalidValue;  // mixed path only
+#define CTENO_STREAM(R, SC) \
+  (stages == 3 ? launch_recon_stream<2, R, SC, 3>(a, warps, s) : launch_recon_stream<2, R, SC, 2>(a, warps, s))
+      if (degree == 2 && scheme == 0) CTENO_STREAM(2, 0);
+      if (degree == 2 && scheme == 1) CTENO_STREAM(2, 1);
+      if (degree == 3 && scheme == 0) CTENO_STREAM(3, 0);
+      if (degree == 3 && scheme == 1) CTENO_STREAM(3, 1);
+#undef CTENO_STREAM
+      return cudaSuccess;
+    }
   }
   if (block >= kStagedCells) {  // staged persistent schedules (mixed path; the launch value is
                                 // validated by the caller)
