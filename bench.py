@@ -44,7 +44,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mcell-RK-stage/s (deg 2/3, 2D tri & 3D tet), FP32-mixed vs FP64 on one GB300"
 UNIT = "Mcell-RK-stage/s"
-SCHEMES = {0: "CTENO", 1: "CTENOZ"}
+SCHEMES = {0: "CTENO", 1: "CTENOZ", 2: "CWENO", 3: "TENO"}
 PRECISIONS = {0: "fp64", 1: "mixed"}
 WORKLOADS = ["blast_3d_96", "shock_tube_2d", "density_wave_3d_64", "batch_2d"]
 
@@ -67,7 +67,7 @@ def make_case(name, n=0):
         wl = W.shock_tube_2d(512, 128)
         return Case(name, "2D shock tube [0,1]x[0,0.25], 512x128 squares -> 131072 triangles, jitter 0.1h, "
                     "Sod states, transmissive, CFL 0.4", [wl.mesh], [wl.U0], 2, 0, 2, 0.4,
-                    [(0, 2), (0, 3), (1, 2), (1, 3)], (0.5, 0.125))
+                    [(0, 2), (0, 3), (1, 2), (1, 3), (2, 2), (2, 3), (3, 2), (3, 3)], (0.5, 0.125))
     if name == "density_wave_3d_64":
         n = n or 64
         wl = W.density_wave_3d(n)
@@ -431,6 +431,16 @@ def run_ours(args, rank, world, local):
                     m = variants[f"{oc.name}:{variant_name(sc, dg, 1)}"]
                     m["speedup_vs_fp64"] = round(m["value"] / variants[f"{oc.name}:{variant_name(sc, dg, 0)}"]["value"], 2)
                     m["config"] = oc.description
+                # the cost comparison of the paper's Tables 4-5 (time per step normalised to CWENO
+                # of the same order), here per degree and precision on the GPU
+                for dg in sorted({dg for sc, dg in oc.variants}):
+                    for pr in (1, 0):
+                        base = variants.get(f"{oc.name}:{variant_name(2, dg, pr)}")
+                        if base:
+                            for sc in (2, 3, 0, 1):
+                                v = variants.get(f"{oc.name}:{variant_name(sc, dg, pr)}")
+                                if v:
+                                    v["time_vs_cweno_same_order"] = round(v["ms_per_step"] / base["ms_per_step"], 3)
                 del oc
             else:
                 oc, sc, dg, pr = item

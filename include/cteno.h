@@ -48,7 +48,7 @@ enum {
   CTENO_ERR_NOMEM = -8     /* host or device allocation failed */
 };
 
-enum { CTENO_SCHEME_CTENO = 0, CTENO_SCHEME_CTENOZ = 1 };
+enum { CTENO_SCHEME_CTENO = 0, CTENO_SCHEME_CTENOZ = 1, CTENO_SCHEME_CWENO = 2, CTENO_SCHEME_TENO = 3 };
 enum { CTENO_FP64 = 0, CTENO_MIXED = 1 };
 enum { CTENO_BOUNDARY_TRANSMISSIVE = 0 };
 
@@ -56,7 +56,11 @@ enum { CTENO_BOUNDARY_TRANSMISSIVE = 0 };
 typedef struct {
   int dim;              /* d = 2 (triangles) or 3 (tetrahedra) */
   int degree;           /* r = 2 or 3: central polynomial degree, order r+1 (Sec. 2.1) */
-  int scheme;           /* CTENO_SCHEME_CTENO (Alg. 1) or CTENO_SCHEME_CTENOZ (Alg. 2) */
+  int scheme;           /* CTENO_SCHEME_CTENO (Alg. 1) or CTENO_SCHEME_CTENOZ (Alg. 2); for
+                           comparison in the same kernels, CTENO_SCHEME_CWENO (Sec. 2.3: every
+                           stencil with the weights of eq. 14, b = 4, on the CWENO split p_1) and
+                           CTENO_SCHEME_TENO (Sec. 2.4: the cut-off of eqs. 19-23 without linear
+                           coefficients, on the central least-squares polynomial itself) */
   int precision;        /* CTENO_FP64: all arithmetic in FP64. CTENO_MIXED: reconstruction and
                            flux in FP32; geometry, least-squares build, residual accumulation and
                            the RK update in FP64 */

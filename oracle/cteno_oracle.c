@@ -43,7 +43,7 @@
 /* Parameters and state                                                                        */
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {
-  int dim, degree, scheme; /* scheme 0 = CTENO (Alg. 1), 1 = CTENOZ (Alg. 2) */
+  int dim, degree, scheme; /* 0 = CTENO (Alg. 1), 1 = CTENOZ (Alg. 2), 2 = CWENO (Sec. 2.3), 3 = TENO (Sec. 2.4) */
   int guard;               /* Reading: positivity fall-back to the cell mean */
   int lam_gamma;           /* Reading: 1 = gamma_s carries lambda_s (eq. 18), 0 = as printed */
   int ctenoz_form;         /* Reading: 0 = CTENOZ measure as printed, 1 = WENO-Z form */
@@ -761,10 +761,14 @@ static double pressure(const orc *o, const double *u) {
   return (o->p.gamma - 1.0) * (u[d + 1] - 0.5 * ke / u[0]);
 }
 
-/* Scale separation, smoothness measure and cut-off of one cell and one variable (Sec. 2.5-2.6).
+/* Scale separation, smoothness measure and cut-off of one cell and one variable (Sec. 2.4-2.6),
+ * or the nonlinear weights of CWENO (Sec. 2.2-2.3).
  * Stencil s = 0 is the central one (SI[0] = SI of p_1), s = 1 .. st-1 the admissible directional
  * ones, so st is s_t. Linear coefficients of eq. 18: lambda_1 = 1 - 1/lambda_1' and
  * lambda_s = (1 - lambda_1) / (s_t - 1).
+ *   CWENO (eqs. 13-14 with the linear coefficients of eq. 18): w~_s = lambda_s / (eps + SI_s)^b,
+ *     b = 4, w_s = w~_s / sum_t w~_t. chi[] receives w_s, and every stencil is kept (all bits).
+ *   TENO (eqs. 19-23): gamma_s = 1 / (SI_s + eps)^6 as printed (TENO has no linear coefficients).
  *   CTENO (Alg. 1):  gamma_s = 1 / (SI_s + eps)^6.
  *   CTENOZ (Alg. 2): tau = (sum_{s>=2} |SI_s - SI_1| / (s_t - 1))^6, gamma_s = 1 + tau / (SI_s + eps).
  *     Reading (ctenoz_form = 1, not the printed form): the WENO-Z arrangement, with the power on
@@ -777,7 +781,13 @@ static unsigned select_stencils(const orc_params *p, int st, const double *SI, d
   const double lam1 = 1.0 - 1.0 / p->lambda1p;
   const double lams = (st > 1) ? (1.0 - lam1) / (st - 1) : 0.0;
   double gam[1 + MAXNF], sum = 0.0;
-  if (p->scheme == 0) {
+  if (p->scheme == 2) { /* CWENO: nonlinear weights, every stencil contributes */
+    for (int s = 0; s < st; ++s) gam[s] = ((s == 0) ? lam1 : lams) / pow(p->eps + SI[s], 4.0);
+    for (int s = 0; s < st; ++s) sum += gam[s];
+    for (int s = 0; s < st; ++s) chi[s] = gam[s] / sum;
+    return (1u << st) - 1u;
+  }
+  if (p->scheme == 0 || p->scheme == 3) {
     for (int s = 0; s < st; ++s) gam[s] = 1.0 / pow(SI[s] + p->eps, 6.0);
   } else {
     double tau = 0.0;
@@ -792,7 +802,7 @@ static unsigned select_stencils(const orc_params *p, int st, const double *SI, d
       else gam[s] = 1.0 + pow(tau / (SI[s] + p->eps), 6.0);
     }
   }
-  if (p->lam_gamma)
+  if (p->lam_gamma && p->scheme != 3)
     for (int s = 0; s < st; ++s) gam[s] *= (s == 0) ? lam1 : lams;
   for (int s = 0; s < st; ++s) sum += gam[s];
   unsigned bits = 0;
@@ -831,9 +841,10 @@ static void recon_cell(orc *o, int i, const double *U) {
       lsq_solve(c->ndir[f], d, &c->dA[f][0][0], MAXD, &c->dR[f][0][0], MAXD, bd, ad[f]);
     }
     /* p_1 = (p_opt - sum_{s>=2} lambda_s p_s) / lambda_1  (eq. 17); the directional
-     * polynomials are linear, so only the first d coefficients receive their terms */
+     * polynomials are linear, so only the first d coefficients receive their terms; TENO keeps
+     * p_1 = p_opt */
     double a1[MAXK];
-    if (st > 1) {
+    if (st > 1 && o->p.scheme != 3) { /* TENO keeps the central polynomial itself (Sec. 2.4) */
       for (int k = 0; k < nk; ++k) {
         double s = aopt[k];
         if (k < d)
@@ -861,10 +872,16 @@ static void recon_cell(orc *o, int i, const double *U) {
       delta[s] = (dbits >> s) & 1u;
       if (s > 0) ndel += delta[s];
     }
-    /* final polynomial: p_1 if delta_1, else sum_{s>=2} delta_s p_s / sum delta_s */
+    /* final polynomial: CWENO sum_s w_s p_s (Sec. 2.3); otherwise p_1 if delta_1, else
+     * sum_{s>=2} delta_s p_s / sum delta_s (Alg. 1 / 2) */
     double af[MAXK];
     uint8_t fl = 0;
-    if (delta[0]) {
+    if (o->p.scheme == 2) {
+      for (int k = 0; k < nk; ++k) af[k] = chi[0] * a1[k];
+      for (int s = 1; s < st; ++s)
+        for (int k = 0; k < d; ++k) af[k] += chi[s] * ad[adm[s - 1]][k];
+      fl = (uint8_t)(o->stmask[i] & 0xFF);
+    } else if (delta[0]) {
       for (int k = 0; k < nk; ++k) af[k] = a1[k];
       fl = 1;
     } else {

@@ -92,6 +92,10 @@ cudaError_t dalloc(cteno_ctx *ctx, P **ptr, size_t bytes) {
   return e;
 }
 
+// Kernel instantiation of the scheme: the CTENOZ measure (1) or the CTENO measure (0), which
+// CWENO (weights on the same indicators) and TENO (cut-off without linear coefficients) share.
+int kscheme(const cteno_ctx *ctx) { return ctx->p.scheme == CTENO_SCHEME_CTENOZ ? 1 : 0; }
+
 KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   KArgs a{};
   a.N = ctx->N;
@@ -131,8 +135,10 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.eps = ctx->p.eps;
   a.gamma = ctx->p.gamma;
   a.cfl = ctx->p.cfl;
-  a.lam_gamma = ctx->p.lam_gamma;
+  a.lam_gamma = ctx->p.scheme == CTENO_SCHEME_TENO ? 0 : ctx->p.lam_gamma;  // TENO has no linear coefficients
   a.ctenoz_form = ctx->p.ctenoz_form;
+  a.cweno = ctx->p.scheme == CTENO_SCHEME_CWENO;
+  a.central_split = ctx->p.scheme != CTENO_SCHEME_TENO;
   a.guard_on = ctx->p.positivity_guard;
   a.lam1 = 1.0 - 1.0 / ctx->p.lambda1p;
   a.inv_lam1 = 1.0 / a.lam1;
@@ -163,7 +169,7 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
 
 cudaError_t enqueue_stage(cteno_ctx *ctx, int stage, int dt_swap, cudaStream_t s) {
   const KArgs a = make_args(ctx, stage, dt_swap);
-  const cudaError_t e = launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, ctx->p.scheme, a, ctx->recon_block, s);
+  const cudaError_t e = launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, kscheme(ctx), a, ctx->recon_block, s);
   if (e != cudaSuccess) return e;
   launch_flux(ctx->d, ctx->fp32 ? 1 : 0, a, ctx->flux_block, s);
   return cudaSuccess;
@@ -258,7 +264,7 @@ int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream) {
   if (!out || !p) return CTENO_ERR_ARG;
   *out = nullptr;
   if ((p->dim != 2 && p->dim != 3) || (p->degree != 2 && p->degree != 3) ||
-      (p->scheme != 0 && p->scheme != 1) || (p->precision != 0 && p->precision != 1) ||
+      p->scheme < 0 || p->scheme > 3 || (p->precision != 0 && p->precision != 1) ||
       (p->ctenoz_form != 0 && p->ctenoz_form != 1) || (p->lam_gamma != 0 && p->lam_gamma != 1) ||
       !(p->lambda1p > 1.0) || !(p->C_T >= 0.0 && p->C_T < 1.0) || !(p->eps >= 0.0) ||
       !(p->cfl > 0.0) || !(p->gamma > 1.0))
@@ -695,7 +701,7 @@ int cteno_run(cteno_ctx *ctx, int nsteps) {
     for (int s = 0; s < 3; ++s) {
       const KArgs a = make_args(ctx, s, s == 0 ? 1 : 0);
       const cudaError_t le =
-          launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, ctx->p.scheme, a, ctx->recon_block, ctx->capture);
+          launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, kscheme(ctx), a, ctx->recon_block, ctx->capture);
       if (le != cudaSuccess) {  // end the capture before reporting
         cudaGraph_t g = nullptr;
         cudaStreamEndCapture(ctx->capture, &g);
@@ -940,9 +946,9 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
   int br = ctx->recon_block, bf = ctx->flux_block;
   const KArgs a = make_args(ctx, 1, 0);  // stage 1: reads U^n, writes U only
   for (int b : rcand) {  // the reconstruction writes only face states: no restore needed
-    CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, b, ctx->stream));
+    CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, kscheme(ctx), a, b, ctx->stream));
     CK(cudaEventRecord(e0, ctx->stream));
-    for (int r = 0; r < reps; ++r) CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, b, ctx->stream));
+    for (int r = 0; r < reps; ++r) CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, kscheme(ctx), a, b, ctx->stream));
     CK(cudaEventRecord(e1, ctx->stream));
     CK(cudaEventSynchronize(e1));
     float ms = 0;
@@ -1018,7 +1024,7 @@ int cteno_profile_step(cteno_ctx *ctx, int nsteps, double *ms_out) {
     for (int s = 0; s < 3; ++s) {
       const KArgs a = make_args(ctx, s, s == 0 ? 1 : 0);
       CK(cudaEventRecord(ev[2 * s], ctx->stream));
-      CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, ctx->p.scheme, a, ctx->recon_block, ctx->stream));
+      CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, kscheme(ctx), a, ctx->recon_block, ctx->stream));
       CK(cudaEventRecord(ev[2 * s + 1], ctx->stream));
       launch_flux(ctx->d, ctx->fp32, a, ctx->flux_block, ctx->stream);
     }

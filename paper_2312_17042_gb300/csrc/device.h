@@ -92,6 +92,8 @@ struct KArgs {
   // parameters
   double C_T, lambda1p, eps, gamma, cfl;
   int lam_gamma, guard_on, ctenoz_form;
+  int cweno;          // CWENO weighting (Sec. 2.3) instead of the cut-off selection
+  int central_split;  // p_1 from the CWENO split of eq. 17 (CTENO, CTENOZ, CWENO); 0: TENO's p_opt
   // linear coefficients of eq. 18, evaluated once on the host in FP64:
   // lam1 = 1 - 1/lambda_1', 1/lam1, 1 - lam1 (lambda_s = (1 - lam1) / (s_t - 1)) and base-2 logs
   double lam1, inv_lam1, one_m_lam1;

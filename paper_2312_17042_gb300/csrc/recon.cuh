@@ -97,6 +97,11 @@ __device__ __forceinline__ T pow6(T x) {
   const T x2 = x * x;
   return x2 * x2 * x2;
 }
+template <typename T>
+__device__ __forceinline__ T pow4(T x) {
+  const T x2 = x * x;
+  return x2 * x2;
+}
 
 // Selection of eqs. 19-23 / Alg. 1-2 in FP64, as printed (gamma_s times lambda_s when
 // lam_gamma). SI0: central; SId[f]: directional stencil of face f, used where bit f of adm is
@@ -237,6 +242,46 @@ __device__ __forceinline__ uint32_t select_fp32(float SI0, const float *SId, uin
 // One cell of the thread-per-cell schedule. Pci, Pdi, sti: the cell's central pseudo-inverse,
 // directional operators and stencil ids, in global memory (SH = false) or in a shared-memory copy
 // (SH = true); sPhi: 3D face-point basis values in shared memory.
+// CWENO nonlinear weights (Sec. 2.3: the weights of eq. 14 with b = 4 on the linear coefficients
+// of eq. 18): w~_s = lambda_s / (eps + SI_s)^4, normalised over the admissible stencils. FP64 as
+// written; FP32 in the base-2 log domain like select_fp32 (no overflow of (eps + SI)^-4).
+template <int NF>
+__device__ __forceinline__ void cweno_weights(double SI0, const double *SId, uint32_t adm, double lam1,
+                                              double lams, double eps, double &w0, double *wd) {
+  const double g0 = lam1 / pow4(eps + SI0);
+  double g[NF], sum = g0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    g[f] = ((adm >> f) & 1u) ? lams / pow4(eps + SId[f]) : 0.0;
+    sum += g[f];
+  }
+  w0 = g0 / sum;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) wd[f] = g[f] / sum;
+}
+template <int NF>
+__device__ __forceinline__ void cweno_weights(float SI0, const float *SId, uint32_t adm, float log2lam1,
+                                              float log2lams, float eps, float &w0, float *wd) {
+  const float L0 = log2lam1 - 4.0f * lg2_approx(SI0 + eps);
+  float Ld[NF], Lmax = L0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    Ld[f] = log2lams - 4.0f * lg2_approx(SId[f] + eps);
+    if ((adm >> f) & 1u) Lmax = fmaxf(Lmax, Ld[f]);
+  }
+  const float e0 = ex2_approx(L0 - Lmax);
+  float sum = e0;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    wd[f] = ((adm >> f) & 1u) ? ex2_approx(Ld[f] - Lmax) : 0.0f;
+    sum += wd[f];
+  }
+  const float inv = 1.0f / sum;
+  w0 = e0 * inv;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) wd[f] *= inv;
+}
+
 // Own cell means of cell i: FP64, or (mixed path) the FP32 pair hi + lo of every FP64 value, so
 // that U_m - U_0 = (hi_m - hi_0) + (lo_m - lo_0) keeps FP64 accuracy in FP32 arithmetic.
 template <int D, typename T>
@@ -357,7 +402,7 @@ __device__ __forceinline__ void cell_finish(const KArgs &a, const int64_t i,
     T a1[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) a1[k] = ao[k][v];
-    if (stn > 1) {
+    if (stn > 1 && a.central_split) {  // TENO keeps p_opt (Sec. 2.4)
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         T s = (T)0;
@@ -387,28 +432,42 @@ __device__ __forceinline__ void cell_finish(const KArgs &a, const int64_t i,
     }
     // 5: selection
     uint32_t bits;
-    if constexpr (F32) {
-      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, log2lam1, log2lams,
-                             inv_stm1, a.eps32, a.C_T32);
-    } else {
-      bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
-    }
-    // final coefficients, written over a_opt
-    if (bits & 1u) {
+    if (a.cweno) {  // CWENO (Sec. 2.3): every stencil, with the weights of eq. 14
+      T w0, wd[NF];
+      if constexpr (F32) cweno_weights<NF>(SI0, SId, adm, a.log2_lam1, log2lams, a.eps32, w0, wd);
+      else cweno_weights<NF>(SI0, SId, adm, a.lam1, lamsd, a.eps, w0, wd);
 #pragma unroll
-      for (int k = 0; k < NK; ++k) ao[k][v] = a1[k];
-    } else {
-      const T w = (T)1 / (T)__popc(bits >> 1);
-#pragma unroll
-      for (int k = 0; k < NK; ++k) ao[k][v] = (T)0;
+      for (int k = 0; k < NK; ++k) ao[k][v] = w0 * a1[k];
 #pragma unroll
       for (int f = 0; f < NF; ++f)
-        if ((bits >> (1 + f)) & 1u) {
 #pragma unroll
-          for (int k = 0; k < D; ++k) ao[k][v] += w * ad[f][k][v];
-        }
+        for (int k = 0; k < D; ++k) ao[k][v] += wd[f] * ad[f][k][v];  // zero weight where inadmissible
+      bits = 1u | (adm << 1);
+    } else {
+      if constexpr (F32) {
+        bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, log2lam1, log2lams,
+                               inv_stm1, a.eps32, a.C_T32);
+      } else {
+        bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
+      }
+      // final coefficients, written over a_opt
+      if (bits & 1u) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) ao[k][v] = a1[k];
+      } else {
+        const T w = (T)1 / (T)__popc(bits >> 1);
+#pragma unroll
+        for (int k = 0; k < NK; ++k) ao[k][v] = (T)0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          if ((bits >> (1 + f)) & 1u) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) ao[k][v] += w * ad[f][k][v];
+          }
+      }
+      if (bits & 1u) bits = 1u;
     }
-    if (a.flags) a.flags[v * N + i] = (uint8_t)((bits & 1u) ? 1u : bits);
+    if (a.flags) a.flags[v * N + i] = (uint8_t)bits;
   }
 
   // 6: face Gauss-point values, one contiguous vector per face; positivity guard (not part of
@@ -593,7 +652,7 @@ __device__ __forceinline__ void lane_finish(const KArgs &a, const int64_t i, con
     T a1[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) a1[k] = ao[k];
-    if (stn > 1) {
+    if (stn > 1 && a.central_split) {  // TENO keeps p_opt (Sec. 2.4)
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         T s = (T)0;
@@ -623,27 +682,41 @@ __device__ __forceinline__ void lane_finish(const KArgs &a, const int64_t i, con
       SId[f] = s * INV_FACT;
     }
     uint32_t bits;
-    if constexpr (F32) {
-      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.log2_lam1, log2lams,
-                             inv_stm1, a.eps32, a.C_T32);
-    } else {
-      bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
-    }
-    if (bits & 1u) {
+    if (a.cweno) {  // CWENO (Sec. 2.3): every stencil, with the weights of eq. 14
+      T w0, wd[NF];
+      if constexpr (F32) cweno_weights<NF>(SI0, SId, adm, a.log2_lam1, log2lams, a.eps32, w0, wd);
+      else cweno_weights<NF>(SI0, SId, adm, a.lam1, lamsd, a.eps, w0, wd);
 #pragma unroll
-      for (int k = 0; k < NK; ++k) ao[k] = a1[k];
-    } else {
-      const T w = (T)1 / (T)__popc(bits >> 1);
-#pragma unroll
-      for (int k = 0; k < NK; ++k) ao[k] = (T)0;
+      for (int k = 0; k < NK; ++k) ao[k] = w0 * a1[k];
 #pragma unroll
       for (int f = 0; f < NF; ++f)
-        if ((bits >> (1 + f)) & 1u) {
 #pragma unroll
-          for (int k = 0; k < D; ++k) ao[k] += w * ad[f][k];
-        }
+        for (int k = 0; k < D; ++k) ao[k] += wd[f] * ad[f][k];  // zero weight where inadmissible
+      bits = 1u | (adm << 1);
+    } else {
+      if constexpr (F32) {
+        bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.log2_lam1, log2lams,
+                               inv_stm1, a.eps32, a.C_T32);
+      } else {
+        bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
+      }
+      if (bits & 1u) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) ao[k] = a1[k];
+      } else {
+        const T w = (T)1 / (T)__popc(bits >> 1);
+#pragma unroll
+        for (int k = 0; k < NK; ++k) ao[k] = (T)0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          if ((bits >> (1 + f)) & 1u) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) ao[k] += w * ad[f][k];
+          }
+      }
+      if (bits & 1u) bits = 1u;
     }
-    if (a.flags && active) a.flags[v * N + i] = (uint8_t)((bits & 1u) ? 1u : bits);
+    if (a.flags && active) a.flags[v * N + i] = (uint8_t)bits;
   }
 
   // face values of variable v; the positivity guard gathers rho, momentum and E of each point

@@ -8,7 +8,7 @@ import os
 
 import numpy as np
 
-CTENO_SCHEME_CTENO, CTENO_SCHEME_CTENOZ = 0, 1
+CTENO_SCHEME_CTENO, CTENO_SCHEME_CTENOZ, CTENO_SCHEME_CWENO, CTENO_SCHEME_TENO = 0, 1, 2, 3
 CTENO_FP64, CTENO_MIXED = 0, 1
 CTENO_BOUNDARY_TRANSMISSIVE = 0
 

@@ -56,7 +56,8 @@ SCHEDULES = [(128, 128), (1024 + 256, 1024 + 128)]
 
 
 @pytest.mark.parametrize("launch", SCHEDULES, ids=["cell-thread", "var-lanes"])
-@pytest.mark.parametrize("scheme,form", [(0, 0), (1, 0), (1, 1)], ids=["CTENO", "CTENOZ", "CTENOZ-wenoz"])
+@pytest.mark.parametrize("scheme,form", [(0, 0), (1, 0), (1, 1), (2, 0), (3, 0)],
+                         ids=["CTENO", "CTENOZ", "CTENOZ-wenoz", "CWENO", "TENO"])
 @pytest.mark.parametrize("name,make,degree", CASES, ids=[c[0] for c in CASES])
 def test_one_stage_face_states_flags_and_update(name, make, degree, scheme, form, launch):
     native = _native()
@@ -104,7 +105,7 @@ def test_density_wave_10_steps_fp64_matches_oracle():
     s.close()
 
 
-@pytest.mark.parametrize("scheme,degree", [(0, 2), (1, 2), (0, 3), (1, 3)])
+@pytest.mark.parametrize("scheme,degree", [(0, 2), (1, 2), (0, 3), (1, 3), (2, 2), (3, 2), (2, 3), (3, 3)])
 def test_shock_tube_fp64_matches_oracle(scheme, degree):
     """Sod states on a reduced copy of the 512x128 shock-tube mesh (same construction), CFL 0.4,
     10 steps."""

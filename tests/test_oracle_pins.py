@@ -163,10 +163,11 @@ def _poly_state(mesh, polys):
     return np.array([[X.poly_cell_average(p, V[c]) for c in range(mesh.ncells)] for p in polys])
 
 
+@pytest.mark.parametrize("scheme", [0, 2, 3], ids=["CTENO", "CWENO", "TENO"])
 @pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 6), (3, 3, 5)])
-def test_linear_fields_reproduced_by_whole_reconstruction(dim, degree, n):
-    """A linear field is reproduced exactly by every stencil, hence by any CTENO selection:
-    the face-point states equal the field at the face points."""
+def test_linear_fields_reproduced_by_whole_reconstruction(dim, degree, n, scheme):
+    """A linear field is reproduced exactly by every stencil, hence by any selection or convex
+    weighting: the face-point states equal the field at the face points."""
     mesh = W.tri_mesh(n, n, periodic=False) if dim == 2 else W.tet_mesh(n, periodic=False)
     rng = _rng(11)
     nv = dim + 2
@@ -176,7 +177,7 @@ def test_linear_fields_reproduced_by_whole_reconstruction(dim, degree, n):
         p[(0,) * dim] = 2.0 + v
         polys.append(p)
     U = _poly_state(mesh, polys)
-    o = Oracle(mesh, degree=degree, guard=0)
+    o = Oracle(mesh, degree=degree, guard=0, scheme=scheme)
     o.set_state(U)
     o.residual()
     fs = o.face_states()
@@ -221,13 +222,14 @@ def test_degree_r_fields_reproduced_by_central_polynomial(dim, degree, n):
         assert np.abs(fs[..., v] - ref).max() < tol
 
 
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3], ids=["CTENO", "CTENOZ", "CWENO", "TENO"])
 @pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 6), (3, 3, 6)])
-def test_reconstruction_preserves_cell_mean(dim, degree, n):
-    """eq. 4: the cell average of the final polynomial equals U_i, for any selection."""
+def test_reconstruction_preserves_cell_mean(dim, degree, n, scheme):
+    """eq. 4: the cell average of the final polynomial equals U_i, for any selection or weights."""
     wl = W.density_wave_2d(n) if dim == 2 else W.density_wave_3d(n)
     rng = _rng(13)
     U = wl.U0 * (1.0 + 0.05 * rng.uniform(-1, 1, size=wl.U0.shape))
-    o = Oracle(wl.mesh, degree=degree)
+    o = Oracle(wl.mesh, degree=degree, scheme=scheme)
     o.set_state(U)
     o.residual()
     coef = o.coefficients()
@@ -472,11 +474,12 @@ def test_lambda1p_sensitivity_matches_tables_1_and_2():
     assert oZ > 2.65 and oC < oZ - 0.4, (oC, oZ)
 
 
-def test_sod_shock_tube_against_exact_riemann_solution():
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3], ids=["CTENO", "CTENOZ", "CWENO", "TENO"])
+def test_sod_shock_tube_against_exact_riemann_solution(scheme):
     """Sec. 3.2: density of the 2D Sod problem (conserved variables) against the exact solution,
     averaged across y; a coarse mesh, t = 0.15."""
     wl = W.shock_tube_2d(nx=80, ny=8)
-    o = Oracle(wl.mesh, degree=2, scheme=0, cfl=0.4)
+    o = Oracle(wl.mesh, degree=2, scheme=scheme, cfl=0.4)
     o.set_state(wl.U0)
     t, T = 0.0, 0.15
     while t < T - 1e-14:

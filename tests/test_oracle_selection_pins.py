@@ -220,3 +220,67 @@ def test_time_step_closed_form_3d():
     o = Oracle(mesh, setup=False, degree=2, cfl=cfl)
     o.set_state(W.uniform_state(mesh, [rho, w, w, w, p]))
     assert abs(o.dt() - expect) < 1e-14 * expect
+
+
+# --------------------------------------------------------------------------------------------
+# CWENO (Sec. 2.3, weights of eq. 14 with b = 4) and TENO (Sec. 2.4)
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("st", [2, 3, 4])
+@pytest.mark.parametrize("lambda1p", [2.0, 1e4, 1e15])
+def test_cweno_weights_closed_form(st, lambda1p):
+    """w~_s = lambda_s / (eps + SI_s)^4 normalised. Equal indicators give w_s = lambda_s; with the
+    directional indicators y = x (lambda_s / lambda_1)^(1/4) every w~_s is equal, so w_s = 1/s_t.
+    Every stencil contributes (all bits)."""
+    lam1, lams = _lams(lambda1p, st)
+    bits, w = select([0.3] * st, scheme=2, lambda1p=lambda1p, eps=0.0)
+    assert bits == (1 << st) - 1
+    assert np.allclose(w, [lam1] + [lams] * (st - 1), rtol=1e-13, atol=0)
+    x = 0.7
+    y = x * (lams / lam1) ** 0.25
+    bits, w = select([x] + [y] * (st - 1), scheme=2, lambda1p=lambda1p, eps=0.0)
+    assert np.allclose(w, 1.0 / st, rtol=1e-12), w
+
+
+@pytest.mark.parametrize("st", [2, 3, 4])
+def test_teno_cutoff_has_no_linear_coefficients(st):
+    """TENO (eqs. 19-23) has no linear coefficients: chi_1 < C_T exactly when
+    (x/S)^6 > (1 - C_T)/(C_T (s_t - 1)), whatever lam_gamma says."""
+    C_T = 1e-6
+    r = ((1.0 - C_T) / (C_T * (st - 1))) ** (1.0 / 6.0)
+    for lam_gamma in (0, 1):
+        for side, kept in ((1 - MARGIN, True), (1 + MARGIN, False)):
+            bits, _ = select([r * side] + [1.0] * (st - 1), scheme=3, lam_gamma=lam_gamma, C_T=C_T, eps=0.0)
+            assert bool(bits & 1) == kept
+
+
+def _poly_field(mesh, degree, rng):
+    from tests import exact as X
+    V = W.unwrapped_cell_vertices(mesh)
+    polys = []
+    for v in range(mesh.dim + 2):
+        p = X.random_poly(mesh.dim, degree, rng, 0.2)
+        p[(0,) * mesh.dim] = 2.0 + v
+        polys.append(p)
+    U = np.array([[X.poly_cell_average(p, V[c]) for c in range(mesh.ncells)] for p in polys])
+    return polys, U
+
+
+@pytest.mark.parametrize("dim,degree,n", [(2, 2, 8), (2, 3, 10), (3, 2, 5)])
+def test_teno_central_polynomial_is_the_least_squares_fit(dim, degree, n):
+    """TENO keeps the central stencil's own least-squares polynomial (Sec. 2.4), CTENO the CWENO
+    split p_1 = (p_opt - sum lambda_s p_s)/lambda_1 (eq. 17). At lambda_1' = 2 and C_T = 0 (central
+    always kept) TENO reproduces a degree-r field exactly; CTENO does not (its p_1 carries the
+    directional fits, which are only linear)."""
+    from tests import exact as X
+    mesh = W.tri_mesh(n, n, periodic=False) if dim == 2 else W.tet_mesh(n, periodic=False)
+    polys, U = _poly_field(mesh, degree, np.random.default_rng(41))
+    errs = {}
+    for scheme in (3, 0):
+        o = Oracle(mesh, degree=degree, scheme=scheme, lambda1p=2.0, C_T=0.0, guard=0)
+        o.set_state(U)
+        o.residual()
+        fs = o.face_states()
+        fq, _ = o.face_points()
+        errs[scheme] = max(np.abs(fs[..., v] - X.poly_eval(polys[v], fq)).max() for v in range(dim + 2))
+    assert errs[3] < 1e-11, errs
+    assert errs[0] > 1e-4, errs
