@@ -114,6 +114,7 @@ class Oracle:
         info = np.zeros(8, np.int32)
         self.lib.orc_info(self.h, info)
         self.nv, self.nf, self.nq, self.nk, self.M = (int(x) for x in info[:5])
+        self.dmax = int(info[7])   # members kept per directional stencil
         self.ncells = mesh.ncells
         if setup:
             rc = self.lib.orc_setup_all(self.h)
@@ -206,7 +207,7 @@ class Oracle:
     def stencil(self, i: int):
         d = self.dim
         central = np.empty(self.M, np.int32)
-        dirm = np.empty((self.nf, 2 * d), np.int32)
+        dirm = np.empty((self.nf, self.dmax), np.int32)
         dok = np.empty(self.nf, np.int32)
         self.lib.orc_get_stencil(self.h, int(i), central, dirm, dok)
         return central, dirm, dok

@@ -32,10 +32,12 @@
 #endif
 
 #define MAXD 3
-#define MAXK 20   /* K(3,3): coefficients of a cubic in 3D, constant included (eq. 6) */
-#define MAXM 40   /* M = 2K (Sec. 2.1) */
+#define MAXK 28   /* K(6,2) = K(3,3) + 8: coefficients of a sextic in 2D, constant included (eq. 6) */
+#define MAXM 56   /* M = 2K (Sec. 2.1) */
 #define MAXNF 4   /* faces of a simplex */
-#define MAXDIR 6  /* Reading: at most 2d cells in a directional stencil */
+#define MAXDIR 10 /* Reading: at most 2 (K_dir - 1) cells in a directional stencil */
+#define MAXKD 5   /* unknowns of a directional polynomial: degree 1 (d of them) or, for central
+                     degree >= 4 in 2D, degree 2 (5 of them) */
 #define MAXNQ 4   /* face Gauss points */
 #define MAXNV 5   /* conserved variables */
 
@@ -61,13 +63,14 @@ typedef struct {
   int ndir[MAXNF];              /* members of each directional stencil */
   int dmem[MAXNF][MAXDIR];      /* their positions in the central list */
   int dok[MAXNF];               /* admissible? */
-  double dA[MAXNF][MAXDIR][MAXD];
-  double dR[MAXNF][MAXD][MAXD];
+  double dA[MAXNF][MAXDIR][MAXKD];
+  double dR[MAXNF][MAXKD][MAXKD];
 } orc_cell;
 
 typedef struct {
   orc_params p;
   int nverts, ncells, nv, nf, nq, nk; /* nk = K-1 unknowns of the central polynomial */
+  int dk, ddeg, dmax;  /* directional polynomials: unknowns, degree, members kept */
   int M;
   double period[MAXD];
   double *xyz;         /* [nverts][dim] */
@@ -339,12 +342,19 @@ static void sort_ints(int *a, int n) {
  * order", Sec. 2 after eq. 2): 2D edges use 2-point Gauss-Legendre; 3D triangles use the
  * collapsed 2x2 rule (Gauss-Jacobi with weight (1-u) in u, Gauss-Legendre in v), exact for
  * degree 3. Weights sum to 1. */
-static void face_rule(int d, double t[MAXNQ][3], double *w) {
-  if (d == 2) {
+static void face_rule(int d, int nq, double t[MAXNQ][3], double *w) {
+  if (d == 2 && nq == 2) {
     double g = 1.0 / sqrt(3.0);
     t[0][0] = 0.5 * (1.0 - g); /* fraction along sorted edge a->b */
     t[1][0] = 0.5 * (1.0 + g);
     w[0] = w[1] = 0.5;
+  } else if (d == 2) {
+    double g[MAXNQ], gw[MAXNQ];
+    gauss_legendre(nq, g, gw);
+    for (int q = 0; q < nq; ++q) {
+      t[q][0] = 0.5 * (1.0 + g[q]); /* fraction along sorted edge a->b, ascending */
+      w[q] = 0.5 * gw[q];
+    }
   } else {
     /* Gauss-Jacobi, weight (1-u) on [0,1]: roots of u^2 - 0.8 u + 0.1 */
     double u[2] = {0.4 - sqrt(0.06), 0.4 + sqrt(0.06)};
@@ -400,7 +410,7 @@ static int build_faces(orc *o) {
   free(fr);
   /* outward unit normals, areas, canonical Gauss points */
   double t[MAXNQ][3];
-  face_rule(d, t, o->fw);
+  face_rule(d, o->nq, t, o->fw);
   o->area = (double *)malloc(sizeof(double) * n * nf);
   o->nrm = (double *)malloc(sizeof(double) * n * nf * d);
   o->fq = (double *)malloc(sizeof(double) * n * nf * o->nq * d);
@@ -594,7 +604,7 @@ static void directional_stencils(orc *o, int i, orc_cell *c) {
       for (int j = 0; j < d; ++j)
         if (beta[j] < 0.0) inside = 0;
       if (inside) {
-        if (c->ndir[f] < 2 * d) c->dmem[f][c->ndir[f]++] = k;
+        if (c->ndir[f] < o->dmax) c->dmem[f][c->ndir[f]++] = k;
         break;
       }
     }
@@ -707,7 +717,7 @@ static int cell_setup(orc *o, int i) {
   int rc = central_stencil(o, i, c);
   if (rc) return rc;
   directional_stencils(o, i, c);
-  const int d = o->p.dim, nk = o->nk;
+  const int nk = o->nk;
   if (!c->A) c->A = (double *)malloc(sizeof(double) * c->nst * nk);
   if (!c->R) c->R = (double *)malloc(sizeof(double) * nk * nk);
   for (int k = 0; k < c->nst; ++k) {
@@ -716,13 +726,15 @@ static int cell_setup(orc *o, int i) {
     moments(o, xi, nk, c->A + k * nk, &c->Vp[k]);
   }
   if (!householder_R(c->nst, nk, c->A, nk, c->R, nk)) return -7;
+  const int dk = o->dk;
   for (int f = 0; f < o->nf; ++f) {
-    /* degree-1 directional polynomial: its d unknowns are the linear coefficients, whose
-     * moments are the first d columns of the central A rows */
+    /* directional polynomial of degree 1 (or 2): its dk unknowns are the coefficients of the
+     * first dk basis functions (graded), whose moments are the first dk columns of the central
+     * A rows */
     for (int j = 0; j < c->ndir[f]; ++j)
-      for (int k = 0; k < d; ++k) c->dA[f][j][k] = c->A[c->dmem[f][j] * nk + k];
-    c->dok[f] = (c->ndir[f] >= d) &&
-                householder_R(c->ndir[f], d, &c->dA[f][0][0], MAXD, &c->dR[f][0][0], MAXD);
+      for (int k = 0; k < dk; ++k) c->dA[f][j][k] = c->A[c->dmem[f][j] * nk + k];
+    c->dok[f] = (c->ndir[f] >= dk) &&
+                householder_R(c->ndir[f], dk, &c->dA[f][0][0], MAXKD, &c->dR[f][0][0], MAXKD);
   }
   c->ready = 1;
   return 0;
@@ -831,23 +843,23 @@ static void recon_cell(orc *o, int i, const double *U) {
   double fout[MAXNF][MAXNQ][MAXNV];
   for (int v = 0; v < nv; ++v) {
     const double U0 = U[v * n + i];
-    double b[MAXM], aopt[MAXK], ad[MAXNF][MAXD];
+    double b[MAXM], aopt[MAXK], ad[MAXNF][MAXKD];
     for (int k = 0; k < c->nst; ++k) b[k] = c->Vp[k] * (U[v * n + c->ids[k]] - U0); /* eq. 10 */
     lsq_solve(c->nst, nk, c->A, nk, c->R, nk, b, aopt);   /* p_opt */
     for (int s = 0; s < na; ++s) {
       int f = adm[s];
       double bd[MAXDIR];
       for (int j = 0; j < c->ndir[f]; ++j) bd[j] = b[c->dmem[f][j]];
-      lsq_solve(c->ndir[f], d, &c->dA[f][0][0], MAXD, &c->dR[f][0][0], MAXD, bd, ad[f]);
+      lsq_solve(c->ndir[f], o->dk, &c->dA[f][0][0], MAXKD, &c->dR[f][0][0], MAXKD, bd, ad[f]);
     }
     /* p_1 = (p_opt - sum_{s>=2} lambda_s p_s) / lambda_1  (eq. 17); the directional
-     * polynomials are linear, so only the first d coefficients receive their terms; TENO keeps
-     * p_1 = p_opt */
+     * polynomials only have the first dk coefficients, so only those receive their terms; TENO
+     * keeps p_1 = p_opt */
     double a1[MAXK];
     if (st > 1 && o->p.scheme != 3) { /* TENO keeps the central polynomial itself (Sec. 2.4) */
       for (int k = 0; k < nk; ++k) {
         double s = aopt[k];
-        if (k < d)
+        if (k < o->dk)
           for (int t = 0; t < na; ++t) s -= lams * ad[adm[t]][k];
         a1[k] = s / lam1;
       }
@@ -857,7 +869,7 @@ static void recon_cell(orc *o, int i, const double *U) {
     /* smoothness indicators (eq. 15) of p_1 and of the directional polynomials */
     double SI[1 + MAXNF];
     SI[0] = smoothness(o, a1, nk, o->p.degree);
-    for (int s = 0; s < na; ++s) SI[1 + s] = smoothness(o, ad[adm[s]], d, 1);
+    for (int s = 0; s < na; ++s) SI[1 + s] = smoothness(o, ad[adm[s]], o->dk, o->ddeg);
     for (int s = 0; s <= nf; ++s) o->SI[((size_t)i * nv + v) * (1 + nf) + s] = 0.0;
     o->SI[((size_t)i * nv + v) * (1 + nf)] = SI[0];
     for (int s = 0; s < na; ++s) o->SI[((size_t)i * nv + v) * (1 + nf) + 1 + adm[s]] = SI[1 + s];
@@ -879,7 +891,7 @@ static void recon_cell(orc *o, int i, const double *U) {
     if (o->p.scheme == 2) {
       for (int k = 0; k < nk; ++k) af[k] = chi[0] * a1[k];
       for (int s = 1; s < st; ++s)
-        for (int k = 0; k < d; ++k) af[k] += chi[s] * ad[adm[s - 1]][k];
+        for (int k = 0; k < o->dk; ++k) af[k] += chi[s] * ad[adm[s - 1]][k];
       fl = (uint8_t)(o->stmask[i] & 0xFF);
     } else if (delta[0]) {
       for (int k = 0; k < nk; ++k) af[k] = a1[k];
@@ -888,7 +900,7 @@ static void recon_cell(orc *o, int i, const double *U) {
       for (int k = 0; k < nk; ++k) af[k] = 0.0;
       for (int s = 1; s < st; ++s)
         if (delta[s]) {
-          for (int k = 0; k < d; ++k) af[k] += ad[adm[s - 1]][k] / (double)ndel;
+          for (int k = 0; k < o->dk; ++k) af[k] += ad[adm[s - 1]][k] / (double)ndel;
           fl |= (uint8_t)(1 << (1 + adm[s - 1]));
         }
     }
@@ -1072,7 +1084,7 @@ orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form,
                 double lambda1p, double eps, double gamma, double cfl, int guard, int nverts,
                 const double *xyz, int ncells, const int *cells, const double *period, int *err) {
   *err = 0;
-  if ((dim != 2 && dim != 3) || degree < 1 || degree > 3) {
+  if ((dim != 2 && dim != 3) || degree < 1 || degree > (dim == 2 ? 6 : 3)) {
     *err = -1;
     return NULL;
   }
@@ -1092,7 +1104,16 @@ orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form,
   o->ncells = ncells;
   o->nv = dim + 2;
   o->nf = dim + 1;
-  o->nq = (dim == 2) ? 2 : 4;
+  /* Reading ("a Gauss rule suited to the polynomial order", Sec. 2): edges carry
+   * ceil((r + 1) / 2) Gauss-Legendre points, exact for the degree-r face polynomials */
+  o->nq = (dim == 2) ? (degree + 2) / 2 : 4;
+  if (dim == 2 && o->nq < 2) o->nq = 2;
+  /* Reading (Fig. 1: third-order directional stencils beside a fifth-order central one):
+   * directional polynomials of degree 1, or 2 when the central degree is 4 or more; each
+   * directional stencil keeps up to twice as many cells as its polynomial has unknowns */
+  o->ddeg = (degree >= 4) ? 2 : 1;
+  o->dk = K_of(o->ddeg, dim) - 1;
+  o->dmax = 2 * o->dk;
   o->nk = make_exponents(dim, degree, o->ex);
   o->M = 2 * K_of(degree, dim);
   for (int j = 0; j < dim; ++j) o->period[j] = period ? period[j] : 0.0;
@@ -1257,7 +1278,7 @@ int orc_reconstruct_cells(orc *o, int count, const int *ids) {
 
 int orc_info(const orc *o, int *out) {
   out[0] = o->nv; out[1] = o->nf; out[2] = o->nq; out[3] = o->nk; out[4] = o->M;
-  out[5] = o->err; out[6] = o->nguard;
+  out[5] = o->err; out[6] = o->nguard; out[7] = o->dmax;
   return 0;
 }
 
@@ -1279,14 +1300,13 @@ void orc_get_face_points(const orc *o, double *fq, double *fw) {
   if (fw) memcpy(fw, o->fw, sizeof(double) * o->nq);
 }
 
-/* Stencil of cell i: central ids [M], directional member positions [nf][2d] (-1 padded),
+/* Stencil of cell i: central ids [M], directional member positions [nf][dmax] (-1 padded),
  * admissibility [nf]. Cell i must be set up. */
 void orc_get_stencil(const orc *o, int i, int *central, int *dir, int *dok) {
   const orc_cell *c = o->cell[i];
-  const int d = o->p.dim;
   for (int k = 0; k < o->M; ++k) central[k] = c->ids[k];
   for (int f = 0; f < o->nf; ++f) {
-    for (int j = 0; j < 2 * d; ++j) dir[f * 2 * d + j] = (j < c->ndir[f]) ? c->dmem[f][j] : -1;
+    for (int j = 0; j < o->dmax; ++j) dir[f * o->dmax + j] = (j < c->ndir[f]) ? c->dmem[f][j] : -1;
     dok[f] = c->dok[f];
   }
 }
