@@ -60,11 +60,15 @@ typedef struct {
   double Vp[MAXM];              /* |V'_m| */
   double *A;                    /* [M][nk]: A_mk of eq. 10 (central) */
   double *R;                    /* [nk][nk]: Householder R of A (eq. 12) */
+  double *V;                    /* [M][nk]: Householder vectors of that QR (column k, rows >= k) */
+  double beta[MAXK];            /*   and their factors, H_k = I - beta_k v_k v_k^T */
   int ndir[MAXNF];              /* members of each directional stencil */
   int dmem[MAXNF][MAXDIR];      /* their positions in the central list */
   int dok[MAXNF];               /* admissible? */
   double dA[MAXNF][MAXDIR][MAXKD];
   double dR[MAXNF][MAXKD][MAXKD];
+  double dV[MAXNF][MAXDIR][MAXKD];
+  double dbeta[MAXNF][MAXKD];
 } orc_cell;
 
 typedef struct {
@@ -652,11 +656,17 @@ static void moments(orc *o, double xi[4][3], int nk, double *Arow, double *Vp) {
 
 /* Householder QR of the m x n matrix A (Golub & Van Loan, Alg. 5.2.1), returning R (n x n)
  * and the rank test min|R_kk| > 1e-10 max|R_kk|. */
-static int householder_R(int m, int n, const double *A, int lda, double *R, int ldr) {
+/* Householder QR of the m x n matrix A (m >= n): A = Q R with Q = H_0 H_1 ... H_{n-1},
+ * H_k = I - beta_k v_k v_k^T. Stores R (n x n, upper) and the vectors v_k (column k of V, rows
+ * k..m-1). Returns 1 if A has numerically full column rank (min |R_kk| > 1e-10 max |R_kk|). */
+static int householder_qr(int m, int n, const double *A, int lda, double *V, int ldv, double *beta,
+                          double *R, int ldr) {
   double W[MAXM][MAXK];
   for (int r = 0; r < m; ++r)
     for (int k = 0; k < n; ++k) W[r][k] = A[r * lda + k];
   for (int k = 0; k < n; ++k) {
+    for (int r = 0; r < m; ++r) V[r * ldv + k] = 0.0;
+    beta[k] = 0.0;
     double nrm = 0.0;
     for (int r = k; r < m; ++r) nrm += W[r][k] * W[r][k];
     nrm = sqrt(nrm);
@@ -668,10 +678,12 @@ static int householder_R(int m, int n, const double *A, int lda, double *R, int 
     double vv = 0.0;
     for (int r = k; r < m; ++r) vv += v[r] * v[r];
     if (vv == 0.0) continue;
+    for (int r = k; r < m; ++r) V[r * ldv + k] = v[r];
+    beta[k] = 2.0 / vv;
     for (int cc = k; cc < n; ++cc) {
       double s = 0.0;
       for (int r = k; r < m; ++r) s += v[r] * W[r][cc];
-      s = 2.0 * s / vv;
+      s *= beta[k];
       for (int r = k; r < m; ++r) W[r][cc] -= s * v[r];
     }
   }
@@ -686,22 +698,20 @@ static int householder_R(int m, int n, const double *A, int lda, double *R, int 
   return (m >= n && mx > 0.0 && mn > 1e-10 * mx) ? 1 : 0;
 }
 
-/* a = (R^T R)^-1 A^T b  (eq. 12), with R from the Householder QR of A. */
-static void lsq_solve(int m, int n, const double *A, int lda, const double *R, int ldr,
+/* The least-squares solution of eq. 12, a = (A^T A)^-1 A^T b, through the QR of A: y = Q^T b
+ * (the reflectors applied in order), then R a = y_{0..n-1} by back substitution. */
+static void lsq_solve(int m, int n, const double *V, int ldv, const double *beta, const double *R, int ldr,
                       const double *b, double *a) {
-  double y[MAXK], z[MAXK];
+  double y[MAXM];
+  for (int r = 0; r < m; ++r) y[r] = b[r];
   for (int k = 0; k < n; ++k) {
     double s = 0.0;
-    for (int r = 0; r < m; ++r) s += A[r * lda + k] * b[r];
-    y[k] = s;
+    for (int r = k; r < m; ++r) s += V[r * ldv + k] * y[r];
+    s *= beta[k];
+    for (int r = k; r < m; ++r) y[r] -= s * V[r * ldv + k];
   }
-  for (int k = 0; k < n; ++k) { /* R^T z = y */
+  for (int k = n - 1; k >= 0; --k) {
     double s = y[k];
-    for (int j = 0; j < k; ++j) s -= R[j * ldr + k] * z[j];
-    z[k] = s / R[k * ldr + k];
-  }
-  for (int k = n - 1; k >= 0; --k) { /* R a = z */
-    double s = z[k];
     for (int j = k + 1; j < n; ++j) s -= R[k * ldr + j] * a[j];
     a[k] = s / R[k * ldr + k];
   }
@@ -720,12 +730,13 @@ static int cell_setup(orc *o, int i) {
   const int nk = o->nk;
   if (!c->A) c->A = (double *)malloc(sizeof(double) * c->nst * nk);
   if (!c->R) c->R = (double *)malloc(sizeof(double) * nk * nk);
+  if (!c->V) c->V = (double *)malloc(sizeof(double) * c->nst * nk);
   for (int k = 0; k < c->nst; ++k) {
     double xi[4][3];
     member_ref_vertices(o, i, c, k, xi);
     moments(o, xi, nk, c->A + k * nk, &c->Vp[k]);
   }
-  if (!householder_R(c->nst, nk, c->A, nk, c->R, nk)) return -7;
+  if (!householder_qr(c->nst, nk, c->A, nk, c->V, nk, c->beta, c->R, nk)) return -7;
   const int dk = o->dk;
   for (int f = 0; f < o->nf; ++f) {
     /* directional polynomial of degree 1 (or 2): its dk unknowns are the coefficients of the
@@ -734,7 +745,8 @@ static int cell_setup(orc *o, int i) {
     for (int j = 0; j < c->ndir[f]; ++j)
       for (int k = 0; k < dk; ++k) c->dA[f][j][k] = c->A[c->dmem[f][j] * nk + k];
     c->dok[f] = (c->ndir[f] >= dk) &&
-                householder_R(c->ndir[f], dk, &c->dA[f][0][0], MAXKD, &c->dR[f][0][0], MAXKD);
+                householder_qr(c->ndir[f], dk, &c->dA[f][0][0], MAXKD, &c->dV[f][0][0], MAXKD, c->dbeta[f],
+                               &c->dR[f][0][0], MAXKD);
   }
   c->ready = 1;
   return 0;
@@ -845,12 +857,12 @@ static void recon_cell(orc *o, int i, const double *U) {
     const double U0 = U[v * n + i];
     double b[MAXM], aopt[MAXK], ad[MAXNF][MAXKD];
     for (int k = 0; k < c->nst; ++k) b[k] = c->Vp[k] * (U[v * n + c->ids[k]] - U0); /* eq. 10 */
-    lsq_solve(c->nst, nk, c->A, nk, c->R, nk, b, aopt);   /* p_opt */
+    lsq_solve(c->nst, nk, c->V, nk, c->beta, c->R, nk, b, aopt);   /* p_opt */
     for (int s = 0; s < na; ++s) {
       int f = adm[s];
       double bd[MAXDIR];
       for (int j = 0; j < c->ndir[f]; ++j) bd[j] = b[c->dmem[f][j]];
-      lsq_solve(c->ndir[f], o->dk, &c->dA[f][0][0], MAXKD, &c->dR[f][0][0], MAXKD, bd, ad[f]);
+      lsq_solve(c->ndir[f], o->dk, &c->dV[f][0][0], MAXKD, c->dbeta[f], &c->dR[f][0][0], MAXKD, bd, ad[f]);
     }
     /* p_1 = (p_opt - sum_{s>=2} lambda_s p_s) / lambda_1  (eq. 17); the directional
      * polynomials only have the first dk coefficients, so only those receive their terms; TENO
@@ -1190,6 +1202,7 @@ void orc_destroy(orc *o) {
       if (o->cell[i]) {
         free(o->cell[i]->A);
         free(o->cell[i]->R);
+        free(o->cell[i]->V);
         free(o->cell[i]);
       }
     free(o->cell);
@@ -1326,7 +1339,7 @@ void orc_lsq_apply(const orc *o, int i, const double *Um, double U0, double *a) 
   const orc_cell *c = o->cell[i];
   double b[MAXM];
   for (int k = 0; k < c->nst; ++k) b[k] = c->Vp[k] * (Um[k] - U0);
-  lsq_solve(c->nst, o->nk, c->A, o->nk, c->R, o->nk, b, a);
+  lsq_solve(c->nst, o->nk, c->V, o->nk, c->beta, c->R, o->nk, b, a);
 }
 
 void orc_get_face_states(const orc *o, double *out) {
