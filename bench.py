@@ -67,7 +67,8 @@ def make_case(name, n=0):
         wl = W.shock_tube_2d(512, 128)
         return Case(name, "2D shock tube [0,1]x[0,0.25], 512x128 squares -> 131072 triangles, jitter 0.1h, "
                     "Sod states, transmissive, CFL 0.4", [wl.mesh], [wl.U0], 2, 0, 2, 0.4,
-                    [(0, 2), (0, 3), (1, 2), (1, 3), (2, 2), (2, 3), (3, 2), (3, 3)], (0.5, 0.125))
+                    [(0, 2), (0, 3), (1, 2), (1, 3), (2, 2), (2, 3), (3, 2), (3, 3),
+                     (0, 4), (1, 4), (0, 5), (1, 5), (0, 6), (1, 6)], (0.5, 0.125))
     if name == "density_wave_3d_64":
         n = n or 64
         wl = W.density_wave_3d(n)
@@ -101,7 +102,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--variant-seconds", type=float, default=1.0,
                     help="timed work per variant (steps chosen from the warm-up's step time)")
-    ap.add_argument("--variants", choices=["all", "none"], default="all")
+    ap.add_argument("--variants", choices=["all", "workload", "none"], default="all",
+                    help="all: every workload's variants; workload: the chosen workload's only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="blast_3d_96", choices=WORKLOADS)
     ap.add_argument("--n", type=int, default=0,
@@ -230,6 +232,8 @@ def alu_peak(native):
 def recon_kernel_name(dim, degree, scheme, precision, launch):
     """Name of the reconstruction kernel a launch value selects."""
     args = f"{dim},{degree},{'float' if precision else 'double'},{SCHEMES[scheme]}"
+    if degree >= 4:
+        return f"recon_high_kernel<{degree},{'float' if precision else 'double'},{SCHEMES[scheme]}> x{launch - 1024}"
     if 6144 < launch <= 6152:
         return f"recon_stream_cells_kernel<{args}> x{32 * (launch - 6144)}"
     if 5120 < launch <= 5136:
@@ -413,11 +417,11 @@ def run_ours(args, rank, world, local):
 
     # variants: the headline workload in the other precision, then every other configuration ----
     variants = {}
-    if args.variants == "all":
+    if args.variants != "none":
         plan = [(case, sc, dg, pr) for sc, dg in case.variants for pr in (1, 0)
                 if (sc, dg, pr) != (h["scheme"], h["degree"], h["precision"])]
         for other in WORKLOADS:
-            if other != case.name:
+            if other != case.name and args.variants == "all":
                 plan.append((other, None, None, None))
         for item in plan:
             if isinstance(item[0], str):

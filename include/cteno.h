@@ -55,7 +55,10 @@ enum { CTENO_BOUNDARY_TRANSMISSIVE = 0 };
 /* Scheme parameters (paper notation). */
 typedef struct {
   int dim;              /* d = 2 (triangles) or 3 (tetrahedra) */
-  int degree;           /* r = 2 or 3: central polynomial degree, order r+1 (Sec. 2.1) */
+  int degree;           /* r: central polynomial degree, order r+1 (Sec. 2.1); 2 or 3, and in 2D
+                           also 4 to 6 (CTENO5-7, Sec. 2.3 and Fig. 1: directional stencils of
+                           degree 2 with at most 10 members, (r+2)/2 Gauss points per edge; the
+                           reconstruction runs the variable-per-lane schedule only) */
   int scheme;           /* CTENO_SCHEME_CTENO (Alg. 1) or CTENO_SCHEME_CTENOZ (Alg. 2); for
                            comparison in the same kernels, CTENO_SCHEME_CWENO (Sec. 2.3: every
                            stencil with the weights of eq. 14, b = 4, on the CWENO split p_1) and
@@ -194,15 +197,16 @@ int cteno_get_flags(cteno_ctx *ctx, int32_t mesh_id, uint8_t *out);
 int cteno_get_face_states(cteno_ctx *ctx, int32_t mesh_id, double *out);
 
 /* Host-side stencil of one cell (after cteno_stencil_build, before or after lsq_build):
- * central[M] original cell ids in nearest-first order, dir[(d+1)][2d] positions in `central` of
- * the members of each directional stencil (-1 padded). Admissibility is known only after
+ * central[M] original cell ids in nearest-first order, dir[(d+1)][nd] positions in `central` of
+ * the members of each directional stencil (-1 padded; nd = cteno_info out[8]). Admissibility is known only after
  * cteno_lsq_build; dok may be NULL before it. */
 int cteno_get_stencil(cteno_ctx *ctx, int32_t mesh_id, int64_t cell, int32_t *central,
                       int32_t *dir, int32_t *dok);
 
-/* Sizes: out[0] = nmeshes, out[1] = total cells, out[2] = M, out[3] = K-1, out[4] = nv,
+/* Sizes, out[9]: out[0] = nmeshes, out[1] = total cells, out[2] = M, out[3] = K-1, out[4] = nv,
  * out[5] = faces per cell, out[6] = Gauss points per face, out[7] = cells of mesh `mesh_id`
- * (or 0 if mesh_id < 0). */
+ * (or 0 if mesh_id < 0), out[8] = members of a directional stencil at most (2d up to degree 3,
+ * 10 for degrees 4 to 6). */
 int cteno_info(cteno_ctx *ctx, int32_t mesh_id, int64_t *out);
 
 /* Number of cells that fell back to their mean under the positivity guard since the last call,
@@ -235,7 +239,8 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
  * 8192 + b (b a multiple of 32 in
  * [32, 256]) selects the face-based schedule: HLLC once per face, in its owner's orientation, into
  * a face-flux array, then a per-cell gather and update (results bit-identical to the per-cell
- * schedules). */
+ * schedules). At central degrees 4 to 6 the reconstruction takes 1024 + b only (default 1024 +
+ * 128); every other reconstruction value is refused with CTENO_ERR_ARG. */
 int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block);
 
 /* Time the candidate launch configurations (block sizes 64/128/256, on the mixed path the

@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcteno.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU = ["setup.cu", "flux.cu", "recon_2d.cu", "recon_3d.cu", "alu_peak.cu", "noalloc.cu"]
+CU = ["setup.cu", "flux.cu", "recon_2d.cu", "recon_3d.cu", "recon_2d_high.cu", "alu_peak.cu", "noalloc.cu"]
 CPP = ["api.cpp", "mesh.cpp", "tables.cpp"]
 
 

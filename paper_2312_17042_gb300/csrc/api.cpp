@@ -171,7 +171,7 @@ cudaError_t enqueue_stage(cteno_ctx *ctx, int stage, int dt_swap, cudaStream_t s
   const KArgs a = make_args(ctx, stage, dt_swap);
   const cudaError_t e = launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, kscheme(ctx), a, ctx->recon_block, s);
   if (e != cudaSuccess) return e;
-  launch_flux(ctx->d, ctx->fp32 ? 1 : 0, a, ctx->flux_block, s);
+  launch_flux(ctx->d, ctx->nq, ctx->fp32 ? 1 : 0, a, ctx->flux_block, s);
   return cudaSuccess;
 }
 
@@ -263,7 +263,7 @@ void cteno_default_params(cteno_params *p) {
 int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream) {
   if (!out || !p) return CTENO_ERR_ARG;
   *out = nullptr;
-  if ((p->dim != 2 && p->dim != 3) || (p->degree != 2 && p->degree != 3) ||
+  if ((p->dim != 2 && p->dim != 3) || p->degree < 2 || p->degree > (p->dim == 2 ? 6 : 3) ||
       p->scheme < 0 || p->scheme > 3 || (p->precision != 0 && p->precision != 1) ||
       (p->ctenoz_form != 0 && p->ctenoz_form != 1) || (p->lam_gamma != 0 && p->lam_gamma != 1) ||
       !(p->lambda1p > 1.0) || !(p->C_T >= 0.0 && p->C_T < 1.0) || !(p->eps >= 0.0) ||
@@ -278,10 +278,11 @@ int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream) {
   ctx->d = p->dim;
   ctx->nv = p->dim + 2;
   ctx->nf = p->dim + 1;
-  ctx->nq = (p->dim == 2) ? 2 : 4;
+  ctx->nq = face_points(p->dim, p->degree);
   ctx->nk = coeff_count(p->degree, p->dim) - 1;
   ctx->M = 2 * coeff_count(p->degree, p->dim);
-  ctx->nd = 2 * p->dim;
+  ctx->nd = dir_members(p->dim, p->degree);
+  if (p->degree >= 4) ctx->recon_block = kLaneSchedule + 128;  // the schedule of degrees 4 to 6
   ctx->fp32 = (p->precision == CTENO_MIXED);
   build_tables(p->dim, p->degree, &ctx->tab);
   *out = ctx;
@@ -492,7 +493,7 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   CK(cudaMalloc(&dX, hX.size() * sizeof(double)));
   CK(dalloc(ctx, &ctx->d_tab, sizeof(DevTables)));
   CK(dalloc(ctx, &ctx->d_mesh_off, sizeof(int64_t) * (nmesh + 1)));
-  const int nvp = lay_nvp(d), pds = lay_pds(d);
+  const int nvp = lay_nvp(d), pds = dir_pds(d, ctx->p.degree);
   CK(dalloc(ctx, &ctx->U, sizeof(double) * nvp * N));
   CK(dalloc(ctx, &ctx->Un, sizeof(double) * nvp * N));
   if (ctx->fp32) CK(dalloc(ctx, &ctx->U32, 2 * sizeof(float) * nvp * N));
@@ -533,12 +534,13 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   std::memcpy(dt.vq, tab.vq, sizeof(dt.vq));
   std::memcpy(dt.vw, tab.vw, sizeof(dt.vw));
   CK(cudaMemcpyAsync(ctx->d_tab, &dt, sizeof(DevTables), cudaMemcpyHostToDevice, ctx->stream));
-  CK(d == 2 ? upload_recon_tables_2d(ctx->p.degree, tab, ctx->stream)
-            : upload_recon_tables_3d(ctx->p.degree, tab, ctx->stream));
+  CK(d == 3 ? upload_recon_tables_3d(ctx->p.degree, tab, ctx->stream)
+     : ctx->p.degree >= 4 ? upload_recon_tables_2d_high(ctx->p.degree, tab, ctx->stream)
+                          : upload_recon_tables_2d(ctx->p.degree, tab, ctx->stream));
   CK(cudaMemcpyAsync(ctx->d_mesh_off, hoff.data(), sizeof(int64_t) * (nmesh + 1), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(dX, hX.data(), hX.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->st, hst.data(), hst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
-  if (ctx->fp32) {
+  if (ctx->fp32 && ctx->p.degree <= 3) {  // the gather-staged schedule exists up to degree 3
     const int rc = build_gather_tiles(ctx, hst);
     if (rc) return rc;
   }
@@ -709,7 +711,7 @@ int cteno_run(cteno_ctx *ctx, int nsteps) {
         return fail(ctx, CTENO_ERR_CUDA, std::string("reconstruction launch: ") + cudaGetErrorString(le));
       }
       if (ctx->timing) CK(cudaEventRecordWithFlags(ctx->tev[2 * s + 1], ctx->capture, cudaEventRecordExternal));
-      launch_flux(ctx->d, ctx->fp32 ? 1 : 0, a, ctx->flux_block, ctx->capture);
+      launch_flux(ctx->d, ctx->nq, ctx->fp32 ? 1 : 0, a, ctx->flux_block, ctx->capture);
       if (ctx->timing) CK(cudaEventRecordWithFlags(ctx->tev[2 * s + 2], ctx->capture, cudaEventRecordExternal));
     }
     cudaError_t e = cudaStreamEndCapture(ctx->capture, &ctx->graph);
@@ -832,6 +834,7 @@ int cteno_info(cteno_ctx *ctx, int32_t mesh_id, int64_t *out) {
   out[5] = ctx->nf;
   out[6] = ctx->nq;
   out[7] = (mesh_id >= 0 && mesh_id < (int32_t)ctx->meshes.size()) ? ctx->meshes[mesh_id].ncells : 0;
+  out[8] = ctx->nd;
   return CTENO_OK;
 }
 
@@ -852,6 +855,8 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
   // variant (mixed path only, at most 128 threads)
   auto ok = [&](int b, bool recon) {
     if (b == 0) return true;
+    if (recon && ctx->p.degree >= 4)  // degrees 4 to 6: the variable-per-lane schedule only
+      return b >= kLaneSchedule + 32 && b <= kLaneSchedule + 256 && b % 32 == 0;
     if (b >= kFaceFlux)  // face-based flux schedule
       return !recon && b - kFaceFlux >= 32 && b - kFaceFlux <= 256 && b % 32 == 0;
     if (b > kStreamCells && b <= kStreamCells + 8)  // streamed cells: reconstruction, mixed, fits
@@ -922,8 +927,9 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
   // the lane schedules (variable per lane for the reconstruction, face per lane for the flux)
   for (int b : {128, 256}) cand.push_back(kLaneSchedule + b);
   std::vector<int> rcand = cand;
+  if (ctx->p.degree >= 4) rcand = {kLaneSchedule + 64, kLaneSchedule + 128, kLaneSchedule + 256};
   // the staged schedules (mixed path) whose two stages fit
-  if (ctx->fp32)
+  if (ctx->fp32 && ctx->p.degree <= 3)
     for (int b : {kStagedCells + 32, kStagedCells + 64, kStagedCells + 128, kStagedLanes + 64,
                   kStagedLanes + 128, kStagedLanes + 256})
       if (recon_staged_smem(ctx->d, ctx->p.degree, 1, b) <= kMaxStagedSmem) rcand.push_back(b);
@@ -933,7 +939,7 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
     if (hs / 2 <= kMaxStagedSmem) rcand.push_back(kHaloLanes + 1);
   }
   // the streamed lane schedule (mixed path) at the block sizes that fit
-  if (ctx->fp32) {
+  if (ctx->fp32 && ctx->p.degree <= 3) {
     for (int w : {8, 12, 16}) {
       if (recon_stream_smem(ctx->d, ctx->p.degree, w, 3) <= kMaxStreamSmem) rcand.push_back(kStreamLanes + w);
       if (recon_stream_smem(ctx->d, ctx->p.degree, w, 2) <= kMaxStreamSmem) rcand.push_back(kStreamLanes2 + w);
@@ -962,7 +968,7 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
     for (int r = 0; r < reps; ++r) {
       CK(save_restore(false));
       CK(cudaEventRecord(e0, ctx->stream));
-      launch_flux(ctx->d, ctx->fp32, a, b, ctx->stream);
+      launch_flux(ctx->d, ctx->nq, ctx->fp32, a, b, ctx->stream);
       CK(cudaEventRecord(e1, ctx->stream));
       CK(cudaEventSynchronize(e1));
       float ms = 0;
@@ -991,7 +997,7 @@ int cteno_kernel_stats(cteno_ctx *ctx, double *out) {
   const double N = (double)ctx->N, s = ctx->fp32 ? 4.0 : 8.0;
   const int nk = ctx->nk, M = ctx->M, nv = ctx->nv, nf = ctx->nf, nq = ctx->nq, d = ctx->d;
   const double members = (double)ctx->member_sum;
-  const double nvp = lay_nvp(d), pds = lay_pds(d);
+  const double nvp = lay_nvp(d), pds = dir_pds(d, ctx->p.degree);
   const double rec_u = 8.0 * nvp;  // own state record: FP32 (hi, lo) pairs or FP64 values
   // reconstruction: pseudo-inverse records (central + admissible directional faces), stencil ids,
   // cell info, own state record, face-state writes (neighbour means are re-reads of records
@@ -1007,7 +1013,7 @@ int cteno_kernel_stats(cteno_ctx *ctx, double *out) {
   // (SI = a^T O a counted in its symmetric form: nk(nk+1)/2 products and nk more per variable)
   out[2] = N * (2.0 * nk * M * nv + 2.0 * nv * (nk * (nk + 1) / 2.0 + nk) + nv * 30.0 * st +
                 2.0 * nv * nf * nq * nk) +
-           members * 2.0 * d * nv;
+           members * 2.0 * dir_unknowns(d, ctx->p.degree) * nv;
   // HLLC ~ 90 + 20 d operations per Gauss point, plus accumulation and the update
   out[3] = N * (nf * nq * (90.0 + 20.0 * d + 3.0 * nv) + 6.0 * nv);
   return CTENO_OK;
@@ -1026,7 +1032,7 @@ int cteno_profile_step(cteno_ctx *ctx, int nsteps, double *ms_out) {
       CK(cudaEventRecord(ev[2 * s], ctx->stream));
       CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, kscheme(ctx), a, ctx->recon_block, ctx->stream));
       CK(cudaEventRecord(ev[2 * s + 1], ctx->stream));
-      launch_flux(ctx->d, ctx->fp32, a, ctx->flux_block, ctx->stream);
+      launch_flux(ctx->d, ctx->nq, ctx->fp32, a, ctx->flux_block, ctx->stream);
     }
     CK(cudaEventRecord(ev[6], ctx->stream));
     CK(cudaEventSynchronize(ev[6]));

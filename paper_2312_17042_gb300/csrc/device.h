@@ -27,6 +27,20 @@ struct Lay {
 inline int lay_nvp(int d) { return d == 2 ? 4 : 6; }
 inline int lay_pds(int d) { return d == 2 ? 8 : 20; }
 
+// Directional operator records for central degree R. Up to degree 3: degree-1 stencils (D
+// unknowns, at most 2D members), member-major entries j * D + k, padded to Lay<D>::PDS. Degrees 4
+// to 6 (2D): degree-2 stencils (5 unknowns, at most 10 members), unknown-major entries k * NDP + j
+// with NDP = 12 member slots per unknown (16-byte rows in FP32 and FP64).
+template <int D, int R>
+struct Dir {
+  static constexpr bool HIGH = R >= 4;
+  static constexpr int KD = HIGH ? 5 : D;       // unknowns of a directional polynomial
+  static constexpr int ND = 2 * KD;             // members at most
+  static constexpr int NDP = HIGH ? 12 : ND;    // member slots of one unknown's row (HIGH)
+  static constexpr int PDS = HIGH ? KD * NDP : Lay<D>::PDS;
+};
+inline int dir_pds(int d, int degree) { return degree >= 4 ? 60 : lay_pds(d); }
+
 // Bits of the per-cell word `cinfo`:
 //   [4f, 4f+4)   members of the directional stencil of local face f (its first slots in the
 //                device stencil list are those members, face after face)
@@ -52,8 +66,8 @@ struct DevTables {
   double O[kMaxNK][kMaxNK];
   double Phi[kMaxNF][kMaxPerm][kMaxNQ][kMaxNK];
   double fw[kMaxNQ];
-  double vq[8][3];
-  double vw[8];
+  double vq[kMaxVQ][3];
+  double vw[kMaxVQ];
 };
 
 // Everything a kernel touches, passed by value. Layouts (i = device cell, T = FP64 or FP32):
@@ -61,7 +75,7 @@ struct DevTables {
 //   U32     float2 [N][NVP]        mixed path: (hi, lo) = (fl32(U), fl32(U - hi))
 //   st      int32  [N][M]          stencil ids, directional members first (face after face)
 //   Pc      T      [N][M][nk]      central pseudo-inverse, member-major
-//   Pd      T      [N][NF][PDS]    directional pseudo-inverses, member-major (j * D + k)
+//   Pd      T      [N][NF][PDS]    directional pseudo-inverses (layout of Dir<D, R>)
 //   Uf      T      [N][NF][NQ][NV] face Gauss-point states
 //   nbr     int32  [N][4]          face neighbours, -1 on a boundary
 //   geo     double [N][NF][4]      outward unit normal (n_x, n_y[, n_z]) and area in slot 3;
@@ -218,6 +232,10 @@ inline long long recon_staged_smem(int d, int degree, int fp32, int block) {
 }
 
 void launch_setup(int dim, int degree, const SetupArgs &a, cudaStream_t s);
+// Central degrees 4 to 6 (2D): constant banks and the variable-per-lane reconstruction
+// (recon_2d_high.cu); launch values other than kLaneSchedule + b give cudaErrorInvalidValue.
+cudaError_t upload_recon_tables_2d_high(int degree, const Tables &t, cudaStream_t s);
+cudaError_t launch_recon_2d_high(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s);
 // Upload the (d, r) smoothness matrix and face-point basis values to the constant banks of the
 // reconstruction kernels.
 cudaError_t upload_recon_tables_2d(int degree, const Tables &t, cudaStream_t s);
@@ -228,10 +246,12 @@ cudaError_t launch_recon_2d(int degree, int fp32, int scheme, const KArgs &a, in
 cudaError_t launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s);
 inline cudaError_t launch_recon(int dim, int degree, int fp32, int scheme, const KArgs &a, int block,
                                 cudaStream_t s) {
+  if (dim == 2 && degree >= 4) return launch_recon_2d_high(degree, fp32, scheme, a, block, s);
   return dim == 2 ? launch_recon_2d(degree, fp32, scheme, a, block, s)
                   : launch_recon_3d(degree, fp32, scheme, a, block, s);
 }
-void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s);
+// nq: Gauss points per face (face_points(dim, degree)).
+void launch_flux(int dim, int nq, int fp32, const KArgs &a, int block, cudaStream_t s);
 void launch_dt(int dim, const KArgs &a, cudaStream_t s);
 void launch_dt_reset(const KArgs &a, cudaStream_t s);
 // CFL step of one mesh only (device cells [first, first + count)).

@@ -220,10 +220,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-template <int D, typename T, int MINB>
+template <int D, typename T, int MINB, int NQ>
 __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel(const KArgs a) {
   using L = Lay<D>;
-  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, FB = NQ * NV;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, FB = NQ * NV;
   constexpr bool F32 = sizeof(T) == 4;
   pdl_wait(a);  // face states of the reconstruction, the state of the previous stage
   const int64_t N = a.N;
@@ -377,10 +377,10 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
 // Face flux of the face-based schedule: one thread per face, HLLC at the face's Gauss points in
 // its owner's orientation (the same operands and order as flux_kernel's owner side), weighted and
 // scaled by the area; record e holds |A| sum_q w_q F_q, padded to NFP values.
-template <int D, typename T>
+template <int D, typename T, int NQ>
 __global__ void __launch_bounds__(256) face_flux_kernel(const KArgs a) {
   using L = Lay<D>;
-  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, FB = NQ * NV;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, FB = NQ * NV;
   constexpr int NFP = (NV + 3) & ~3;
   constexpr bool F32 = sizeof(T) == 4;
   pdl_wait(a);  // face states of the reconstruction
@@ -658,51 +658,47 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 
 }  // namespace
 
-void launch_flux(int dim, int fp32, const KArgs &a, int block, cudaStream_t s) {
+namespace {
+// The flux kernels of dimension D with NQ Gauss points per face.
+template <int D, int NQ>
+void launch_flux_nq(int fp32, const KArgs &a, int block, cudaStream_t s) {
   if (block >= kFaceFlux) {  // face-based: HLLC once per face, then the per-cell gather and update
     const int threads = block - kFaceFlux;
     const unsigned gf = grid_for(a.nfaces, 256), gc = grid_for(a.N, threads);
-    if (dim == 2 && fp32) {
-      launch_stage_kernel(face_flux_kernel<2, float>, gf, 256, 0, s, a);
-      launch_stage_kernel(cell_update_kernel<2, float, 0>, gc, threads, 0, s, a);
-    }
-    if (dim == 3 && fp32) {
-      launch_stage_kernel(face_flux_kernel<3, float>, gf, 256, 0, s, a);
-      launch_stage_kernel(cell_update_kernel<3, float, 0>, gc, threads, 0, s, a);
-    }
-    if (dim == 2 && !fp32) {
-      launch_stage_kernel(face_flux_kernel<2, double>, gf, 256, 0, s, a);
-      launch_stage_kernel(cell_update_kernel<2, double, 0>, gc, threads, 0, s, a);
-    }
-    if (dim == 3 && !fp32) {
-      launch_stage_kernel(face_flux_kernel<3, double>, gf, 256, 0, s, a);
-      launch_stage_kernel(cell_update_kernel<3, double, 0>, gc, threads, 0, s, a);
+    if (fp32) {
+      launch_stage_kernel(face_flux_kernel<D, float, NQ>, gf, 256, 0, s, a);
+      launch_stage_kernel(cell_update_kernel<D, float, 0>, gc, threads, 0, s, a);
+    } else {
+      launch_stage_kernel(face_flux_kernel<D, double, NQ>, gf, 256, 0, s, a);
+      launch_stage_kernel(cell_update_kernel<D, double, 0>, gc, threads, 0, s, a);
     }
     return;
   }
   if (block >= kLaneSchedule) {  // face-per-lane schedule, block - kLaneSchedule threads
-    const int threads = block - kLaneSchedule, cpw = 32 / (dim + 1);
+    const int threads = block - kLaneSchedule, cpw = 32 / (D + 1);
     const int64_t cells_per_block = (int64_t)(threads / 32) * cpw;
     const unsigned grid = (unsigned)((a.N + cells_per_block - 1) / cells_per_block);
-    if (dim == 2 && fp32) launch_stage_kernel(flux_lanes_kernel<2, float>, grid, threads, 0, s, a);
-    if (dim == 2 && !fp32) launch_stage_kernel(flux_lanes_kernel<2, double>, grid, threads, 0, s, a);
-    if (dim == 3 && fp32) launch_stage_kernel(flux_lanes_kernel<3, float>, grid, threads, 0, s, a);
-    if (dim == 3 && !fp32) launch_stage_kernel(flux_lanes_kernel<3, double>, grid, threads, 0, s, a);
+    if (fp32) launch_stage_kernel(flux_lanes_kernel<D, float, NQ>, grid, threads, 0, s, a);
+    else launch_stage_kernel(flux_lanes_kernel<D, double, NQ>, grid, threads, 0, s, a);
     return;
   }
   const bool capped = block < 0;  // register-capped variant (FP32 only)
   if (capped) block = -block;
   const unsigned grid = grid_for(a.N, block);
-  if (dim == 2 && fp32) {
-    if (capped) launch_stage_kernel(flux_kernel<2, float, 8>, grid, block, 0, s, a);
-    else launch_stage_kernel(flux_kernel<2, float, 0>, grid, block, 0, s, a);
+  if (fp32) {
+    if (capped) launch_stage_kernel(flux_kernel<D, float, 8, NQ>, grid, block, 0, s, a);
+    else launch_stage_kernel(flux_kernel<D, float, 0, NQ>, grid, block, 0, s, a);
+  } else {
+    launch_stage_kernel(flux_kernel<D, double, 0, NQ>, grid, block, 0, s, a);
   }
-  if (dim == 3 && fp32) {
-    if (capped) launch_stage_kernel(flux_kernel<3, float, 8>, grid, block, 0, s, a);
-    else launch_stage_kernel(flux_kernel<3, float, 0>, grid, block, 0, s, a);
-  }
-  if (dim == 2 && !fp32) launch_stage_kernel(flux_kernel<2, double, 0>, grid, block, 0, s, a);
-  if (dim == 3 && !fp32) launch_stage_kernel(flux_kernel<3, double, 0>, grid, block, 0, s, a);
+}
+}  // namespace
+
+void launch_flux(int dim, int nq, int fp32, const KArgs &a, int block, cudaStream_t s) {
+  if (dim == 3) launch_flux_nq<3, 4>(fp32, a, block, s);
+  else if (nq == 2) launch_flux_nq<2, 2>(fp32, a, block, s);
+  else if (nq == 3) launch_flux_nq<2, 3>(fp32, a, block, s);
+  else if (nq == 4) launch_flux_nq<2, 4>(fp32, a, block, s);
 }
 
 namespace {

@@ -10,10 +10,10 @@
 namespace cteno {
 namespace {
 
-template <int D, typename T>
+template <int D, typename T, int NQ>
 __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
   using L = Lay<D>;
-  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, FB = NQ * NV;
+  constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, FB = NQ * NV;
   constexpr int CPW = 32 / NF;
   constexpr bool F32 = sizeof(T) == 4;
   pdl_wait(a);

@@ -12,13 +12,14 @@
 namespace cteno {
 
 constexpr int kMaxDim = 3;
-constexpr int kMaxNK = 19;   // K(3,3) - 1 unknown coefficients of a cubic in 3D
-constexpr int kMaxM = 40;    // M = 2K(3,3)
+constexpr int kMaxNK = 27;   // K(6,2) - 1 unknown coefficients of a sextic in 2D (cubic in 3D: 19)
+constexpr int kMaxM = 56;    // M = 2K(6,2)
 constexpr int kMaxNF = 4;    // faces of a tetrahedron
-constexpr int kMaxNQ = 4;    // Gauss points per face
+constexpr int kMaxNQ = 4;    // Gauss points per face (3D; 2D degree 6)
 constexpr int kMaxNV = 5;    // conserved variables in 3D
-constexpr int kMaxDir = 6;   // members of a directional stencil (2d)
+constexpr int kMaxDir = 10;  // members of a directional stencil (2d; 10 for the quadratic ones)
 constexpr int kMaxPerm = 6;  // orderings of a face's vertices
+constexpr int kMaxVQ = 16;   // points of the volume rule (4 x 4 in 2D at degree 6)
 
 // K(r,d) of eq. 6: number of monomials of degree <= r in d variables, constant included.
 inline int coeff_count(int r, int d) {
@@ -29,6 +30,15 @@ inline int coeff_count(int r, int d) {
   }
   return num / den;
 }
+
+// Directional stencils (Sec. 2.3, Fig. 1): degree 1 for central degrees up to 3, degree 2 (2D)
+// for central degrees 4 to 6; at most twice as many members as unknowns.
+inline int dir_degree(int r) { return r >= 4 ? 2 : 1; }
+inline int dir_unknowns(int d, int r) { return coeff_count(dir_degree(r), d) - 1; }
+inline int dir_members(int d, int r) { return 2 * dir_unknowns(d, r); }
+// Gauss points per face: 2D edges n-point Gauss-Legendre with n = max(2, (r+2)/2) (exact to
+// degree r + 1); 3D faces the collapsed 2 x 2 rule.
+inline int face_points(int d, int r) { return d == 3 ? 4 : (r + 2) / 2 > 2 ? (r + 2) / 2 : 2; }
 
 // Universal constants of one (d, r): basis exponents, basis means, smoothness matrix, face
 // Gauss-point basis values and volume/face quadrature rules. Built once on the host (tables.cpp)
@@ -42,10 +52,10 @@ struct Tables {
   // permutation p of its local vertices
   double Phi[kMaxNF][kMaxPerm][kMaxNQ][kMaxNK] = {};
   double fw[kMaxNQ] = {};               // face weights, sum 1
-  // collapsed Gauss-Jacobi rule on the unit reference simplex, exact to degree 3
+  // collapsed Gauss-Jacobi rule on the unit reference simplex, exact to degree max(3, r)
   int nvq = 0;
-  double vq[8][3] = {};                 // reference coordinates
-  double vw[8] = {};                    // weights, sum |V0'| = 1/d!
+  double vq[kMaxVQ][3] = {};            // reference coordinates
+  double vw[kMaxVQ] = {};               // weights, sum |V0'| = 1/d!
   int perm_list[kMaxPerm][3] = {};      // permutations of the face's vertex slots
 };
 
@@ -66,7 +76,7 @@ struct Mesh {
   std::vector<int32_t> v2c;
   // stencils, original numbering
   std::vector<int32_t> central;  // [ncells][M], nearest first
-  std::vector<int8_t> dirpos;    // [ncells][nf][2d], positions in `central`, -1 padded
+  std::vector<int8_t> dirpos;    // [ncells][nf][dir_members], positions in `central`, -1 padded
   std::vector<int32_t> order;    // Morton order: new index -> original id
   std::vector<int32_t> rank;     // original id -> new index
 };

@@ -174,7 +174,7 @@ struct Cand {
 }  // namespace
 
 int build_stencils(Mesh *m, int degree, std::string *err) {
-  const int d = m->dim, nvc = d + 1, nf = d + 1, nd = 2 * d;
+  const int d = m->dim, nvc = d + 1, nf = d + 1, nd = dir_members(d, degree);
   const int M = 2 * coeff_count(degree, d);
   const int64_t n = m->ncells;
   m->central.assign(n * M, -1);

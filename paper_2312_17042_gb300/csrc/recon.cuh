@@ -36,10 +36,11 @@ struct Shape {
 // phi_k at the two Gauss points of each local edge taken in local vertex order (the other edge
 // orientation visits the same two symmetric points in the opposite order). Indexed with
 // compile-time offsets only, so they become instruction operands.
-__constant__ double c_O_r2d[kMaxNK * kMaxNK], c_O_r3d[kMaxNK * kMaxNK];
-__constant__ float c_O_r2f[kMaxNK * kMaxNK], c_O_r3f[kMaxNK * kMaxNK];
-__constant__ double c_Phi2_r2d[3 * 2 * kMaxNK], c_Phi2_r3d[3 * 2 * kMaxNK];
-__constant__ float c_Phi2_r2f[3 * 2 * kMaxNK], c_Phi2_r3f[3 * 2 * kMaxNK];
+constexpr int kLowNK = 19;  // unknowns of degree <= 3 (a cubic in 3D)
+__constant__ double c_O_r2d[kLowNK * kLowNK], c_O_r3d[kLowNK * kLowNK];
+__constant__ float c_O_r2f[kLowNK * kLowNK], c_O_r3f[kLowNK * kLowNK];
+__constant__ double c_Phi2_r2d[3 * 2 * kLowNK], c_Phi2_r3d[3 * 2 * kLowNK];
+__constant__ float c_Phi2_r2f[3 * 2 * kLowNK], c_Phi2_r3f[3 * 2 * kLowNK];
 
 template <typename T, int R>
 __device__ __forceinline__ T cO(int idx) {
@@ -60,8 +61,9 @@ __device__ __forceinline__ T cPhi2(int idx) {
 
 // Host side: copy O and the 2D edge values of degree r into this module's constant banks.
 inline cudaError_t upload_recon_tables(int dim, int degree, const Tables &t, cudaStream_t s) {
-  double Od[kMaxNK * kMaxNK] = {}, Pd2[3 * 2 * kMaxNK] = {};
-  float Of[kMaxNK * kMaxNK] = {}, Pf2[3 * 2 * kMaxNK] = {};
+  double Od[kLowNK * kLowNK] = {}, Pd2[3 * 2 * kLowNK] = {};
+  float Of[kLowNK * kLowNK] = {}, Pf2[3 * 2 * kLowNK] = {};
+  if (t.nk > kLowNK) return cudaErrorInvalidValue;
   // O is symmetric: the kernels use the upper triangle only, with the off-diagonal entries doubled
   // (exact), a^T O a = sum_k a_k (O_kk a_k + sum_{l>k} 2 O_kl a_l)
   for (int k = 0; k < t.nk; ++k)

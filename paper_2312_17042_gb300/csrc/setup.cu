@@ -107,7 +107,8 @@ __device__ void pinv_column(double (*W)[LD], int rows, int cols, const double *d
 
 template <int D, int R>
 __global__ void __launch_bounds__(128) setup_kernel(const SetupArgs a) {
-  constexpr int NVC = D + 1, NF = D + 1, ND = 2 * D;
+  using DR = Dir<D, R>;
+  constexpr int NVC = D + 1, NF = D + 1, ND = DR::ND, KD = DR::KD;
   constexpr int NK = (D == 2 ? (R + 1) * (R + 2) / 2 : (R + 1) * (R + 2) * (R + 3) / 6) - 1;
   constexpr int M = 2 * (NK + 1);
   constexpr double FACT = (D == 2) ? 2.0 : 6.0;
@@ -220,32 +221,33 @@ __global__ void __launch_bounds__(128) setup_kernel(const SetupArgs a) {
     }
   }
 
-  // directional stencils first (they read the linear columns of A before the QR overwrites it)
+  // directional stencils first (they read the first KD columns of A, those of the graded basis
+  // functions of degree <= 1 or 2, before the QR overwrites them)
   const uint32_t info = a.cinfo[i];
   uint32_t adm = 0;
   int off = 0;
   for (int f = 0; f < NF; ++f) {
     const int nm = (info >> (4 * f)) & 15u;
-    double pd[D][ND];
-    for (int k = 0; k < D; ++k)
+    double pd[KD][ND];
+    for (int k = 0; k < KD; ++k)
       for (int j = 0; j < ND; ++j) pd[k][j] = 0.0;
-    if (nm >= D) {
-      double Wd[ND][D], dg[D], vt[D], bt[D];
+    if (nm >= KD) {
+      double Wd[ND][KD], dg[KD], vt[KD], bt[KD];
       for (int j = 0; j < nm; ++j)
-        for (int k = 0; k < D; ++k) Wd[j][k] = W[off + j][k];
-      if (householder<D>(Wd, nm, D, dg, vt, bt)) {
+        for (int k = 0; k < KD; ++k) Wd[j][k] = W[off + j][k];
+      if (householder<KD>(Wd, nm, KD, dg, vt, bt)) {
         adm |= 1u << f;
         for (int j = 0; j < nm; ++j) {
-          double col[D];
-          pinv_column<D, ND>(Wd, nm, D, dg, vt, bt, j, col);
-          for (int k = 0; k < D; ++k) pd[k][j] = col[k] * Vp[off + j];
+          double col[KD];
+          pinv_column<KD, ND>(Wd, nm, KD, dg, vt, bt, j, col);
+          for (int k = 0; k < KD; ++k) pd[k][j] = col[k] * Vp[off + j];
         }
       }
     }
-    constexpr int PDS = Lay<D>::PDS;
-    for (int e = 0; e < PDS; ++e) {  // member-major: entry j * D + k, zero padding
-      const int j = e / D, k = e % D;
-      const double val = (j < ND) ? pd[k][j] : 0.0;
+    constexpr int PDS = DR::PDS;
+    for (int e = 0; e < PDS; ++e) {  // see Dir: member-major (degree <= 3) or unknown-major rows
+      const int j = DR::HIGH ? e % DR::NDP : e / KD, k = DR::HIGH ? e / DR::NDP : e % KD;
+      const double val = (j < ND && k < KD) ? pd[k][j] : 0.0;
       const int64_t idx = (i * NF + f) * PDS + e;
       if (a.store_fp32)
         ((float *)a.Pd)[idx] = (float)val;
@@ -281,6 +283,9 @@ void launch_setup(int dim, int degree, const SetupArgs &a, cudaStream_t s) {
   if (dim == 2 && degree == 3) setup_kernel<2, 3><<<grid, block, 0, s>>>(a);
   if (dim == 3 && degree == 2) setup_kernel<3, 2><<<grid, block, 0, s>>>(a);
   if (dim == 3 && degree == 3) setup_kernel<3, 3><<<grid, block, 0, s>>>(a);
+  if (dim == 2 && degree == 4) setup_kernel<2, 4><<<grid, block, 0, s>>>(a);
+  if (dim == 2 && degree == 5) setup_kernel<2, 5><<<grid, block, 0, s>>>(a);
+  if (dim == 2 && degree == 6) setup_kernel<2, 6><<<grid, block, 0, s>>>(a);
 }
 
 }  // namespace cteno

@@ -49,6 +49,69 @@ void gauss_jacobi2(int a, double x[2], double w[2]) {
   w[0] = mu[0] - w[1];
 }
 
+// Jacobi polynomial P_n^(al,be)(x) on [-1,1] by its three-term recurrence.
+double jacobi(int n, double al, double be, double x) {
+  if (n == 0) return 1.0;
+  double p0 = 1.0, p1 = (al + 1.0) + 0.5 * (al + be + 2.0) * (x - 1.0);
+  for (int k = 2; k <= n; ++k) {
+    const double s = 2.0 * k + al + be;
+    const double an = 2.0 * k * (k + al + be) * (s - 2.0);
+    const double bn = (s - 1.0) * (s * (s - 2.0) * x + al * al - be * be);
+    const double cn = 2.0 * (k + al - 1.0) * (k + be - 1.0) * s;
+    const double p2 = (bn * p1 - cn * p0) / an;
+    p0 = p1;
+    p1 = p2;
+  }
+  return p1;
+}
+
+// n-point Gauss rule on [0,1] for the weight (1-u)^a (exact for polynomials of degree 2n - 1
+// times the weight). Nodes: the roots of P_n^(a,0) at x = 2u - 1, bracketed by sign changes on a
+// fine grid and bisected to the last bit; weights 1 / ((1 - x^2) P_n'(x)^2), with
+// P_n' = (n + a + 1)/2 P_{n-1}^(a+1,1) (the Gauss-Jacobi weight formula for beta = 0, mapped to
+// [0,1]). For a = 0 (Gauss-Legendre) the rule is made exactly symmetric, x_{n-1-i} = -x_i.
+void gauss_jacobi(int n, int a, double *u, double *w) {
+  const int S = 4093;  // odd: no grid point falls on x = 0, a root of the odd Legendre polynomials
+  double x[8];
+  int found = 0;
+  double xl = -1.0, pl = jacobi(n, a, 0.0, xl);
+  for (int s = 1; s <= S && found < n; ++s) {
+    const double xr = -1.0 + 2.0 * s / S, pr = jacobi(n, a, 0.0, xr);
+    if ((pl < 0.0) != (pr < 0.0)) {
+      double lo = xl, hi = xr, plo = pl;
+      for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        const double pm = jacobi(n, a, 0.0, mid);
+        if (pm == 0.0) {
+          lo = hi = mid;
+          break;
+        }
+        if ((pm < 0.0) == (plo < 0.0)) {
+          lo = mid;
+          plo = pm;
+        } else {
+          hi = mid;
+        }
+      }
+      x[found++] = 0.5 * (lo + hi);
+    }
+    xl = xr;
+    pl = pr;
+  }
+  if (a == 0) {
+    for (int i = 0; i < n / 2; ++i) x[n - 1 - i] = -x[i];
+    if (n % 2) x[n / 2] = 0.0;
+  }
+  for (int i = 0; i < n; ++i) {
+    const double dp = 0.5 * (n + a + 1.0) * jacobi(n - 1, a + 1.0, 1.0, x[i]);
+    u[i] = 0.5 * (1.0 + x[i]);
+    w[i] = 1.0 / ((1.0 - x[i] * x[i]) * dp * dp);
+  }
+  if (a == 0)
+    for (int i = 0; i < n / 2; ++i) w[n - 1 - i] = w[i];
+}
+
 double eval_monomial(const int *e, const double *xi, int d) {
   double v = 1.0;
   for (int j = 0; j < d; ++j)
@@ -64,7 +127,7 @@ void build_tables(int dim, int degree, Tables *t) {
   t->dim = d;
   t->degree = r;
   t->nf = d + 1;
-  t->nq = (d == 2) ? 2 : 4;
+  t->nq = face_points(d, r);
   // basis exponents, graded; within a degree ordered by the zeta then eta power
   int k = 0;
   for (int tdeg = 1; tdeg <= r; ++tdeg)
@@ -100,8 +163,23 @@ void build_tables(int dim, int degree, Tables *t) {
       }
       t->O[i][j] = s;
     }
-  // volume rule: collapsed coordinates, Gauss-Jacobi in each direction
-  {
+  // volume rule: collapsed coordinates, Gauss-Jacobi in each direction (2 points up to degree 3,
+  // (r + 2) / 2 points from degree 4: exact to degree 2n - 1 >= r)
+  if (d == 2 && r >= 4) {
+    const int n = (r + 2) / 2;
+    double xa[8], wa[8], xb[8], wb[8];
+    gauss_jacobi(n, 1, xa, wa);
+    gauss_jacobi(n, 0, xb, wb);
+    int q = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        t->vq[q][0] = xa[i];
+        t->vq[q][1] = xb[j] * (1.0 - xa[i]);
+        t->vw[q] = wa[i] * wb[j];
+        ++q;
+      }
+    t->nvq = q;
+  } else {
     double xa[2], wa[2], xb[2], wb[2], xc[2], wc[2];
     if (d == 2) {
       gauss_jacobi2(1, xa, wa);
@@ -133,9 +211,18 @@ void build_tables(int dim, int degree, Tables *t) {
     }
   }
   // face rule in barycentric coordinates of the face's vertices, sorted by global id:
-  // 2D: 2-point Gauss-Legendre along the edge; 3D: collapsed 2x2 (Gauss-Jacobi (1-u) x Legendre)
+  // 2D: n-point Gauss-Legendre along the edge (symmetric: the reversed edge visits the same
+  // points in the opposite order); 3D: collapsed 2x2 (Gauss-Jacobi (1-u) x Legendre)
   double bary[kMaxNQ][3] = {};
-  {
+  if (d == 2 && t->nq > 2) {
+    double xl[8], wl[8];
+    gauss_jacobi(t->nq, 0, xl, wl);
+    for (int q = 0; q < t->nq; ++q) {
+      bary[q][0] = 1.0 - xl[q];
+      bary[q][1] = xl[q];
+      t->fw[q] = wl[q];
+    }
+  } else {
     double xl[2], wl[2], xj[2], wj[2];
     gauss_jacobi2(0, xl, wl);
     if (d == 2) {

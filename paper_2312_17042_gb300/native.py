@@ -222,7 +222,7 @@ def cteno_get_stencil(ctx, mesh_id: int, cell: int, with_admissibility: bool = T
     M, nf = int(info[2]), int(info[5])
     d = nf - 1
     central = np.empty(M, np.int32)
-    dirm = np.empty((nf, 2 * d), np.int32)
+    dirm = np.empty((nf, int(info[8])), np.int32)
     dok = np.empty(nf, np.int32) if with_admissibility else None
     _check(ctx, load_library().cteno_get_stencil(ctx, mesh_id, int(cell), _ptr(central), _ptr(dirm),
                                                  _ptr(dok) if dok is not None else None))
@@ -230,7 +230,7 @@ def cteno_get_stencil(ctx, mesh_id: int, cell: int, with_admissibility: bool = T
 
 
 def cteno_info(ctx, mesh_id: int = -1) -> np.ndarray:
-    out = np.zeros(8, np.int64)
+    out = np.zeros(9, np.int64)
     _check(ctx, load_library().cteno_info(ctx, mesh_id, _ptr(out)))
     return out
 

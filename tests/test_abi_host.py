@@ -40,9 +40,10 @@ def test_parameter_validation_without_gpu():
     native = _lib()
     p = native.cteno_default_params()
     assert (p.dim, p.degree, p.C_T, p.lambda1p, p.eps, p.ctenoz_form) == (2, 2, 1e-6, 1e15, 1e-24, 0)
-    p.degree = 5
-    with pytest.raises(native.CtenoError):
-        native.cteno_create(p)
+    for dim, degree in ((2, 7), (2, 1), (3, 4)):   # 2D: degrees 2 to 6; 3D: 2 and 3
+        p.dim, p.degree = dim, degree
+        with pytest.raises(native.CtenoError):
+            native.cteno_create(p)
     p = native.cteno_default_params()
     ctx = native.cteno_create(p)
     # rk_stage before lsq_build is an ordering error, not a crash
@@ -68,7 +69,10 @@ def test_parameter_validation_without_gpu():
     (W.tri_mesh(14, 9, periodic=False, seed=2), 3),
     (W.tet_mesh(6, periodic=True, seed=3), 2),
     (W.tet_mesh(5, periodic=False, seed=4), 3),
-], ids=["tri-per-r2", "tri-r3", "tet-per-r2", "tet-r3"])
+    (W.tri_mesh(16, 16, periodic=True, seed=5), 4),
+    (W.tri_mesh(18, 14, periodic=False, seed=6), 5),
+    (W.tri_mesh(20, 20, periodic=True, seed=7), 6),
+], ids=["tri-per-r2", "tri-r3", "tet-per-r2", "tet-r3", "tri-per-r4", "tri-r5", "tri-per-r6"])
 def test_host_stencils_match_oracle_exactly(mesh, degree):
     """Central stencils (ids, nearest-first order) and directional member positions are integer
     results of the same readings, computed independently: they must agree exactly."""
