@@ -27,9 +27,9 @@ def _load():
     lib = C.CDLL(LIB)
     V = C.c_void_p
     lib.orc_create.restype = V
-    lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
-                               C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _dp, C.c_int, _ip, _dp,
-                               C.POINTER(C.c_int)]
+    lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                               C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _dp, C.c_int,
+                               _ip, _dp, C.POINTER(C.c_int)]
     lib.orc_destroy.argtypes = [V]
     lib.orc_setup_all.argtypes = [V]
     lib.orc_setup_cells.argtypes = [V, C.c_int, _ip]
@@ -71,6 +71,7 @@ def _load():
     lib.orc_simplex_monomial.restype = C.c_double
     lib.orc_simplex_monomial.argtypes = [V, _dp, C.c_int]
     lib.orc_num_threads.restype = C.c_int
+    lib.orc_eigen.argtypes = [V, _dp, _dp, _dp, _dp]
     _lib = lib
     return lib
 
@@ -79,8 +80,8 @@ def num_threads() -> int:
     return int(_load().orc_num_threads())
 
 
-DEFAULTS = dict(degree=2, scheme=0, lam_gamma=1, ctenoz_form=0, C_T=1e-6, lambda1p=1e15, eps=1e-24,
-                gamma=1.4, cfl=0.5, guard=1)
+DEFAULTS = dict(degree=2, scheme=0, lam_gamma=1, ctenoz_form=0, characteristic=0, C_T=1e-6, lambda1p=1e15,
+                eps=1e-24, gamma=1.4, cfl=0.5, guard=1)
 
 
 def select(SI, scheme=0, ctenoz_form=0, lam_gamma=1, C_T=1e-6, lambda1p=1e15, eps=1e-24):
@@ -107,7 +108,8 @@ class Oracle:
         period = np.ascontiguousarray(mesh.period, dtype=np.float64)
         err = C.c_int(0)
         self.h = self.lib.orc_create(self.dim, p["degree"], p["scheme"], p["lam_gamma"], p["ctenoz_form"],
-                                     p["C_T"], p["lambda1p"], p["eps"], p["gamma"], p["cfl"], p["guard"],
+                                     p["characteristic"], p["C_T"], p["lambda1p"], p["eps"], p["gamma"], p["cfl"],
+                                     p["guard"],
                                      mesh.nverts, xyz, mesh.ncells, cells, period, C.byref(err))
         if err.value:
             raise RuntimeError(f"oracle mesh set-up failed ({err.value})")
@@ -116,6 +118,8 @@ class Oracle:
         self.nv, self.nf, self.nq, self.nk, self.M = (int(x) for x in info[:5])
         self.dmax = int(info[7])   # members kept per directional stencil
         self.ncells = mesh.ncells
+        # selections per cell: one per variable, or per face and characteristic field
+        self.sel_shape = (self.nf, self.nv) if p["characteristic"] else (self.nv,)
         if setup:
             rc = self.lib.orc_setup_all(self.h)
             if rc:
@@ -229,26 +233,39 @@ class Oracle:
         return out
 
     def flags(self):
-        out = np.empty((self.ncells, self.nv), np.uint8)
+        """Selection flags of the last reconstruction: [ncells, nv], or [ncells, nf, nv] (face,
+        characteristic field) for the characteristic reconstruction."""
+        out = np.empty((self.ncells,) + self.sel_shape, np.uint8)
         self.lib.orc_get_flags(self.h, out)
         return out
 
     def smoothness_indicators(self):
-        out = np.empty((self.ncells, self.nv, 1 + self.nf))
+        out = np.empty((self.ncells,) + self.sel_shape + (1 + self.nf,))
         self.lib.orc_get_si(self.h, out)
         return out
 
     def chi(self):
         """chi_s of eq. 22 of the last reconstruction: [ncells, nv, 1 + nf] (central, then the
-        directional stencil of each local face; 0 where not admissible)."""
-        out = np.empty((self.ncells, self.nv, 1 + self.nf))
+        directional stencil of each local face; 0 where not admissible); [ncells, nf, nv, 1 + nf]
+        for the characteristic reconstruction."""
+        out = np.empty((self.ncells,) + self.sel_shape + (1 + self.nf,))
         self.lib.orc_get_chi(self.h, out)
         return out
 
     def coefficients(self):
-        out = np.empty((self.ncells, self.nv, self.nk))
+        out = np.empty((self.ncells,) + self.sel_shape + (self.nk,))
         self.lib.orc_get_coeffs(self.h, out)
         return out
+
+    def eigen(self, u, n):
+        """(R, L): right and left eigenvectors of the Euler flux Jacobian in unit direction n at
+        the conserved state u, as the characteristic reconstruction uses them."""
+        u = np.ascontiguousarray(u, np.float64)
+        n = np.ascontiguousarray(n, np.float64)
+        R = np.empty((self.nv, self.nv))
+        L = np.empty((self.nv, self.nv))
+        self.lib.orc_eigen(self.h, u, n, R, L)
+        return R, L
 
     def refmap(self, i: int):
         X = np.empty((self.dim + 1, self.dim))

@@ -49,6 +49,7 @@ typedef struct {
   int guard;               /* Reading: positivity fall-back to the cell mean */
   int lam_gamma;           /* Reading: 1 = gamma_s carries lambda_s (eq. 18), 0 = as printed */
   int ctenoz_form;         /* Reading: 0 = CTENOZ measure as printed, 1 = WENO-Z form */
+  int characteristic;      /* 1: reconstruct characteristic variables, per face (Sec. 2.2, 3.2) */
   double C_T, lambda1p, eps, gamma, cfl;
 } orc_params;
 
@@ -97,7 +98,8 @@ typedef struct {
   double *qlam, *qw;
   /* solution */
   double *U, *Un, *Rres, *face; /* face: [ncells][nf][nq][nv] */
-  uint8_t *flags;               /* [ncells][nv]: bit 0 central selected, bit 1+f directional f */
+  int nsel;                     /* selections per cell: nv, or nf * nv (characteristic) */
+  uint8_t *flags;               /* [ncells][nsel]: bit 0 central selected, bit 1+f directional f */
   double *SI;                   /* [ncells][nv][1+nf] smoothness indicators (debug) */
   double *chi;                  /* [ncells][nv][1+nf] chi_s of eq. 22, 0 where inadmissible (debug) */
   double *coef;                 /* [ncells][nv][nk] final polynomial coefficients (debug) */
@@ -837,6 +839,165 @@ static unsigned select_stencils(const orc_params *p, int st, const double *SI, d
   return bits;
 }
 
+/* Right (columns) and left (rows) eigenvectors of the Euler flux Jacobian dF(U).n/dU at the
+ * conserved state u, for the unit direction n: the characteristic variables W = L U in which Sec.
+ * 2.2 and Sec. 3.2 reconstruct. Fields in the order of the eigenvalues u_n - c, u_n (entropy),
+ * u_n (shear: one per tangent t_j of an orthonormal frame n, t_1 .. t_{d-1}), u_n + c; with
+ * H = (E + p)/rho, q^2 = |u|^2, b1 = (gamma - 1)/c^2, b2 = b1 q^2/2:
+ *   r_0 = (1, u - c n, H - c u_n)           l_0 = (b2 + u_n/c, -b1 u - n/c, b1) / 2
+ *   r_1 = (1, u, q^2/2)                     l_1 = (1 - b2, b1 u, -b1)
+ *   r_1+j = (0, t_j, u.t_j)                 l_1+j = (-u.t_j, t_j, 0)
+ *   r_d+1 = (1, u + c n, H + c u_n)         l_d+1 = (b2 - u_n/c, -b1 u + n/c, b1) / 2
+ * Reading: the tangents are t = (-n_y, n_x) in 2D; in 3D t_1 is the component of the axis along
+ * which |n| is smallest orthogonal to n, normalised, and t_2 = n x t_1. */
+static void euler_eigen(const orc *o, const double *u, const double *n, double R[MAXNV][MAXNV],
+                        double L[MAXNV][MAXNV]) {
+  const int d = o->p.dim, nv = o->nv;
+  const double g = o->p.gamma, rho = u[0];
+  double vel[3] = {0, 0, 0}, q2 = 0.0, un = 0.0;
+  for (int j = 0; j < d; ++j) {
+    vel[j] = u[1 + j] / rho;
+    q2 += vel[j] * vel[j];
+    un += vel[j] * n[j];
+  }
+  const double p = pressure(o, u), c = sqrt(g * p / rho), H = (u[d + 1] + p) / rho;
+  const double b1 = (g - 1.0) / (c * c), b2 = 0.5 * b1 * q2;
+  double t[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  if (d == 2) {
+    t[0][0] = -n[1];
+    t[0][1] = n[0];
+  } else {
+    int a = 0;
+    for (int j = 1; j < 3; ++j)
+      if (fabs(n[j]) < fabs(n[a])) a = j;
+    double len = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      t[0][j] = (j == a ? 1.0 : 0.0) - n[a] * n[j];
+      len += t[0][j] * t[0][j];
+    }
+    len = sqrt(len);
+    for (int j = 0; j < 3; ++j) t[0][j] /= len;
+    t[1][0] = n[1] * t[0][2] - n[2] * t[0][1];
+    t[1][1] = n[2] * t[0][0] - n[0] * t[0][2];
+    t[1][2] = n[0] * t[0][1] - n[1] * t[0][0];
+  }
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b < nv; ++b) R[a][b] = L[a][b] = 0.0;
+  R[0][0] = 1.0;
+  R[0][1] = 1.0;
+  R[0][d + 1] = 1.0;
+  for (int j = 0; j < d; ++j) {
+    R[1 + j][0] = vel[j] - c * n[j];
+    R[1 + j][1] = vel[j];
+    R[1 + j][d + 1] = vel[j] + c * n[j];
+  }
+  R[d + 1][0] = H - c * un;
+  R[d + 1][1] = 0.5 * q2;
+  R[d + 1][d + 1] = H + c * un;
+  L[0][0] = 0.5 * (b2 + un / c);
+  L[1][0] = 1.0 - b2;
+  L[d + 1][0] = 0.5 * (b2 - un / c);
+  for (int j = 0; j < d; ++j) {
+    L[0][1 + j] = 0.5 * (-b1 * vel[j] - n[j] / c);
+    L[1][1 + j] = b1 * vel[j];
+    L[d + 1][1 + j] = 0.5 * (-b1 * vel[j] + n[j] / c);
+  }
+  L[0][d + 1] = 0.5 * b1;
+  L[1][d + 1] = -b1;
+  L[d + 1][d + 1] = 0.5 * b1;
+  for (int m = 0; m < d - 1; ++m) { /* shear fields */
+    double ut = 0.0;
+    for (int j = 0; j < d; ++j) ut += vel[j] * t[m][j];
+    for (int j = 0; j < d; ++j) {
+      R[1 + j][2 + m] = t[m][j];
+      L[2 + m][1 + j] = t[m][j];
+    }
+    R[d + 1][2 + m] = ut;
+    L[2 + m][0] = -ut;
+  }
+}
+
+/* p_1, smoothness indicators, scale separation, cut-off and final polynomial (Sec. 2.3-2.6, eqs.
+ * 15-23, Alg. 1 / 2, CWENO eq. 14) of one cell for one variable (or characteristic field) from its
+ * central least-squares coefficients aopt and directional ones ad (admissible stencils adm[0..na));
+ * debug records at selection index sel. Returns the flags byte; af receives the final
+ * coefficients. */
+static uint8_t weigh(orc *o, int i, int sel, int na, const int *adm, const double *aopt,
+                     double ad[][MAXKD], double *af) {
+  const int nf = o->nf, nk = o->nk, st = 1 + na;
+  const double lam1 = 1.0 - 1.0 / o->p.lambda1p;
+  const double lams = (st > 1) ? (1.0 - lam1) / (st - 1) : 0.0; /* eq. 18 */
+  /* p_1 = (p_opt - sum_{s>=2} lambda_s p_s) / lambda_1  (eq. 17); the directional
+   * polynomials only have the first dk coefficients, so only those receive their terms; TENO
+   * keeps p_1 = p_opt */
+  double a1[MAXK];
+  if (st > 1 && o->p.scheme != 3) { /* TENO keeps the central polynomial itself (Sec. 2.4) */
+    for (int k = 0; k < nk; ++k) {
+      double s = aopt[k];
+      if (k < o->dk)
+        for (int t = 0; t < na; ++t) s -= lams * ad[adm[t]][k];
+      a1[k] = s / lam1;
+    }
+  } else {
+    for (int k = 0; k < nk; ++k) a1[k] = aopt[k];
+  }
+  /* smoothness indicators (eq. 15) of p_1 and of the directional polynomials */
+  double SI[1 + MAXNF];
+  SI[0] = smoothness(o, a1, nk, o->p.degree);
+  for (int s = 0; s < na; ++s) SI[1 + s] = smoothness(o, ad[adm[s]], o->dk, o->ddeg);
+  double *si_out = o->SI + ((size_t)i * o->nsel + sel) * (1 + nf);
+  for (int s = 0; s <= nf; ++s) si_out[s] = 0.0;
+  si_out[0] = SI[0];
+  for (int s = 0; s < na; ++s) si_out[1 + adm[s]] = SI[1 + s];
+  /* scale separation and cut-off (eqs. 19-23, Alg. 1 / Alg. 2) */
+  double chi[1 + MAXNF];
+  const unsigned dbits = select_stencils(&o->p, st, SI, chi);
+  double *chi_out = o->chi + ((size_t)i * o->nsel + sel) * (1 + nf);
+  for (int s = 0; s <= nf; ++s) chi_out[s] = 0.0;
+  chi_out[0] = chi[0];
+  for (int s = 0; s < na; ++s) chi_out[1 + adm[s]] = chi[1 + s];
+  int delta[1 + MAXNF] = {0, 0, 0, 0, 0}, ndel = 0;
+  for (int s = 0; s < st; ++s) {
+    delta[s] = (dbits >> s) & 1u;
+    if (s > 0) ndel += delta[s];
+  }
+  /* final polynomial: CWENO sum_s w_s p_s (Sec. 2.3); otherwise p_1 if delta_1, else
+   * sum_{s>=2} delta_s p_s / sum delta_s (Alg. 1 / 2) */
+  uint8_t fl = 0;
+  if (o->p.scheme == 2) {
+    for (int k = 0; k < nk; ++k) af[k] = chi[0] * a1[k];
+    for (int s = 1; s < st; ++s)
+      for (int k = 0; k < o->dk; ++k) af[k] += chi[s] * ad[adm[s - 1]][k];
+    fl = (uint8_t)(o->stmask[i] & 0xFF);
+  } else if (delta[0]) {
+    for (int k = 0; k < nk; ++k) af[k] = a1[k];
+    fl = 1;
+  } else {
+    for (int k = 0; k < nk; ++k) af[k] = 0.0;
+    for (int s = 1; s < st; ++s)
+      if (delta[s]) {
+        for (int k = 0; k < o->dk; ++k) af[k] += ad[adm[s - 1]][k] / (double)ndel;
+        fl |= (uint8_t)(1 << (1 + adm[s - 1]));
+      }
+  }
+  o->flags[(size_t)i * o->nsel + sel] = fl;
+  for (int k = 0; k < nk; ++k) o->coef[((size_t)i * o->nsel + sel) * nk + k] = af[k];
+  return fl;
+}
+
+/* Value of the polynomial mean + sum_k a_k phi_k at Gauss point q of face f of cell i (eqs. 7, 2). */
+static double face_value(const orc *o, int i, int f, int q, double mean, const double *af) {
+  const int d = o->p.dim;
+  const double *X0 = o->X + (size_t)i * (d + 1) * d, *Ji = o->Jinv + i * d * d;
+  const double *x = o->fq + ((size_t)(i * o->nf + f) * o->nq + q) * d;
+  double xi[3] = {0, 0, 0};
+  for (int r = 0; r < d; ++r)
+    for (int j = 0; j < d; ++j) xi[r] += Ji[r * d + j] * (x[j] - X0[j]);
+  double val = mean;
+  for (int k = 0; k < o->nk; ++k) val += af[k] * (monomial(o->ex[k], xi, d) - o->psibar[k]);
+  return val;
+}
+
 static void recon_cell(orc *o, int i, const double *U) {
   const int d = o->p.dim, nv = o->nv, nf = o->nf, nq = o->nq, nk = o->nk, n = o->ncells;
   orc_cell *c = o->cell[i];
@@ -844,93 +1005,65 @@ static void recon_cell(orc *o, int i, const double *U) {
   int adm[MAXNF], na = 0;
   for (int f = 0; f < nf; ++f)
     if (c->dok[f]) adm[na++] = f;
-  const int st = 1 + na;
-  /* linear coefficients (eq. 18) */
-  const double lam1 = 1.0 - 1.0 / o->p.lambda1p;
-  const double lams = (st > 1) ? (1.0 - lam1) / (st - 1) : 0.0;
   int mask = 1;
   for (int s = 0; s < na; ++s) mask |= 1 << (1 + adm[s]);
   o->stmask[i] = mask;
-  int guard_hit = 0;
-  double fout[MAXNF][MAXNQ][MAXNV];
+  /* least-squares coefficients of every conserved variable (eqs. 10-12) */
+  double U0[MAXNV], aopt[MAXNV][MAXK], ad[MAXNV][MAXNF][MAXKD];
   for (int v = 0; v < nv; ++v) {
-    const double U0 = U[v * n + i];
-    double b[MAXM], aopt[MAXK], ad[MAXNF][MAXKD];
-    for (int k = 0; k < c->nst; ++k) b[k] = c->Vp[k] * (U[v * n + c->ids[k]] - U0); /* eq. 10 */
-    lsq_solve(c->nst, nk, c->V, nk, c->beta, c->R, nk, b, aopt);   /* p_opt */
+    U0[v] = U[v * n + i];
+    double b[MAXM];
+    for (int k = 0; k < c->nst; ++k) b[k] = c->Vp[k] * (U[v * n + c->ids[k]] - U0[v]); /* eq. 10 */
+    lsq_solve(c->nst, nk, c->V, nk, c->beta, c->R, nk, b, aopt[v]);   /* p_opt */
     for (int s = 0; s < na; ++s) {
       int f = adm[s];
       double bd[MAXDIR];
       for (int j = 0; j < c->ndir[f]; ++j) bd[j] = b[c->dmem[f][j]];
-      lsq_solve(c->ndir[f], o->dk, &c->dV[f][0][0], MAXKD, c->dbeta[f], &c->dR[f][0][0], MAXKD, bd, ad[f]);
+      lsq_solve(c->ndir[f], o->dk, &c->dV[f][0][0], MAXKD, c->dbeta[f], &c->dR[f][0][0], MAXKD, bd, ad[v][f]);
     }
-    /* p_1 = (p_opt - sum_{s>=2} lambda_s p_s) / lambda_1  (eq. 17); the directional
-     * polynomials only have the first dk coefficients, so only those receive their terms; TENO
-     * keeps p_1 = p_opt */
-    double a1[MAXK];
-    if (st > 1 && o->p.scheme != 3) { /* TENO keeps the central polynomial itself (Sec. 2.4) */
-      for (int k = 0; k < nk; ++k) {
-        double s = aopt[k];
-        if (k < o->dk)
-          for (int t = 0; t < na; ++t) s -= lams * ad[adm[t]][k];
-        a1[k] = s / lam1;
+  }
+  double fout[MAXNF][MAXNQ][MAXNV];
+  if (!o->p.characteristic) { /* conserved variables, each selected independently (Alg. 1 / 2) */
+    for (int v = 0; v < nv; ++v) {
+      double af[MAXK];
+      weigh(o, i, v, na, adm, aopt[v], ad[v], af);
+      for (int f = 0; f < nf; ++f)
+        for (int q = 0; q < nq; ++q) fout[f][q][v] = face_value(o, i, f, q, U0[v], af);
+    }
+  } else {
+    /* Reading of the characteristic reconstruction (Sec. 2.2, 3.2): for each face f, the
+     * eigenvectors at the cell's mean state in the face's outward normal direction; the
+     * reconstruction runs on W = L U of every stencil member, i.e. on L applied to the
+     * least-squares coefficients (the least squares are linear in the data), each field selected
+     * independently; the face's Gauss-point values are transformed back, U = R W. */
+    for (int f = 0; f < nf; ++f) {
+      double R[MAXNV][MAXNV], L[MAXNV][MAXNV];
+      euler_eigen(o, U0, o->nrm + (size_t)(i * nf + f) * d, R, L);
+      double W[MAXNQ][MAXNV];
+      for (int w = 0; w < nv; ++w) {
+        double aw[MAXK], adw[MAXNF][MAXKD], af[MAXK], Wbar = 0.0;
+        for (int v = 0; v < nv; ++v) Wbar += L[w][v] * U0[v];
+        for (int k = 0; k < nk; ++k) {
+          aw[k] = 0.0;
+          for (int v = 0; v < nv; ++v) aw[k] += L[w][v] * aopt[v][k];
+        }
+        for (int s = 0; s < na; ++s)
+          for (int k = 0; k < o->dk; ++k) {
+            adw[adm[s]][k] = 0.0;
+            for (int v = 0; v < nv; ++v) adw[adm[s]][k] += L[w][v] * ad[v][adm[s]][k];
+          }
+        weigh(o, i, f * nv + w, na, adm, aw, adw, af);
+        for (int q = 0; q < nq; ++q) W[q][w] = face_value(o, i, f, q, Wbar, af);
       }
-    } else {
-      for (int k = 0; k < nk; ++k) a1[k] = aopt[k];
-    }
-    /* smoothness indicators (eq. 15) of p_1 and of the directional polynomials */
-    double SI[1 + MAXNF];
-    SI[0] = smoothness(o, a1, nk, o->p.degree);
-    for (int s = 0; s < na; ++s) SI[1 + s] = smoothness(o, ad[adm[s]], o->dk, o->ddeg);
-    for (int s = 0; s <= nf; ++s) o->SI[((size_t)i * nv + v) * (1 + nf) + s] = 0.0;
-    o->SI[((size_t)i * nv + v) * (1 + nf)] = SI[0];
-    for (int s = 0; s < na; ++s) o->SI[((size_t)i * nv + v) * (1 + nf) + 1 + adm[s]] = SI[1 + s];
-    /* scale separation and cut-off (eqs. 19-23, Alg. 1 / Alg. 2) */
-    double chi[1 + MAXNF];
-    const unsigned dbits = select_stencils(&o->p, st, SI, chi);
-    for (int s = 0; s <= nf; ++s) o->chi[((size_t)i * nv + v) * (1 + nf) + s] = 0.0;
-    o->chi[((size_t)i * nv + v) * (1 + nf)] = chi[0];
-    for (int s = 0; s < na; ++s) o->chi[((size_t)i * nv + v) * (1 + nf) + 1 + adm[s]] = chi[1 + s];
-    int delta[1 + MAXNF] = {0, 0, 0, 0, 0}, ndel = 0;
-    for (int s = 0; s < st; ++s) {
-      delta[s] = (dbits >> s) & 1u;
-      if (s > 0) ndel += delta[s];
-    }
-    /* final polynomial: CWENO sum_s w_s p_s (Sec. 2.3); otherwise p_1 if delta_1, else
-     * sum_{s>=2} delta_s p_s / sum delta_s (Alg. 1 / 2) */
-    double af[MAXK];
-    uint8_t fl = 0;
-    if (o->p.scheme == 2) {
-      for (int k = 0; k < nk; ++k) af[k] = chi[0] * a1[k];
-      for (int s = 1; s < st; ++s)
-        for (int k = 0; k < o->dk; ++k) af[k] += chi[s] * ad[adm[s - 1]][k];
-      fl = (uint8_t)(o->stmask[i] & 0xFF);
-    } else if (delta[0]) {
-      for (int k = 0; k < nk; ++k) af[k] = a1[k];
-      fl = 1;
-    } else {
-      for (int k = 0; k < nk; ++k) af[k] = 0.0;
-      for (int s = 1; s < st; ++s)
-        if (delta[s]) {
-          for (int k = 0; k < o->dk; ++k) af[k] += ad[adm[s - 1]][k] / (double)ndel;
-          fl |= (uint8_t)(1 << (1 + adm[s - 1]));
+      for (int q = 0; q < nq; ++q)
+        for (int v = 0; v < nv; ++v) {
+          double s = 0.0;
+          for (int w = 0; w < nv; ++w) s += R[v][w] * W[q][w];
+          fout[f][q][v] = s;
         }
     }
-    o->flags[(size_t)i * nv + v] = fl;
-    for (int k = 0; k < nk; ++k) o->coef[((size_t)i * nv + v) * nk + k] = af[k];
-    /* values at the face Gauss points: U0 + sum_k a_k phi_k(xi_q) (eqs. 7, 2) */
-    const double *X0 = o->X + (size_t)i * (d + 1) * d, *Ji = o->Jinv + i * d * d;
-    for (int f = 0; f < nf; ++f)
-      for (int q = 0; q < nq; ++q) {
-        const double *x = o->fq + ((size_t)(i * nf + f) * nq + q) * d;
-        double xi[3] = {0, 0, 0};
-        for (int r = 0; r < d; ++r)
-          for (int j = 0; j < d; ++j) xi[r] += Ji[r * d + j] * (x[j] - X0[j]);
-        double val = U0;
-        for (int k = 0; k < nk; ++k) val += af[k] * (monomial(o->ex[k], xi, d) - o->psibar[k]);
-        fout[f][q][v] = val;
-      }
   }
+  int guard_hit = 0;
   if (o->p.guard) { /* Reading: non-physical face state -> first order in this cell */
     for (int f = 0; f < nf; ++f)
       for (int q = 0; q < nq; ++q)
@@ -938,7 +1071,7 @@ static void recon_cell(orc *o, int i, const double *U) {
     if (guard_hit) {
       for (int f = 0; f < nf; ++f)
         for (int q = 0; q < nq; ++q)
-          for (int v = 0; v < nv; ++v) fout[f][q][v] = U[v * n + i];
+          for (int v = 0; v < nv; ++v) fout[f][q][v] = U0[v];
     }
   }
   for (int f = 0; f < nf; ++f)
@@ -1092,8 +1225,8 @@ double orc_step(orc *o, double dt) {
 /* ------------------------------------------------------------------------------------------ */
 /* Construction and accessors (ctypes interface)                                               */
 /* ------------------------------------------------------------------------------------------ */
-orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form, double C_T,
-                double lambda1p, double eps, double gamma, double cfl, int guard, int nverts,
+orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form, int characteristic,
+                double C_T, double lambda1p, double eps, double gamma, double cfl, int guard, int nverts,
                 const double *xyz, int ncells, const int *cells, const double *period, int *err) {
   *err = 0;
   if ((dim != 2 && dim != 3) || degree < 1 || degree > (dim == 2 ? 6 : 3)) {
@@ -1112,10 +1245,12 @@ orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form,
   o->p.guard = guard;
   o->p.lam_gamma = lam_gamma;
   o->p.ctenoz_form = ctenoz_form;
+  o->p.characteristic = characteristic;
   o->nverts = nverts;
   o->ncells = ncells;
   o->nv = dim + 2;
   o->nf = dim + 1;
+  o->nsel = characteristic ? o->nf * o->nv : o->nv;
   /* Reading ("a Gauss rule suited to the polynomial order", Sec. 2): edges carry
    * ceil((r + 1) / 2) Gauss-Legendre points, exact for the degree-r face polynomials */
   o->nq = (dim == 2) ? (degree + 2) / 2 : 4;
@@ -1153,12 +1288,12 @@ orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form,
   o->Un = (double *)calloc(n * o->nv, sizeof(double));
   o->Rres = (double *)calloc(n * o->nv, sizeof(double));
   o->face = (double *)calloc(n * o->nf * o->nq * o->nv, sizeof(double));
-  o->flags = (uint8_t *)calloc(n * o->nv, 1);
-  o->SI = (double *)calloc(n * o->nv * (1 + o->nf), sizeof(double));
-  o->chi = (double *)calloc(n * o->nv * (1 + o->nf), sizeof(double));
+  o->flags = (uint8_t *)calloc(n * o->nsel, 1);
+  o->SI = (double *)calloc(n * o->nsel * (1 + o->nf), sizeof(double));
+  o->chi = (double *)calloc(n * o->nsel * (1 + o->nf), sizeof(double));
   o->stmask = (int *)calloc(n, sizeof(int));
   o->guarded = (uint8_t *)calloc(n, 1);
-  o->coef = (double *)calloc(n * o->nv * o->nk, sizeof(double));
+  o->coef = (double *)calloc(n * o->nsel * o->nk, sizeof(double));
   return o;
 }
 
@@ -1345,15 +1480,28 @@ void orc_lsq_apply(const orc *o, int i, const double *Um, double U0, double *a) 
 void orc_get_face_states(const orc *o, double *out) {
   memcpy(out, o->face, sizeof(double) * o->ncells * o->nf * o->nq * o->nv);
 }
-void orc_get_flags(const orc *o, uint8_t *out) { memcpy(out, o->flags, (size_t)o->ncells * o->nv); }
+/* Debug records per cell and selection: [ncells][nsel] with nsel = nv, or nf * nv (face-major)
+ * for the characteristic reconstruction. */
+void orc_get_flags(const orc *o, uint8_t *out) { memcpy(out, o->flags, (size_t)o->ncells * o->nsel); }
 void orc_get_si(const orc *o, double *out) {
-  memcpy(out, o->SI, sizeof(double) * o->ncells * o->nv * (1 + o->nf));
+  memcpy(out, o->SI, sizeof(double) * o->ncells * o->nsel * (1 + o->nf));
 }
 void orc_get_chi(const orc *o, double *out) {
-  memcpy(out, o->chi, sizeof(double) * o->ncells * o->nv * (1 + o->nf));
+  memcpy(out, o->chi, sizeof(double) * o->ncells * o->nsel * (1 + o->nf));
 }
 void orc_get_coeffs(const orc *o, double *out) {
-  memcpy(out, o->coef, sizeof(double) * o->ncells * o->nv * o->nk);
+  memcpy(out, o->coef, sizeof(double) * o->ncells * o->nsel * o->nk);
+}
+/* Eigenvectors of the Euler flux Jacobian in direction n at the conserved state u (row-major
+ * [nv][nv]), as the characteristic reconstruction uses them. */
+void orc_eigen(const orc *o, const double *u, const double *n, double *R, double *L) {
+  double Rm[MAXNV][MAXNV], Lm[MAXNV][MAXNV];
+  euler_eigen(o, u, n, Rm, Lm);
+  for (int a = 0; a < o->nv; ++a)
+    for (int b = 0; b < o->nv; ++b) {
+      R[a * o->nv + b] = Rm[a][b];
+      L[a * o->nv + b] = Lm[a][b];
+    }
 }
 /* Reference map of cell i: oriented vertex coordinates [(d+1)][d] (unwrapped) and J^-1. */
 void orc_get_refmap(const orc *o, int i, double *X, double *Jinv) {
