@@ -27,7 +27,7 @@ def _load():
     lib = C.CDLL(LIB)
     V = C.c_void_p
     lib.orc_create.restype = V
-    lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+    lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _dp, C.c_int,
                                _ip, _dp, C.POINTER(C.c_int)]
     lib.orc_destroy.argtypes = [V]
@@ -80,8 +80,8 @@ def num_threads() -> int:
     return int(_load().orc_num_threads())
 
 
-DEFAULTS = dict(degree=2, scheme=0, lam_gamma=1, ctenoz_form=0, characteristic=0, C_T=1e-6, lambda1p=1e15,
-                eps=1e-24, gamma=1.4, cfl=0.5, guard=1)
+DEFAULTS = dict(degree=2, scheme=0, lam_gamma=1, ctenoz_form=0, characteristic=0, boundary=0, rk=3, C_T=1e-6,
+                lambda1p=1e15, eps=1e-24, gamma=1.4, cfl=0.5, guard=1)
 
 
 def select(SI, scheme=0, ctenoz_form=0, lam_gamma=1, C_T=1e-6, lambda1p=1e15, eps=1e-24):
@@ -108,7 +108,8 @@ class Oracle:
         period = np.ascontiguousarray(mesh.period, dtype=np.float64)
         err = C.c_int(0)
         self.h = self.lib.orc_create(self.dim, p["degree"], p["scheme"], p["lam_gamma"], p["ctenoz_form"],
-                                     p["characteristic"], p["C_T"], p["lambda1p"], p["eps"], p["gamma"], p["cfl"],
+                                     p["characteristic"], p["boundary"], p["rk"], p["C_T"], p["lambda1p"], p["eps"],
+                                     p["gamma"], p["cfl"],
                                      p["guard"],
                                      mesh.nverts, xyz, mesh.ncells, cells, period, C.byref(err))
         if err.value:

@@ -50,6 +50,8 @@ typedef struct {
   int lam_gamma;           /* Reading: 1 = gamma_s carries lambda_s (eq. 18), 0 = as printed */
   int ctenoz_form;         /* Reading: 0 = CTENOZ measure as printed, 1 = WENO-Z form */
   int characteristic;      /* 1: reconstruct characteristic variables, per face (Sec. 2.2, 3.2) */
+  int boundary;            /* boundary faces: 0 transmissive, 1 reflective walls (Sec. 3.3, 3.4) */
+  int rk;                  /* Runge-Kutta scheme (Sec. 2, "3rd- or 4th-order"): 3 SSP-RK3, 4 classical RK4 */
   double C_T, lambda1p, eps, gamma, cfl;
 } orc_params;
 
@@ -98,6 +100,7 @@ typedef struct {
   double *qlam, *qw;
   /* solution */
   double *U, *Un, *Rres, *face; /* face: [ncells][nf][nq][nv] */
+  double *Acc;                  /* RK4: U^n + dt/6 (k_1 + 2 k_2 + 2 k_3) so far */
   int nsel;                     /* selections per cell: nv, or nf * nv (characteristic) */
   uint8_t *flags;               /* [ncells][nsel]: bit 0 central selected, bit 1+f directional f */
   double *SI;                   /* [ncells][nv][1+nf] smoothness indicators (debug) */
@@ -1153,7 +1156,9 @@ static void hllc(const orc *o, const double *uL, const double *uR, const double 
 /* Residual (eq. 2), time step, SSP-RK3                                                        */
 /* ------------------------------------------------------------------------------------------ */
 /* dU_i/dt = -(1/|V_i|) sum_faces sum_q F(U_L, U_R) w_q |A|  (eq. 2). Reading: on a transmissive
- * boundary face the outside state is the cell mean, U_R = U_i (zeroth-order extrapolation); the
+ * boundary face the outside state is the cell mean, U_R = U_i (zeroth-order extrapolation); on a
+ * reflective wall it is the mirror image of the reconstructed inside state, U_R = (rho, m - 2 (m.n) n,
+ * E) at each Gauss point (zero normal velocity at the wall, same density and pressure); the
  * reconstructed U_L stays the inside state. */
 static void residual_cell(orc *o, int i, double *Rout) {
   const int d = o->p.dim, nv = o->nv, nf = o->nf, nq = o->nq;
@@ -1164,7 +1169,15 @@ static void residual_cell(orc *o, int i, double *Rout) {
     for (int q = 0; q < nq; ++q) {
       const double *uL = o->face + (((size_t)i * nf + f) * nq + q) * nv;
       double ub[MAXNV];
-      for (int v = 0; v < nv; ++v) ub[v] = o->U[v * o->ncells + i];
+      if (o->p.boundary == 1) {
+        double mn = 0.0;
+        for (int k = 0; k < d; ++k) mn += uL[1 + k] * n[k];
+        ub[0] = uL[0];
+        for (int k = 0; k < d; ++k) ub[1 + k] = uL[1 + k] - 2.0 * mn * n[k];
+        ub[d + 1] = uL[d + 1];
+      } else {
+        for (int v = 0; v < nv; ++v) ub[v] = o->U[v * o->ncells + i];
+      }
       const double *uR = (j >= 0) ? o->face + (((size_t)j * nf + fj) * nq + q) * nv : ub;
       double F[MAXNV];
       hllc(o, uL, uR, n, F);
@@ -1206,11 +1219,33 @@ double orc_dt(orc *o) {
   return o->p.cfl * best;
 }
 
-/* Third-order SSP Runge-Kutta (Shu-Osher form), the paper's "3rd-order explicit RK" (Sec. 2). */
+/* The paper's explicit Runge-Kutta step ("3rd- or 4th-order", Sec. 2). rk = 3: third-order SSP
+ * Runge-Kutta in Shu-Osher form, U1 = U^n + dt R(U^n), U2 = 3/4 U^n + 1/4 (U1 + dt R(U1)),
+ * U^{n+1} = 1/3 U^n + 2/3 (U2 + dt R(U2)). rk = 4: the classical four-stage method, k_s = R(U_s),
+ * U_1 = U^n, U_2 = U^n + dt/2 k_1, U_3 = U^n + dt/2 k_2, U_4 = U^n + dt k_3,
+ * U^{n+1} = U^n + dt/6 (k_1 + 2 k_2 + 2 k_3 + k_4) (accumulated stage by stage in Acc). */
 void orc_stage(orc *o, int stage, double dt) {
   const int n = o->ncells, nv = o->nv;
   if (stage == 0) memcpy(o->Un, o->U, sizeof(double) * nv * n);
   residual_all(o, o->U);
+  if (o->p.rk == 4) {
+    for (int k = 0; k < nv * n; ++k) {
+      const double dk = dt * o->Rres[k];
+      if (stage == 0) {
+        o->Acc[k] = o->Un[k] + dk / 6.0;
+        o->U[k] = o->Un[k] + 0.5 * dk;
+      } else if (stage == 1) {
+        o->Acc[k] += dk / 3.0;
+        o->U[k] = o->Un[k] + 0.5 * dk;
+      } else if (stage == 2) {
+        o->Acc[k] += dk / 3.0;
+        o->U[k] = o->Un[k] + dk;
+      } else {
+        o->U[k] = o->Acc[k] + dk / 6.0;
+      }
+    }
+    return;
+  }
   static const double a[3] = {0.0, 0.75, 1.0 / 3.0}, b[3] = {1.0, 0.25, 2.0 / 3.0};
   for (int k = 0; k < nv * n; ++k)
     o->U[k] = a[stage] * o->Un[k] + b[stage] * (o->U[k] + dt * o->Rres[k]);
@@ -1218,7 +1253,7 @@ void orc_stage(orc *o, int stage, double dt) {
 
 double orc_step(orc *o, double dt) {
   if (!(dt > 0.0)) dt = orc_dt(o);
-  for (int s = 0; s < 3; ++s) orc_stage(o, s, dt);
+  for (int s = 0; s < (o->p.rk == 4 ? 4 : 3); ++s) orc_stage(o, s, dt);
   return dt;
 }
 
@@ -1226,10 +1261,11 @@ double orc_step(orc *o, double dt) {
 /* Construction and accessors (ctypes interface)                                               */
 /* ------------------------------------------------------------------------------------------ */
 orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form, int characteristic,
-                double C_T, double lambda1p, double eps, double gamma, double cfl, int guard, int nverts,
+                int boundary, int rk, double C_T, double lambda1p, double eps, double gamma, double cfl, int guard, int nverts,
                 const double *xyz, int ncells, const int *cells, const double *period, int *err) {
   *err = 0;
-  if ((dim != 2 && dim != 3) || degree < 1 || degree > (dim == 2 ? 6 : 3)) {
+  if ((dim != 2 && dim != 3) || degree < 1 || degree > (dim == 2 ? 6 : 3) || (boundary != 0 && boundary != 1) ||
+      (rk != 3 && rk != 4)) {
     *err = -1;
     return NULL;
   }
@@ -1246,6 +1282,8 @@ orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form,
   o->p.lam_gamma = lam_gamma;
   o->p.ctenoz_form = ctenoz_form;
   o->p.characteristic = characteristic;
+  o->p.boundary = boundary;
+  o->p.rk = rk;
   o->nverts = nverts;
   o->ncells = ncells;
   o->nv = dim + 2;
@@ -1286,6 +1324,7 @@ orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form,
   o->cell = (orc_cell **)calloc(n, sizeof(orc_cell *));
   o->U = (double *)calloc(n * o->nv, sizeof(double));
   o->Un = (double *)calloc(n * o->nv, sizeof(double));
+  o->Acc = (double *)calloc(n * o->nv, sizeof(double));
   o->Rres = (double *)calloc(n * o->nv, sizeof(double));
   o->face = (double *)calloc(n * o->nf * o->nq * o->nv, sizeof(double));
   o->flags = (uint8_t *)calloc(n * o->nsel, 1);
@@ -1345,7 +1384,7 @@ void orc_destroy(orc *o) {
   free(o->cv); free(o->X); free(o->vol); free(o->cen); free(o->Jinv); free(o->detJ);
   free(o->nbr); free(o->nbrf); free(o->area); free(o->nrm); free(o->fq);
   free(o->v2c_off); free(o->v2c); free(o->qlam); free(o->qw);
-  free(o->U); free(o->Un); free(o->Rres); free(o->face); free(o->flags); free(o->SI); free(o->chi);
+  free(o->U); free(o->Un); free(o->Acc); free(o->Rres); free(o->face); free(o->flags); free(o->SI); free(o->chi);
   free(o->stmask);
   free(o->guarded);
   free(o->coef);
