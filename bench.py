@@ -13,12 +13,15 @@ the metric counts cells x 3 stages.
 object: the blast in FP64; the 2D shock tube (512x128 squares -> 131072 triangles, Sod, CFL 0.4)
 with CTENO and CTENOZ at degree 2 and 3; the 3D density wave (64^3 x 6 tetrahedra, CTENO degree
 2); the batch of 64 four-quadrant Riemann problems (1.74M triangles, CTENOZ degree 2, one launch
-per kernel for all meshes) -- each in both precisions. L2 (129 MB) is flushed between timed steps
-by a 256 MB write outside the timed events.
+per kernel for all meshes); the single-material triple point (Sec. 3.4: 215000 triangles, walls,
+lambda_1' = 1e4) with CWENO, TENO, CTENO and CTENOZ at fifth and seventh order, whose times per
+step relative to CWENO of the same order are the GPU counterpart of the paper's Table 5 -- each
+in both precisions. L2 (129 MB) is flushed between timed steps by a 256 MB write outside the
+timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload blast_3d_96|shock_tube_2d|density_wave_3d_64|batch_2d]
-                  [--variants all|none] [--profile]
+                  [--workload blast_3d_96|shock_tube_2d|density_wave_3d_64|batch_2d|triple_point_2d]
+                  [--variants all|workload|none] [--profile]
 
 --profile runs only warm-up + steps of the headline (a short command for ncu).
 
@@ -46,14 +49,16 @@ METRIC = "Mcell-RK-stage/s (deg 2/3, 2D tri & 3D tet), FP32-mixed vs FP64 on one
 UNIT = "Mcell-RK-stage/s"
 SCHEMES = {0: "CTENO", 1: "CTENOZ", 2: "CWENO", 3: "TENO"}
 PRECISIONS = {0: "fp64", 1: "mixed"}
-WORKLOADS = ["blast_3d_96", "shock_tube_2d", "density_wave_3d_64", "batch_2d"]
+WORKLOADS = ["blast_3d_96", "shock_tube_2d", "density_wave_3d_64", "batch_2d", "triple_point_2d"]
 
 
 class Case:
     """A workload: meshes + initial states + the scheme it is defined with."""
 
-    def __init__(self, name, description, meshes, states, dim, scheme, degree, cfl, variants, sample_centre):
+    def __init__(self, name, description, meshes, states, dim, scheme, degree, cfl, variants, sample_centre,
+                 extra=None):
         self.name, self.description = name, description
+        self.extra = extra or {}          # further solver parameters (boundary kind, lambda_1')
         self.meshes, self.states, self.dim = meshes, states, dim
         self.scheme, self.degree, self.cfl = scheme, degree, cfl
         self.variants = variants          # (scheme, degree) pairs timed in both precisions
@@ -87,6 +92,13 @@ def make_case(name, n=0):
                     f"{sum(w.mesh.ncells for w in wls)} cells, four-quadrant Riemann states, CFL 0.4, "
                     "one launch per kernel for all meshes", [w.mesh for w in wls], [w.U0 for w in wls],
                     2, 1, 2, 0.4, [(1, 2)], (0.5, 0.5))
+    if name == "triple_point_2d":
+        wl = W.triple_point_2d()
+        return Case(name, f"single-material triple point (Sec. 3.4), [0,7]x[0,3], 500x215 squares -> "
+                    f"{wl.mesh.ncells} triangles, walls all round, lambda_1' = 1e4, CFL 0.4",
+                    [wl.mesh], [wl.U0], 2, 1, 4, 0.4,
+                    [(2, 4), (3, 4), (0, 4), (1, 4), (2, 6), (3, 6), (0, 6), (1, 6)], (3.5, 1.5),
+                    extra=dict(lambda1p=1e4, boundary=1))
     raise ValueError(name)
 
 
@@ -268,7 +280,7 @@ def ncu_traffic(key):
 
 def make_solver(native, case, scheme, degree, precision, stream):
     s = native.Solver(case.meshes, case.dim, degree=degree, scheme=scheme, precision=precision,
-                      stream=stream, cfl=case.cfl)
+                      stream=stream, cfl=case.cfl, **case.extra)
     native.cteno_set_state_all(s.ctx, case.states)
     return s
 
@@ -500,7 +512,8 @@ def _subbox_sample(case, target):
 
 
 # cells of one oracle stage of the sample, by (dim, degree): about 1-2 s of one stage on 16 cores
-SAMPLE_CELLS = {(2, 2): 131072, (2, 3): 131072, (3, 2): 300000, (3, 3): 60000}
+SAMPLE_CELLS = {(2, 2): 131072, (2, 3): 131072, (3, 2): 300000, (3, 3): 60000, (2, 4): 60000, (2, 5): 40000,
+                (2, 6): 30000}
 
 
 def oracle_sample_timing(case, h, budget_s=20.0):
@@ -512,7 +525,7 @@ def oracle_sample_timing(case, h, budget_s=20.0):
     mesh, U0 = case.meshes[0], case.states[0]
     ids = _subbox_sample(case, SAMPLE_CELLS[(case.dim, h["degree"])])
     t0 = time.perf_counter()
-    o = Oracle(mesh, setup=False, degree=h["degree"], scheme=h["scheme"], cfl=case.cfl)
+    o = Oracle(mesh, setup=False, degree=h["degree"], scheme=h["scheme"], cfl=case.cfl, **case.extra)
     o.set_state(U0)
     nbr = o.geometry()["nbr"][ids]
     o.setup_cells(np.unique(np.concatenate([ids, nbr[nbr >= 0]])))
@@ -541,7 +554,7 @@ def run_reference(args, rank, world):
     h = dict(scheme=case.scheme, degree=case.degree)
     mesh, U0 = case.meshes[0], case.states[0]
     ids = _subbox_sample(case, SAMPLE_CELLS[(case.dim, case.degree)])
-    o = Oracle(mesh, setup=False, degree=case.degree, scheme=case.scheme, cfl=case.cfl)
+    o = Oracle(mesh, setup=False, degree=case.degree, scheme=case.scheme, cfl=case.cfl, **case.extra)
     o.set_state(U0)
     nbr = o.geometry()["nbr"][ids]
     o.setup_cells(np.unique(np.concatenate([ids, nbr[nbr >= 0]])))

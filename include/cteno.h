@@ -50,7 +50,11 @@ enum {
 
 enum { CTENO_SCHEME_CTENO = 0, CTENO_SCHEME_CTENOZ = 1, CTENO_SCHEME_CWENO = 2, CTENO_SCHEME_TENO = 3 };
 enum { CTENO_FP64 = 0, CTENO_MIXED = 1 };
-enum { CTENO_BOUNDARY_TRANSMISSIVE = 0 };
+/* Boundary faces of a mesh: transmissive (the outside state is the cell mean) or reflective walls
+ * (the outside state at each Gauss point is the mirror image of the reconstructed inside state,
+ * (rho, m - 2 (m.n) n, E); the paper's Sec. 3.3 and 3.4 run walls without printing their
+ * treatment). Periodic directions have no boundary faces. */
+enum { CTENO_BOUNDARY_TRANSMISSIVE = 0, CTENO_BOUNDARY_WALL = 1 };
 
 /* Scheme parameters (paper notation). */
 typedef struct {
@@ -76,6 +80,15 @@ typedef struct {
                            tau = (sum_{s>=2} |SI_s - SI_1| / (s_t - 1))^6, gamma_s = 1 + tau/(SI_s + eps).
                            1: the WENO-Z arrangement, tau = sum_{s>=2} |SI_s - SI_1| / (s_t - 1),
                            gamma_s = 1 + (tau/(SI_s + eps))^6 (a reading; scale invariant) */
+  int characteristic;   /* 0: reconstruct the conserved variables, each selected independently.
+                           1: reconstruct characteristic variables (Sec. 2.2, 3.2): for each face,
+                           W = L U with L the left eigenvectors of the Euler flux Jacobian in the
+                           face's outward normal direction at the cell's mean state; every field
+                           selected independently; the face's Gauss-point values transformed back
+                           with R = L^-1. Reconstruction schedule 1024 + b only */
+  int rk;               /* explicit Runge-Kutta step (Sec. 2, "3rd- or 4th-order"): 3 = SSP-RK3
+                           (Shu-Osher form, 3 stages), 4 = the classical RK4 (4 stages, one more
+                           FP64 state array); cteno_run replays all stages of a step */
   double C_T;           /* cut-off of eq. 23 (paper: 1e-6) */
   double lambda1p;      /* lambda_1' of eq. 18 (paper: 1e4 or 1e15) */
   double eps;           /* epsilon of eqs. 19 and CTENOZ (not given by the paper; default 1e-24,
@@ -90,6 +103,7 @@ typedef struct {
 typedef struct cteno_ctx cteno_ctx;
 
 /* Fill *p with the defaults: d = 2, r = 2, CTENO, FP64, lam_gamma 1, guard 1, ctenoz_form 0,
+ * characteristic 0, rk 3,
  * C_T = 1e-6, lambda_1' = 1e15, eps = 1e-24, CFL 0.5, gamma 1.4. */
 void cteno_default_params(cteno_params *p);
 
@@ -107,7 +121,9 @@ int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream);
  *   ncells, cell_verts : host, cell_verts[ncells][dim+1] vertex ids (any orientation; copied).
  *   period             : host, period[dim]; period[j] > 0 makes direction j periodic with that
  *                        length (vertices are stored once and cells unwrap across the box);
- *                        NULL or 0 = bounded. Bounded boundary faces are transmissive.
+ *                        NULL or 0 = bounded.
+ *   boundary_kind      : CTENO_BOUNDARY_TRANSMISSIVE or CTENO_BOUNDARY_WALL, for every bounded
+ *                        boundary face of this mesh (meshes of a batch may differ).
  *   mesh_id_out        : receives the index of the mesh in the batch.
  * Errors: CTENO_ERR_MESH for degenerate cells or faces shared by more than two cells. Meshes can
  * only be added before cteno_stencil_build. */
@@ -140,16 +156,16 @@ int cteno_set_state(cteno_ctx *ctx, int32_t mesh_id, const double *U, int is_dev
  * memory is staged through device memory before the call returns. */
 int cteno_set_state_all(cteno_ctx *ctx, const double *U, int is_device);
 
-/* One stage (stage = 0, 1, 2) of the SSP-RK3 step, for every mesh. dt: host array of the time
- * step of each mesh (length nmeshes), or NULL: at stage 0 each mesh then takes the CFL step of its
- * current state, dt = CFL min_i |V_i| / sum_f |A_f| (|u_i.n_f| + c_i) (the step cteno_run takes;
- * it is computed by cteno_set_state / cteno_set_state_all and by every stage 2), and stages 1 and 2
- * keep the step of the last stage 0. Stage 0 stores U^n. */
+/* One stage (stage = 0 .. rk - 1) of the Runge-Kutta step (cteno_params.rk), for every mesh. dt:
+ * host array of the time step of each mesh (length nmeshes), or NULL: at stage 0 each mesh then
+ * takes the CFL step of its current state, dt = CFL min_i |V_i| / sum_f |A_f| (|u_i.n_f| + c_i)
+ * (the step cteno_run takes; it is computed by cteno_set_state / cteno_set_state_all and by every
+ * last stage), and the later stages keep the step of the last stage 0. Stage 0 stores U^n. */
 int cteno_rk_stage(cteno_ctx *ctx, int stage, const double *dt);
 
-/* nsteps full SSP-RK3 steps, each with dt = CFL * min_i |V_i| / sum_f |A_f| (|u_i.n_f| + c_i)
- * taken per mesh from the state at the start of the step. The 3 stages of a step are captured
- * once into a CUDA graph and replayed. */
+/* nsteps full Runge-Kutta steps (SSP-RK3 or RK4, cteno_params.rk), each with dt = CFL * min_i
+ * |V_i| / sum_f |A_f| (|u_i.n_f| + c_i) taken per mesh from the state at the start of the step.
+ * The stages of a step are captured once into a CUDA graph and replayed. */
 int cteno_run(cteno_ctx *ctx, int nsteps);
 
 /* Read the conserved cell means of one mesh into U_out[v][c] (host or device). A host read
@@ -188,7 +204,8 @@ int cteno_record_flags(cteno_ctx *ctx, int enable);
 
 /* Selection flags of the last reconstruction of one mesh, host out[c][v] (original numbering):
  * bit 0 = central stencil kept (delta_1 = 1); bit 1+f = directional stencil of local face f
- * selected (eq. 23 and Alg. 1 / 2). Local faces follow the positively oriented vertex order. */
+ * selected (eq. 23 and Alg. 1 / 2). Local faces follow the positively oriented vertex order.
+ * With the characteristic reconstruction out[c][f][w]: face f, characteristic field w. */
 int cteno_get_flags(cteno_ctx *ctx, int32_t mesh_id, uint8_t *out);
 
 /* Reconstructed face Gauss-point states of the last reconstruction (debug), host
@@ -203,10 +220,11 @@ int cteno_get_face_states(cteno_ctx *ctx, int32_t mesh_id, double *out);
 int cteno_get_stencil(cteno_ctx *ctx, int32_t mesh_id, int64_t cell, int32_t *central,
                       int32_t *dir, int32_t *dok);
 
-/* Sizes, out[9]: out[0] = nmeshes, out[1] = total cells, out[2] = M, out[3] = K-1, out[4] = nv,
+/* Sizes, out[10]: out[0] = nmeshes, out[1] = total cells, out[2] = M, out[3] = K-1, out[4] = nv,
  * out[5] = faces per cell, out[6] = Gauss points per face, out[7] = cells of mesh `mesh_id`
  * (or 0 if mesh_id < 0), out[8] = members of a directional stencil at most (2d up to degree 3,
- * 10 for degrees 4 to 6). */
+ * 10 for degrees 4 to 6), out[9] = selection flags per cell (nv, or (d+1) nv with the
+ * characteristic reconstruction). */
 int cteno_info(cteno_ctx *ctx, int32_t mesh_id, int64_t *out);
 
 /* Number of cells that fell back to their mean under the positivity guard since the last call,
@@ -239,8 +257,9 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
  * 8192 + b (b a multiple of 32 in
  * [32, 256]) selects the face-based schedule: HLLC once per face, in its owner's orientation, into
  * a face-flux array, then a per-cell gather and update (results bit-identical to the per-cell
- * schedules). At central degrees 4 to 6 the reconstruction takes 1024 + b only (default 1024 +
- * 128); every other reconstruction value is refused with CTENO_ERR_ARG. */
+ * schedules). At central degrees 4 to 6 and with the characteristic reconstruction the reconstruction
+ * takes 1024 + b only (default 1024 + 128); every other reconstruction value is refused with
+ * CTENO_ERR_ARG. */
 int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block);
 
 /* Time the candidate launch configurations (block sizes 64/128/256, on the mixed path the

@@ -20,6 +20,7 @@ struct cteno_ctx {
   cudaStream_t stream = nullptr;     // borrowed
   cudaStream_t capture = nullptr;    // owned, for graph capture
   int d = 0, nv = 0, nf = 0, nq = 0, nk = 0, M = 0, nd = 0;
+  int nsel = 0;  // selections per cell: nv, or nf * nv (characteristic reconstruction)
   bool fp32 = false;
   std::vector<Mesh> meshes;
   bool stencils = false, built = false;
@@ -31,6 +32,7 @@ struct cteno_ctx {
   DevTables *d_tab = nullptr;
   int64_t *d_mesh_off = nullptr;
   double *U = nullptr, *Un = nullptr;
+  double *Acc = nullptr;             // RK4 running sum
   float *U32 = nullptr;
   int32_t *st = nullptr, *nbr = nullptr;
   int32_t *hl = nullptr;             // gather staging: per-tile distinct member lists (mixed path)
@@ -64,7 +66,8 @@ struct cteno_ctx {
   unsigned long long test_wait_ns = 0;  // test hook of the bounded waits (0 = off)
   double *noalloc_stage = nullptr;   // device address of the allocation-free staging array
   int64_t noalloc_cap = 0;           //   and its capacity in doubles (looked up by lsq_build)
-  cudaEvent_t tev[7] = {};           // event record nodes of the step graph
+  cudaEvent_t tev[9] = {};           // event record nodes of the step graph (2 per stage + 1)
+  int nst = 3;                       // Runge-Kutta stages per step (3, or 4 for RK4)
 };
 
 namespace {
@@ -137,6 +140,10 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.cfl = ctx->p.cfl;
   a.lam_gamma = ctx->p.scheme == CTENO_SCHEME_TENO ? 0 : ctx->p.lam_gamma;  // TENO has no linear coefficients
   a.ctenoz_form = ctx->p.ctenoz_form;
+  a.characteristic = ctx->p.characteristic;
+  a.Acc = ctx->Acc;
+  a.rk4 = ctx->nst == 4;
+  a.last_stage = ctx->nst - 1;
   a.cweno = ctx->p.scheme == CTENO_SCHEME_CWENO;
   a.central_split = ctx->p.scheme != CTENO_SCHEME_TENO;
   a.guard_on = ctx->p.positivity_guard;
@@ -253,6 +260,8 @@ void cteno_default_params(cteno_params *p) {
   p->lam_gamma = 1;
   p->positivity_guard = 1;
   p->ctenoz_form = 0;
+  p->characteristic = 0;
+  p->rk = 3;
   p->C_T = 1e-6;
   p->lambda1p = 1e15;
   p->eps = 1e-24;
@@ -266,6 +275,7 @@ int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream) {
   if ((p->dim != 2 && p->dim != 3) || p->degree < 2 || p->degree > (p->dim == 2 ? 6 : 3) ||
       p->scheme < 0 || p->scheme > 3 || (p->precision != 0 && p->precision != 1) ||
       (p->ctenoz_form != 0 && p->ctenoz_form != 1) || (p->lam_gamma != 0 && p->lam_gamma != 1) ||
+      (p->characteristic != 0 && p->characteristic != 1) || (p->rk != 3 && p->rk != 4) ||
       !(p->lambda1p > 1.0) || !(p->C_T >= 0.0 && p->C_T < 1.0) || !(p->eps >= 0.0) ||
       !(p->cfl > 0.0) || !(p->gamma > 1.0))
     return CTENO_ERR_ARG;
@@ -282,7 +292,10 @@ int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream) {
   ctx->nk = coeff_count(p->degree, p->dim) - 1;
   ctx->M = 2 * coeff_count(p->degree, p->dim);
   ctx->nd = dir_members(p->dim, p->degree);
-  if (p->degree >= 4) ctx->recon_block = kLaneSchedule + 128;  // the schedule of degrees 4 to 6
+  // the variable-per-lane schedule for degrees 4 to 6 and for the characteristic reconstruction
+  if (p->degree >= 4 || p->characteristic) ctx->recon_block = kLaneSchedule + 128;
+  ctx->nsel = p->characteristic ? ctx->nf * ctx->nv : ctx->nv;
+  ctx->nst = p->rk;
   ctx->fp32 = (p->precision == CTENO_MIXED);
   build_tables(p->dim, p->degree, &ctx->tab);
   *out = ctx;
@@ -295,7 +308,7 @@ int cteno_mesh_build(cteno_ctx *ctx, int64_t nverts, const double *xyz, int64_t 
   if (!ctx) return CTENO_ERR_ARG;
   if (ctx->stencils) return fail(ctx, CTENO_ERR_STATE, "meshes must be added before cteno_stencil_build");
   if (!xyz || !cell_verts || nverts <= 0 || ncells <= 0 || ncells > INT32_MAX / 2 ||
-      boundary_kind != CTENO_BOUNDARY_TRANSMISSIVE)
+      (boundary_kind != CTENO_BOUNDARY_TRANSMISSIVE && boundary_kind != CTENO_BOUNDARY_WALL))
     return fail(ctx, CTENO_ERR_ARG, "invalid mesh arguments");
   Mesh m;
   int rc = ingest_mesh(ctx->d, nverts, xyz, ncells, cell_verts, period, &m, &ctx->err);
@@ -304,6 +317,7 @@ int cteno_mesh_build(cteno_ctx *ctx, int64_t nverts, const double *xyz, int64_t 
     for (int j = 0; j < 3; ++j)
       if (ctx->meshes[0].period[j] != m.period[j])
         return fail(ctx, CTENO_ERR_ARG, "all meshes of one context must have the same period");
+  m.wall = boundary_kind == CTENO_BOUNDARY_WALL;
   ctx->meshes.push_back(std::move(m));
   if (mesh_id_out) *mesh_id_out = (int32_t)ctx->meshes.size() - 1;
   return CTENO_OK;
@@ -438,6 +452,7 @@ int cteno_lsq_build(cteno_ctx *ctx) {
         if (nb < 0) {
           hnbr[(size_t)g * 4 + f] = -1;
           meta |= 1u << (kMetaOwnerShift + f);
+          if (m.wall) meta |= 1u << (kMetaWallShift + f);
         } else {
           const int64_t gn = m.offset + m.rank[nb];
           hnbr[(size_t)g * 4 + f] = (int32_t)gn;
@@ -496,6 +511,7 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   const int nvp = lay_nvp(d), pds = dir_pds(d, ctx->p.degree);
   CK(dalloc(ctx, &ctx->U, sizeof(double) * nvp * N));
   CK(dalloc(ctx, &ctx->Un, sizeof(double) * nvp * N));
+  if (ctx->nst == 4) CK(dalloc(ctx, &ctx->Acc, sizeof(double) * nvp * N));
   if (ctx->fp32) CK(dalloc(ctx, &ctx->U32, 2 * sizeof(float) * nvp * N));
   CK(dalloc(ctx, &ctx->st, sizeof(int32_t) * M * N));
   CK(dalloc(ctx, &ctx->nbr, sizeof(int32_t) * 4 * N));
@@ -680,13 +696,13 @@ int cteno_get_state_all(cteno_ctx *ctx, double *U_out, int is_device) {
 int cteno_rk_stage(cteno_ctx *ctx, int stage, const double *dt) {
   int rc = check_built(ctx);
   if (rc) return rc;
-  if (stage < 0 || stage > 2) return fail(ctx, CTENO_ERR_ARG, "bad stage");
+  if (stage < 0 || stage >= ctx->nst) return fail(ctx, CTENO_ERR_ARG, "bad stage");
   int swap = 0;
   if (dt) {
     CK(cudaMemcpyAsync(ctx->dt, dt, sizeof(double) * ctx->meshes.size(), cudaMemcpyHostToDevice, ctx->stream));
     if (stage == 0) launch_dt_reset(make_args(ctx, 0, 0), ctx->stream);
   } else if (stage == 0) {
-    swap = 1;  // the CFL step of the current state (computed by set_state or the last stage 2)
+    swap = 1;  // the CFL step of the current state (computed by set_state or the last stage)
   }
   CK(enqueue_stage(ctx, stage, swap, ctx->stream));
   CK(cudaGetLastError());
@@ -700,7 +716,7 @@ int cteno_run(cteno_ctx *ctx, int nsteps) {
   if (!ctx->graph_exec) {
     CK(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
     if (ctx->timing) CK(cudaEventRecordWithFlags(ctx->tev[0], ctx->capture, cudaEventRecordExternal));
-    for (int s = 0; s < 3; ++s) {
+    for (int s = 0; s < ctx->nst; ++s) {
       const KArgs a = make_args(ctx, s, s == 0 ? 1 : 0);
       const cudaError_t le =
           launch_recon(ctx->d, ctx->p.degree, ctx->fp32 ? 1 : 0, kscheme(ctx), a, ctx->recon_block, ctx->capture);
@@ -755,8 +771,8 @@ int cteno_record_flags(cteno_ctx *ctx, int enable) {
   int rc = check_built(ctx);
   if (rc) return rc;
   if (enable && !ctx->flags) {
-    CK(dalloc(ctx, &ctx->flags, (size_t)ctx->nv * ctx->N));
-    CK(cudaMemsetAsync(ctx->flags, 0, (size_t)ctx->nv * ctx->N, ctx->stream));
+    CK(dalloc(ctx, &ctx->flags, (size_t)ctx->nsel * ctx->N));
+    CK(cudaMemsetAsync(ctx->flags, 0, (size_t)ctx->nsel * ctx->N, ctx->stream));
   }
   if ((bool)enable != ctx->record_flags) drop_graph(ctx);
   ctx->record_flags = enable != 0;
@@ -771,13 +787,14 @@ int cteno_get_flags(cteno_ctx *ctx, int32_t mesh_id, uint8_t *out) {
   if (!ctx->flags) return fail(ctx, CTENO_ERR_STATE, "flag recording is off");
   const Mesh &m = ctx->meshes[mesh_id];
   const int64_t N = ctx->N;
-  std::vector<uint8_t> h((size_t)ctx->nv * m.ncells);
-  for (int v = 0; v < ctx->nv; ++v)
+  const int ns = ctx->nsel;  // one plane per selection: variable, or (face, field)
+  std::vector<uint8_t> h((size_t)ns * m.ncells);
+  for (int v = 0; v < ns; ++v)
     CK(cudaMemcpyAsync(h.data() + (size_t)v * m.ncells, ctx->flags + (size_t)v * N + m.offset, m.ncells,
                        cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   for (int64_t c = 0; c < m.ncells; ++c)
-    for (int v = 0; v < ctx->nv; ++v) out[c * ctx->nv + v] = h[(size_t)v * m.ncells + m.rank[c]];
+    for (int v = 0; v < ns; ++v) out[c * ns + v] = h[(size_t)v * m.ncells + m.rank[c]];
   return CTENO_OK;
 }
 
@@ -835,6 +852,7 @@ int cteno_info(cteno_ctx *ctx, int32_t mesh_id, int64_t *out) {
   out[6] = ctx->nq;
   out[7] = (mesh_id >= 0 && mesh_id < (int32_t)ctx->meshes.size()) ? ctx->meshes[mesh_id].ncells : 0;
   out[8] = ctx->nd;
+  out[9] = ctx->nsel;
   return CTENO_OK;
 }
 
@@ -856,6 +874,9 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
   auto ok = [&](int b, bool recon) {
     if (b == 0) return true;
     if (recon && ctx->p.degree >= 4)  // degrees 4 to 6: the variable-per-lane schedule only
+      return b >= kLaneSchedule + 32 && b <= kLaneSchedule + 256 && b % 32 == 0;
+    // the characteristic reconstruction: the variable-per-lane schedule only
+    if (recon && ctx->p.characteristic)
       return b >= kLaneSchedule + 32 && b <= kLaneSchedule + 256 && b % 32 == 0;
     if (b >= kFaceFlux)  // face-based flux schedule
       return !recon && b - kFaceFlux >= 32 && b - kFaceFlux <= 256 && b % 32 == 0;
@@ -947,6 +968,8 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
     for (int w : {2, 4, 6, 7, 8})
       if (recon_stream_cells_smem(ctx->d, ctx->p.degree, w) <= kMaxStreamSmem) rcand.push_back(kStreamCells + w);
   }
+  if (ctx->p.characteristic)  // the variable-per-lane schedule only
+    rcand = {kLaneSchedule + 64, kLaneSchedule + 128, kLaneSchedule + 256};
   const int reps = 5;
   float best_r = 1e30f, best_f = 1e30f;
   int br = ctx->recon_block, bf = ctx->flux_block;
@@ -1023,23 +1046,24 @@ int cteno_profile_step(cteno_ctx *ctx, int nsteps, double *ms_out) {
   int rc = check_built(ctx);
   if (rc) return rc;
   if (!ms_out || nsteps <= 0) return fail(ctx, CTENO_ERR_ARG, "bad arguments");
-  cudaEvent_t ev[7];
+  const int ns = ctx->nst;
+  cudaEvent_t ev[9];
   for (auto &e : ev) CK(cudaEventCreate(&e));
   double tr = 0.0, tf = 0.0;
   for (int k = 0; k < nsteps; ++k) {
-    for (int s = 0; s < 3; ++s) {
+    for (int s = 0; s < ns; ++s) {
       const KArgs a = make_args(ctx, s, s == 0 ? 1 : 0);
       CK(cudaEventRecord(ev[2 * s], ctx->stream));
       CK(launch_recon(ctx->d, ctx->p.degree, ctx->fp32, kscheme(ctx), a, ctx->recon_block, ctx->stream));
       CK(cudaEventRecord(ev[2 * s + 1], ctx->stream));
       launch_flux(ctx->d, ctx->nq, ctx->fp32, a, ctx->flux_block, ctx->stream);
     }
-    CK(cudaEventRecord(ev[6], ctx->stream));
-    CK(cudaEventSynchronize(ev[6]));
-    for (int s = 0; s < 3; ++s) {
+    CK(cudaEventRecord(ev[2 * ns], ctx->stream));
+    CK(cudaEventSynchronize(ev[2 * ns]));
+    for (int s = 0; s < ns; ++s) {
       float a = 0, b = 0;
       CK(cudaEventElapsedTime(&a, ev[2 * s], ev[2 * s + 1]));
-      CK(cudaEventElapsedTime(&b, ev[2 * s + 1], (s < 2) ? ev[2 * s + 2] : ev[6]));
+      CK(cudaEventElapsedTime(&b, ev[2 * s + 1], ev[2 * s + 2]));
       tr += a;
       tf += b;
     }
@@ -1065,9 +1089,9 @@ int cteno_last_kernel_ms(cteno_ctx *ctx, double *ms_out) {
   if (rc) return rc;
   if (!ms_out) return fail(ctx, CTENO_ERR_ARG, "null output");
   if (!ctx->timing || !ctx->graph_exec) return fail(ctx, CTENO_ERR_STATE, "timing is off or no step has run");
-  CK(cudaEventSynchronize(ctx->tev[6]));
+  CK(cudaEventSynchronize(ctx->tev[2 * ctx->nst]));
   double r = 0.0, f = 0.0;
-  for (int s = 0; s < 3; ++s) {
+  for (int s = 0; s < ctx->nst; ++s) {
     float a = 0, b = 0;
     CK(cudaEventElapsedTime(&a, ctx->tev[2 * s], ctx->tev[2 * s + 1]));
     CK(cudaEventElapsedTime(&b, ctx->tev[2 * s + 1], ctx->tev[2 * s + 2]));

@@ -50,8 +50,10 @@ inline int dir_pds(int d, int degree) { return degree >= 4 ? 60 : lay_pds(d); }
 constexpr int kInfoAdmShift = 16;
 constexpr int kInfoPermShift = 20;
 // Bits of `fmeta`: [2f, 2f+2) neighbour's local face; 8 + f: this cell owns face f (computes the
-// flux in its own orientation; the other cell uses the exact negative normal and negates).
+// flux in its own orientation; the other cell uses the exact negative normal and negates);
+// 12 + f: face f is a reflective wall (a boundary face of a mesh built with CTENO_BOUNDARY_WALL).
 constexpr int kMetaOwnerShift = 8;
+constexpr int kMetaWallShift = 12;
 
 // Error word bits.
 constexpr int kErrNonFinite = 1;
@@ -87,6 +89,7 @@ struct KArgs {
   const int64_t *mesh_off;  // [nmesh + 1] first device cell of each mesh
   double *U;
   double *Un;
+  double *Acc;              // classical RK4: U^n + dt/6 (k1 + 2 k2 + 2 k3) so far, [N][NVP]
   float *U32;
   const int32_t *st;
   const uint32_t *cinfo;
@@ -106,6 +109,7 @@ struct KArgs {
   // parameters
   double C_T, lambda1p, eps, gamma, cfl;
   int lam_gamma, guard_on, ctenoz_form;
+  int characteristic;  // characteristic-variable reconstruction per face (Sec. 2.2, 3.2)
   int cweno;          // CWENO weighting (Sec. 2.3) instead of the cut-off selection
   int central_split;  // p_1 from the CWENO split of eq. 17 (CTENO, CTENOZ, CWENO); 0: TENO's p_opt
   // linear coefficients of eq. 18, evaluated once on the host in FP64:
@@ -137,7 +141,9 @@ struct KArgs {
   // test hook of the bounded waits (0 = off): the staged schedules first wait at most this many
   // nanoseconds on a barrier that nothing completes, then take their timeout path
   unsigned long long test_wait_ns;
-  int stage;                // 0, 1, 2
+  int stage;                // 0 .. last_stage
+  int rk4;                  // classical four-stage Runge-Kutta (else SSP-RK3)
+  int last_stage;           // 2 (SSP-RK3) or 3 (RK4): the stage that computes the next CFL step
   int dt_swap;              // stage 0 of a CFL step: move dt[next] to dt[cur] first
 };
 

@@ -80,6 +80,20 @@ __device__ __forceinline__ float2 f64_split(double x) {
   return make_float2(hi, __uint_as_float(sign | ((uint32_t)el << 23) | ml));
 }
 
+// Outside state of a reflective wall at a Gauss point (reading: the paper runs walls in Sec. 3.3
+// and 3.4 without printing their treatment): the mirror image of the inside state u across the
+// wall with outward unit normal n, (rho, m - 2 (m.n) n, E).
+template <int D, typename T>
+__device__ __forceinline__ void wall_mirror(const T *u, const T *n, T *o) {
+  T mn = (T)0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) mn += u[1 + j] * n[j];
+  o[0] = u[0];
+#pragma unroll
+  for (int j = 0; j < D; ++j) o[1 + j] = u[1 + j] - (T)2 * mn * n[j];
+  o[D + 1] = u[D + 1];
+}
+
 template <int D, typename T>
 __device__ __forceinline__ void physical_flux(const T *u, const T *n, T p, T un, T *F) {
   F[0] = u[0] * un;
@@ -220,6 +234,101 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// Residual (eq. 2) and stage update in FP64, the FP32 shadow of the new state and, at the last
+// stage, the cell's CFL step of the next step: the common end of the per-cell flux kernels. u64:
+// the cell's current state, acc: sum_f |A_f| sum_q w_q F_q. Runge-Kutta (Sec. 2, "3rd- or
+// 4th-order"): SSP-RK3 in Shu-Osher form, U1 = U^n + dt R, U2 = 3/4 U^n + 1/4 (U1 + dt R(U1)),
+// U^{n+1} = 1/3 U^n + 2/3 (U2 + dt R(U2)); or the classical RK4 with its running sum in Acc:
+// Acc = U^n + dt/6 k1, U = U^n + dt/2 k1; Acc += dt/3 k2, U = U^n + dt/2 k2; Acc += dt/3 k3,
+// U = U^n + dt k3; U^{n+1} = Acc + dt/6 k4.
+template <int D, typename T>
+__device__ __forceinline__ void stage_tail(const KArgs &a, const int64_t i, const bool active,
+                                           const double (&u64)[Lay<D>::NVP], const double (&acc)[Lay<D>::NV]) {
+  using L = Lay<D>;
+  constexpr int NV = L::NV, NVP = L::NVP;
+  constexpr bool F32 = sizeof(T) == 4;
+  const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
+  const double dtv = a.dt[mesh] * a.vol[i];  // dt / |V_i|
+  double un[NVP], res[NVP], ac[NVP];
+  if (a.stage != 0) {
+#pragma unroll
+    for (int c = 0; c < NVP / 2; ++c) {
+      const double2 x = reinterpret_cast<const double2 *>(a.Un + i * NVP)[c];
+      un[2 * c] = x.x;
+      un[2 * c + 1] = x.y;
+    }
+  }
+  if (a.rk4 && a.stage != 0) {
+#pragma unroll
+    for (int c = 0; c < NVP / 2; ++c) {
+      const double2 x = reinterpret_cast<const double2 *>(a.Acc + i * NVP)[c];
+      ac[2 * c] = x.x;
+      ac[2 * c + 1] = x.y;
+    }
+  }
+  bool finite = true;
+#pragma unroll
+  for (int v = 0; v < NVP; ++v) {
+    if (v >= NV) {
+      res[v] = 0.0;
+      ac[v] = 0.0;
+      continue;
+    }
+    if (!a.rk4) {
+      const double upd = u64[v] - dtv * acc[v];
+      if (a.stage == 0) res[v] = upd;
+      else if (a.stage == 1) res[v] = 0.75 * un[v] + 0.25 * upd;
+      else res[v] = (1.0 / 3.0) * un[v] + (2.0 / 3.0) * upd;
+    } else {
+      const double F = -dtv * acc[v];  // dt k_s
+      if (a.stage == 0) {
+        ac[v] = u64[v] + F / 6.0;
+        res[v] = u64[v] + 0.5 * F;
+      } else if (a.stage == 1) {
+        ac[v] += F / 3.0;
+        res[v] = un[v] + 0.5 * F;
+      } else if (a.stage == 2) {
+        ac[v] += F / 3.0;
+        res[v] = un[v] + F;
+      } else {
+        res[v] = ac[v] + F / 6.0;
+      }
+    }
+    finite = finite && finite64(res[v]);
+  }
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < NVP / 2; ++c) {
+      reinterpret_cast<double2 *>(a.U + i * NVP)[c] = make_double2(res[2 * c], res[2 * c + 1]);
+      if (a.stage == 0)
+        reinterpret_cast<double2 *>(a.Un + i * NVP)[c] = make_double2(u64[2 * c], u64[2 * c + 1]);
+      if (a.rk4 && a.stage < 3)
+        reinterpret_cast<double2 *>(a.Acc + i * NVP)[c] = make_double2(ac[2 * c], ac[2 * c + 1]);
+    }
+  }
+  T ust[NVP];  // the new state in the path's type, for the CFL step
+  if constexpr (F32) {  // FP32 (hi, lo) shadow of the new state
+    float4 hl[NVP / 2];
+#pragma unroll
+    for (int c = 0; c < NVP / 2; ++c) {
+      const float2 s0 = f64_split(res[2 * c]), s1 = f64_split(res[2 * c + 1]);
+      hl[c] = make_float4(s0.x, s0.y, s1.x, s1.y);
+      ust[2 * c] = s0.x;
+      ust[2 * c + 1] = s1.x;
+    }
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < NVP / 2; ++c) reinterpret_cast<float4 *>(a.U32 + i * 2 * NVP)[c] = hl[c];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NVP; ++v) ust[v] = res[v];
+  }
+  if (!finite && active) atomicOr(a.err, kErrNonFinite);
+  if (a.stage == a.last_stage)
+    warp_min_to(a.dt, a.nmesh + mesh, (finite && active) ? a.cfl * local_dt<D, T>(a, i, ust) : 1e300);
+}
+
 template <int D, typename T, int MINB, int NQ>
 __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel(const KArgs a) {
   using L = Lay<D>;
@@ -270,6 +379,9 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
       load16<T, FB>(Uf + (i * NF + f) * FB, uI[ff]);
       if (j >= 0) {
         load16<T, FB>(Uf + (j * NF + fj) * FB, uO[ff]);
+      } else if ((meta >> (kMetaWallShift + f)) & 1u) {  // reflective wall: the mirror image
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) wall_mirror<D, T>(uI[ff] + q * NV, gf[ff], uO[ff] + q * NV);
       } else {  // transmissive boundary: the cell mean outside
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
@@ -318,60 +430,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = f32_to_f64(acc_hi[v]) + f32_to_f64(acc_lo[v]);
   }
-  // residual and SSP-RK3 (Shu-Osher) stage update in FP64
-  const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
-  const double dtv = a.dt[mesh] * a.vol[i];  // dt / |V_i|
-  double un[NVP], res[NVP];
-  if (a.stage != 0) {
-#pragma unroll
-    for (int c = 0; c < NVP / 2; ++c) {
-      const double2 x = reinterpret_cast<const double2 *>(a.Un + i * NVP)[c];
-      un[2 * c] = x.x;
-      un[2 * c + 1] = x.y;
-    }
-  }
-  bool finite = true;
-#pragma unroll
-  for (int v = 0; v < NVP; ++v) {
-    if (v >= NV) {
-      res[v] = 0.0;
-      continue;
-    }
-    const double upd = u64[v] - dtv * acc[v];
-    if (a.stage == 0) res[v] = upd;
-    else if (a.stage == 1) res[v] = 0.75 * un[v] + 0.25 * upd;
-    else res[v] = (1.0 / 3.0) * un[v] + (2.0 / 3.0) * upd;
-    finite = finite && finite64(res[v]);
-  }
-  if (active) {
-#pragma unroll
-    for (int c = 0; c < NVP / 2; ++c) {
-      reinterpret_cast<double2 *>(a.U + i * NVP)[c] = make_double2(res[2 * c], res[2 * c + 1]);
-      if (a.stage == 0)
-        reinterpret_cast<double2 *>(a.Un + i * NVP)[c] = make_double2(u64[2 * c], u64[2 * c + 1]);
-    }
-  }
-  T ust[NVP];  // the new state in the path's type, for the CFL step
-  if constexpr (F32) {  // FP32 (hi, lo) shadow of the new state
-    float4 hl[NVP / 2];
-#pragma unroll
-    for (int c = 0; c < NVP / 2; ++c) {
-      const float2 s0 = f64_split(res[2 * c]), s1 = f64_split(res[2 * c + 1]);
-      hl[c] = make_float4(s0.x, s0.y, s1.x, s1.y);
-      ust[2 * c] = s0.x;
-      ust[2 * c + 1] = s1.x;
-    }
-    if (active) {
-#pragma unroll
-      for (int c = 0; c < NVP / 2; ++c) reinterpret_cast<float4 *>(a.U32 + i * 2 * NVP)[c] = hl[c];
-    }
-  } else {
-#pragma unroll
-    for (int v = 0; v < NVP; ++v) ust[v] = res[v];
-  }
-  if (!finite && active) atomicOr(a.err, kErrNonFinite);
-  if (a.stage == 2)
-    warp_min_to(a.dt, a.nmesh + mesh, (finite && active) ? a.cfl * local_dt<D, T>(a, i, ust) : 1e300);
+  stage_tail<D, T>(a, i, active, u64, acc);
 }
 
 // Face flux of the face-based schedule: one thread per face, HLLC at the face's Gauss points in
@@ -400,6 +459,9 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const KArgs a) {
     const int64_t j = codes.y >> 2;
     const int fj = codes.y & 3;
     load16<T, FB>(Uf + (j * NF + fj) * FB, uO);
+  } else if ((__ldg(a.fmeta + i) >> (kMetaWallShift + f)) & 1u) {  // reflective wall: the mirror image
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) wall_mirror<D, T>(uI + q * NV, gf, uO + q * NV);
   } else {  // transmissive boundary: the cell mean outside
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -485,60 +547,7 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) cell_update
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = f32_to_f64(acc_hi[v]) + f32_to_f64(acc_lo[v]);
   }
-  // residual and SSP-RK3 (Shu-Osher) stage update in FP64
-  const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
-  const double dtv = a.dt[mesh] * a.vol[i];  // dt / |V_i|
-  double un[NVP], res[NVP];
-  if (a.stage != 0) {
-#pragma unroll
-    for (int c = 0; c < NVP / 2; ++c) {
-      const double2 x = reinterpret_cast<const double2 *>(a.Un + i * NVP)[c];
-      un[2 * c] = x.x;
-      un[2 * c + 1] = x.y;
-    }
-  }
-  bool finite = true;
-#pragma unroll
-  for (int v = 0; v < NVP; ++v) {
-    if (v >= NV) {
-      res[v] = 0.0;
-      continue;
-    }
-    const double upd = u64[v] - dtv * acc[v];
-    if (a.stage == 0) res[v] = upd;
-    else if (a.stage == 1) res[v] = 0.75 * un[v] + 0.25 * upd;
-    else res[v] = (1.0 / 3.0) * un[v] + (2.0 / 3.0) * upd;
-    finite = finite && finite64(res[v]);
-  }
-  if (active) {
-#pragma unroll
-    for (int c = 0; c < NVP / 2; ++c) {
-      reinterpret_cast<double2 *>(a.U + i * NVP)[c] = make_double2(res[2 * c], res[2 * c + 1]);
-      if (a.stage == 0)
-        reinterpret_cast<double2 *>(a.Un + i * NVP)[c] = make_double2(u64[2 * c], u64[2 * c + 1]);
-    }
-  }
-  T ust[NVP];  // the new state in the path's type, for the CFL step
-  if constexpr (F32) {  // FP32 (hi, lo) shadow of the new state
-    float4 hl[NVP / 2];
-#pragma unroll
-    for (int c = 0; c < NVP / 2; ++c) {
-      const float2 s0 = f64_split(res[2 * c]), s1 = f64_split(res[2 * c + 1]);
-      hl[c] = make_float4(s0.x, s0.y, s1.x, s1.y);
-      ust[2 * c] = s0.x;
-      ust[2 * c + 1] = s1.x;
-    }
-    if (active) {
-#pragma unroll
-      for (int c = 0; c < NVP / 2; ++c) reinterpret_cast<float4 *>(a.U32 + i * 2 * NVP)[c] = hl[c];
-    }
-  } else {
-#pragma unroll
-    for (int v = 0; v < NVP; ++v) ust[v] = res[v];
-  }
-  if (!finite && active) atomicOr(a.err, kErrNonFinite);
-  if (a.stage == 2)
-    warp_min_to(a.dt, a.nmesh + mesh, (finite && active) ? a.cfl * local_dt<D, T>(a, i, ust) : 1e300);
+  stage_tail<D, T>(a, i, active, u64, acc);
 }
 
 }  // namespace

@@ -38,6 +38,9 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
   load16<T, FB>(Uf + (i * NF + f) * FB, uI);
   if (j >= 0) {
     load16<T, FB>(Uf + (j * NF + fj) * FB, uO);
+  } else if ((meta >> (kMetaWallShift + f)) & 1u) {  // reflective wall: the mirror image
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) wall_mirror<D, T>(uI + q * NV, gf, uO + q * NV);
   } else {  // transmissive boundary: the cell mean outside
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -92,22 +95,39 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
     if (v % NF == f) {  // FP64 work only in the lane that updates variable v
       if constexpr (F32) acc = f32_to_f64(hi) + f32_to_f64(lo);
       const double u = a.U[i * NVP + v];
-      const double upd = u - dtv * acc;
-      double r;
-      if (a.stage == 0) r = upd;
-      else if (a.stage == 1) r = 0.75 * a.Un[i * NVP + v] + 0.25 * upd;
-      else r = (1.0 / 3.0) * a.Un[i * NVP + v] + (2.0 / 3.0) * upd;
+      double r, s4 = 0.0;
+      if (!a.rk4) {  // SSP-RK3 (Shu-Osher), as stage_tail
+        const double upd = u - dtv * acc;
+        if (a.stage == 0) r = upd;
+        else if (a.stage == 1) r = 0.75 * a.Un[i * NVP + v] + 0.25 * upd;
+        else r = (1.0 / 3.0) * a.Un[i * NVP + v] + (2.0 / 3.0) * upd;
+      } else {       // classical RK4 with its running sum, as stage_tail
+        const double F = -dtv * acc;
+        if (a.stage == 0) {
+          s4 = u + F / 6.0;
+          r = u + 0.5 * F;
+        } else if (a.stage == 1) {
+          s4 = a.Acc[i * NVP + v] + F / 3.0;
+          r = a.Un[i * NVP + v] + 0.5 * F;
+        } else if (a.stage == 2) {
+          s4 = a.Acc[i * NVP + v] + F / 3.0;
+          r = a.Un[i * NVP + v] + F;
+        } else {
+          r = a.Acc[i * NVP + v] + F / 6.0;
+        }
+      }
       res[v] = r;
       finite = finite && finite64(r);
       if (active) {
         if (a.stage == 0) a.Un[i * NVP + v] = u;
+        if (a.rk4 && a.stage < 3) a.Acc[i * NVP + v] = s4;
         a.U[i * NVP + v] = r;
         if (a.U32) reinterpret_cast<float2 *>(a.U32)[i * NVP + v] = f64_split(r);
       }
     }
   }
   if (!finite && active) atomicOr(a.err, kErrNonFinite);
-  if (a.stage == 2) {  // CFL step of the next step: lane 0 of the group collects the new state
+  if (a.stage == a.last_stage) {  // CFL step of the next step: lane 0 of the group collects the new state
     double full[NVP];
 #pragma unroll
     for (int v = 0; v < NVP; ++v) full[v] = 0.0;

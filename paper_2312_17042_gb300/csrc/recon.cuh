@@ -619,24 +619,16 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) recon_kerne
 // neighbour's record are split over the group. A warp holds floor(32 / NV) cells; spare lanes
 // and lanes past the last cell work on a clamped cell and store nothing.
 // ---------------------------------------------------------------------------------------------
-// The second half of the variable-per-lane schedule, from the central coefficients ao and the
-// directional coefficients ad of variable v (inadmissible stencils hold zeros): p_1 (eq. 17), the
-// smoothness indicators (eq. 15), the selection (eqs. 19-23, Alg. 1 / 2), the final coefficients,
-// and the values at the face Gauss points with the positivity guard (every lane of the warp calls
-// it: the guard exchanges rho, momentum and E of each point by shuffles).
-template <int D, int R, typename T, int SCHEME>
-__device__ __forceinline__ void lane_finish(const KArgs &a, const int64_t i, const bool active, const int v,
-                                            const int base, T (&ao)[Shape<D, R>::NK],
-                                            const T (&ad)[Lay<D>::NF][D], const uint32_t info, const T U0,
-                                            const float L0, const T *__restrict__ sPhi) {
-  using S = Shape<D, R>;
-  using L = Lay<D>;
-  constexpr int NV = L::NV, NF = L::NF, NQ = L::NQ;
-  constexpr int NK = S::NK, NP = S::NP;
+// The selection step of the variable-per-lane schedules for one variable (or characteristic
+// field) of one cell, from its central coefficients ao (K-1) and directional coefficients ad
+// (KD per face; inadmissible stencils hold zeros): p_1 (eq. 17, in place of a_opt), the smoothness
+// indicators (eq. 15: oc(k * NK + l) the upper triangle of the central O, off-diagonal doubled;
+// sid(ad_f) a directional indicator), the selection (eqs. 19-23, Alg. 1 / 2) or the CWENO weights
+// (eq. 14), and the final coefficients in ao. Returns the flags byte.
+template <int NF, int NK, int KD, typename T, int SCHEME, typename OC, typename SID>
+__device__ __forceinline__ uint32_t lane_select(const KArgs &a, const uint32_t adm, T (&ao)[NK],
+                                                const T (&ad)[NF][KD], OC oc, SID sid) {
   constexpr bool F32 = sizeof(T) == 4;
-  const int64_t N = a.N;
-  const uint32_t adm = (info >> kInfoAdmShift) & 0xFu;
-  // p_1, smoothness indicators, selection (eqs. 15-23), final coefficients in ao
   const int stn = 1 + __popc(adm);
   T lams;
   double lamsd = 0.0;
@@ -649,115 +641,275 @@ __device__ __forceinline__ void lane_finish(const KArgs &a, const int64_t i, con
     lamsd = pick<NF>(a.lams_d, stn - 1);
     lams = lamsd;
   }
-  constexpr T INV_FACT = (D == 2) ? (T)0.5 : (T)(1.0 / 6.0);
-  {
-    T a1[NK];
+  if (stn > 1 && a.central_split) {  // TENO keeps p_opt (Sec. 2.4)
 #pragma unroll
-    for (int k = 0; k < NK; ++k) a1[k] = ao[k];
-    if (stn > 1 && a.central_split) {  // TENO keeps p_opt (Sec. 2.4)
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        T s = (T)0;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) s += ad[f][k];
-        a1[k] -= lams * s;
-      }
-      T inv_lam1;
-      if constexpr (F32) inv_lam1 = a.inv_lam1_32; else inv_lam1 = a.inv_lam1;
-#pragma unroll
-      for (int k = 0; k < NK; ++k) a1[k] *= inv_lam1;
-    }
-    T SI0 = (T)0;
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-      T rr = (T)0;
-#pragma unroll
-      for (int l = k; l < NK; ++l) rr += cO<T, R>(k * NK + l) * a1[l];
-      SI0 += a1[k] * rr;
-    }
-    T SId[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
+    for (int k = 0; k < KD; ++k) {
       T s = (T)0;
 #pragma unroll
-      for (int k = 0; k < D; ++k) s += ad[f][k] * ad[f][k];
-      SId[f] = s * INV_FACT;
+      for (int f = 0; f < NF; ++f) s += ad[f][k];
+      ao[k] -= lams * s;
     }
-    uint32_t bits;
-    if (a.cweno) {  // CWENO (Sec. 2.3): every stencil, with the weights of eq. 14
-      T w0, wd[NF];
-      if constexpr (F32) cweno_weights<NF>(SI0, SId, adm, a.log2_lam1, log2lams, a.eps32, w0, wd);
-      else cweno_weights<NF>(SI0, SId, adm, a.lam1, lamsd, a.eps, w0, wd);
+    T inv_lam1;
+    if constexpr (F32) inv_lam1 = a.inv_lam1_32; else inv_lam1 = a.inv_lam1;
 #pragma unroll
-      for (int k = 0; k < NK; ++k) ao[k] = w0 * a1[k];
+    for (int k = 0; k < NK; ++k) ao[k] *= inv_lam1;
+  }
+  T SI0 = (T)0;
+#pragma unroll
+  for (int k = 0; k < NK; ++k) {
+    T rr = (T)0;
+#pragma unroll
+    for (int l = k; l < NK; ++l) rr += oc(k * NK + l) * ao[l];
+    SI0 += ao[k] * rr;
+  }
+  T SId[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) SId[f] = sid(ad[f]);
+  uint32_t bits;
+  if (a.cweno) {  // CWENO (Sec. 2.3): every stencil, with the weights of eq. 14
+    T w0, wd[NF];
+    if constexpr (F32) cweno_weights<NF>(SI0, SId, adm, a.log2_lam1, log2lams, a.eps32, w0, wd);
+    else cweno_weights<NF>(SI0, SId, adm, a.lam1, lamsd, a.eps, w0, wd);
+#pragma unroll
+    for (int k = 0; k < NK; ++k) ao[k] *= w0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int k = 0; k < KD; ++k) ao[k] += wd[f] * ad[f][k];  // zero weight where inadmissible
+    bits = 1u | (adm << 1);
+  } else {
+    if constexpr (F32) {
+      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.log2_lam1, log2lams,
+                             inv_stm1, a.eps32, a.C_T32);
+    } else {
+      bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
+    }
+    if (!(bits & 1u)) {  // the mean of the selected directional polynomials
+      const T w = (T)1 / (T)__popc(bits >> 1);
+#pragma unroll
+      for (int k = 0; k < NK; ++k) ao[k] = (T)0;
 #pragma unroll
       for (int f = 0; f < NF; ++f)
+        if ((bits >> (1 + f)) & 1u) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) ao[k] += wd[f] * ad[f][k];  // zero weight where inadmissible
-      bits = 1u | (adm << 1);
+          for (int k = 0; k < KD; ++k) ao[k] += w * ad[f][k];
+        }
     } else {
-      if constexpr (F32) {
-        bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.log2_lam1, log2lams,
-                               inv_stm1, a.eps32, a.C_T32);
-      } else {
-        bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
-      }
-      if (bits & 1u) {
-#pragma unroll
-        for (int k = 0; k < NK; ++k) ao[k] = a1[k];
-      } else {
-        const T w = (T)1 / (T)__popc(bits >> 1);
-#pragma unroll
-        for (int k = 0; k < NK; ++k) ao[k] = (T)0;
-#pragma unroll
-        for (int f = 0; f < NF; ++f)
-          if ((bits >> (1 + f)) & 1u) {
-#pragma unroll
-            for (int k = 0; k < D; ++k) ao[k] += w * ad[f][k];
-          }
-      }
-      if (bits & 1u) bits = 1u;
+      bits = 1u;
     }
-    if (a.flags && active) a.flags[v * N + i] = (uint8_t)bits;
   }
+  return bits;
+}
 
-  // face values of variable v; the positivity guard gathers rho, momentum and E of each point
-  // from the group's lanes
+// Positivity test of a face-point state from the group's lanes (not part of the paper): rho > 0
+// and p > 0, the latter as rho E - |m|^2 / 2 > 0 on the mixed path (no division).
+template <int D, typename T>
+__device__ __forceinline__ bool lane_point_bad(const KArgs &a, const T val, const int base) {
+  constexpr int NV = D + 2;
+  const T rho = __shfl_sync(0xffffffffu, val, base);
+  const T E = __shfl_sync(0xffffffffu, val, base + NV - 1);
+  T ke = (T)0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const T m = __shfl_sync(0xffffffffu, val, base + 1 + j);
+    ke += m * m;
+  }
+  if constexpr (sizeof(T) == 4) {
+    return !(rho > 0.0f) || !(rho * E - 0.5f * ke > 0.0f);
+  } else {
+    const T pr = (T)(a.gamma - 1.0) * (E - (T)0.5 * ke / rho);
+    return !(rho > (T)0) || !(pr > (T)0);
+  }
+}
+
+// Eigenvectors of the Euler flux Jacobian in the unit direction n at the mean state ub (the
+// characteristic decomposition of Sec. 2.2 / 3.2): row w of L and row v of R, for the fields in the
+// order u_n - c, u_n (entropy), u_n (shear, one per tangent), u_n + c. With H = (E + p)/rho,
+// q^2 = |u|^2, b1 = (gamma - 1)/c^2, b2 = b1 q^2/2 the columns of R are (1, u - c n, H - c u_n),
+// (1, u, q^2/2), (0, t_j, u.t_j), (1, u + c n, H + c u_n), and the rows of L = R^-1 are
+// (b2 + u_n/c, -b1 u - n/c, b1)/2, (1 - b2, b1 u, -b1), (-u.t_j, t_j, 0),
+// (b2 - u_n/c, -b1 u + n/c, b1)/2. Tangents: (-n_y, n_x) in 2D; in 3D t_1 is the axis along which
+// |n| is smallest made orthogonal to n and normalised, t_2 = n x t_1.
+template <int D, typename T>
+__device__ __forceinline__ void euler_eigen_rows(const T (&ub)[D + 2], const T (&n)[D], const T gm1, const int w,
+                                                 T (&Lw)[D + 2], T (&Rw)[D + 2]) {
+  constexpr int NV = D + 2;
+  const T rho = ub[0], irho = (T)1 / rho;
+  T vel[D], q2 = (T)0, un = (T)0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    vel[j] = ub[1 + j] * irho;
+    q2 += vel[j] * vel[j];
+    un += vel[j] * n[j];
+  }
+  const T p = gm1 * (ub[NV - 1] - (T)0.5 * rho * q2);
+  const T c2 = (gm1 + (T)1) * p * irho, c = sqrt(c2), ic = (T)1 / c;
+  const T H = (ub[NV - 1] + p) * irho, b1 = gm1 / c2, b2 = (T)0.5 * b1 * q2;
+  T t[D - 1][D];
+  if constexpr (D == 2) {
+    t[0][0] = -n[1];
+    t[0][1] = n[0];
+  } else {
+    int ax = 0;
+    if (fabs(n[1]) < fabs(n[ax])) ax = 1;
+    if (fabs(n[2]) < fabs(n[ax])) ax = 2;
+    const T na = (ax == 0) ? n[0] : (ax == 1) ? n[1] : n[2];
+    T len = (T)0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      t[0][j] = (j == ax ? (T)1 : (T)0) - na * n[j];
+      len += t[0][j] * t[0][j];
+    }
+    const T il = (T)1 / sqrt(len);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) t[0][j] *= il;
+    t[1][0] = n[1] * t[0][2] - n[2] * t[0][1];
+    t[1][1] = n[2] * t[0][0] - n[0] * t[0][2];
+    t[1][2] = n[0] * t[0][1] - n[1] * t[0][0];
+  }
+  T ut[D - 1];
+#pragma unroll
+  for (int m = 0; m < D - 1; ++m) {
+    ut[m] = (T)0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) ut[m] += vel[j] * t[m][j];
+  }
+  // row w of L
+  if (w == 0 || w == NV - 1) {
+    const T sg = (w == 0) ? (T)1 : (T)-1;
+    Lw[0] = (T)0.5 * (b2 + sg * un * ic);
+#pragma unroll
+    for (int j = 0; j < D; ++j) Lw[1 + j] = (T)0.5 * (-b1 * vel[j] - sg * n[j] * ic);
+    Lw[NV - 1] = (T)0.5 * b1;
+  } else if (w == 1) {
+    Lw[0] = (T)1 - b2;
+#pragma unroll
+    for (int j = 0; j < D; ++j) Lw[1 + j] = b1 * vel[j];
+    Lw[NV - 1] = -b1;
+  } else {
+#pragma unroll
+    for (int m = 0; m < D - 1; ++m)
+      if (w == 2 + m) {
+        Lw[0] = -ut[m];
+#pragma unroll
+        for (int j = 0; j < D; ++j) Lw[1 + j] = t[m][j];
+        Lw[NV - 1] = (T)0;
+      }
+  }
+  // row w of R (variable w, all fields)
+  if (w == 0) {
+    Rw[0] = (T)1;
+    Rw[1] = (T)1;
+#pragma unroll
+    for (int m = 0; m < D - 1; ++m) Rw[2 + m] = (T)0;
+    Rw[NV - 1] = (T)1;
+  } else if (w == NV - 1) {
+    Rw[0] = H - c * un;
+    Rw[1] = (T)0.5 * q2;
+#pragma unroll
+    for (int m = 0; m < D - 1; ++m) Rw[2 + m] = ut[m];
+    Rw[NV - 1] = H + c * un;
+  } else {
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+      if (w == 1 + j) {
+        Rw[0] = vel[j] - c * n[j];
+        Rw[1] = vel[j];
+#pragma unroll
+        for (int m = 0; m < D - 1; ++m) Rw[2 + m] = t[m][j];
+        Rw[NV - 1] = vel[j] + c * n[j];
+      }
+  }
+}
+
+// The face values of the variable-per-lane schedules after the selection, from each lane's final
+// coefficients ao of variable v: U_0 + sum_k phi_k a_k at every face Gauss point (phi(f, q, k)),
+// the positivity guard over the group, and the stores in the canonical point order. Conserved
+// variables (the selection done by the caller) or, with a.characteristic, the characteristic
+// reconstruction (CHR; a compile-time switch, so that the other schedules keep their registers):
+// for each face, lane v takes field w = v of W = L U (L from the cell's mean and the face's outward
+// normal), projects the conserved coefficients by shuffles (the least squares are linear in the
+// data), selects, evaluates W at the face's points and transforms back, U = R W.
+template <int D, int NK, int KD, int NQ, typename T, int SCHEME, bool CHR, typename OC, typename SID,
+          typename PHI>
+__device__ __forceinline__ void lane_faces(const KArgs &a, const int64_t i, const bool active, const int v,
+                                           const int base, T (&ao)[NK], const T (&ad)[D + 1][KD],
+                                           const uint32_t info, const T U0, const float L0, OC oc, SID sid,
+                                           PHI phi) {
+  constexpr int NV = D + 2, NF = D + 1;
+  constexpr bool F32 = sizeof(T) == 4;
+  const int64_t N = a.N;
+  const uint32_t adm = (info >> kInfoAdmShift) & 0xFu;
   T *__restrict__ Ufi = (T *)a.Uf + i * (int64_t)(NF * NQ * NV);
   const uint32_t perm = info >> kInfoPermShift;
-  T gm1;
-  if constexpr (F32) gm1 = a.gm1_32; else gm1 = a.gamma - 1.0;
   bool bad = false;
   T fv[NF][NQ];
+  if constexpr (!CHR) {
+    const uint32_t bits = lane_select<NF, NK, KD, T, SCHEME>(a, adm, ao, ad, oc, sid);
+    if (a.flags && active) a.flags[v * N + i] = (uint8_t)bits;
 #pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const int p = (perm >> (3 * f)) & 7u;
+    for (int f = 0; f < NF; ++f)
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      T val = (T)L0;
-      if constexpr (D == 2) {
+      for (int q = 0; q < NQ; ++q) {
+        T val = (T)L0;
 #pragma unroll
-        for (int k = 0; k < NK; ++k) val += cPhi2<T, R>((f * 2 + q) * NK + k) * ao[k];
-      } else {
-        const T *ph = &sPhi[((f * NP + p) * NQ + q) * NK];
-#pragma unroll
-        for (int k = 0; k < NK; ++k) val += ph[k] * ao[k];
+        for (int k = 0; k < NK; ++k) val += phi(f, q, k) * ao[k];
+        val += U0;
+        fv[f][q] = val;
+        // every lane takes part in the test's shuffles (no short-circuit before it)
+        const bool pb = lane_point_bad<D, T>(a, val, base);
+        bad = bad || pb;
       }
-      val += U0;
-      fv[f][q] = val;
-      const T rho = __shfl_sync(0xffffffffu, val, base);
-      const T E = __shfl_sync(0xffffffffu, val, base + NV - 1);
-      T ke = (T)0;
+  } else {
+    T gm1;
+    if constexpr (F32) gm1 = a.gm1_32; else gm1 = (T)(a.gamma - 1.0);
+    T ub[NV];
+    const T mean = U0 + (T)L0;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) ub[j] = __shfl_sync(0xffffffffu, mean, base + j);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      T n[D];
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        const T m = __shfl_sync(0xffffffffu, val, base + 1 + j);
-        ke += m * m;
+        if constexpr (F32) n[j] = __ldg(a.geo32 + (i * NF + f) * 4 + j);
+        else n[j] = __ldg(a.geo + (i * NF + f) * 4 + j);
       }
-      if constexpr (F32) {  // rho > 0 and p > 0, the latter as rho E - |m|^2 / 2 > 0 (no division)
-        bad = bad || !(rho > 0.0f) || !(rho * E - 0.5f * ke > 0.0f);
-      } else {
-        const T pr = gm1 * (E - (T)0.5 * ke / rho);
-        bad = bad || !(rho > (T)0) || !(pr > (T)0);
+      T Lw[NV], Rv[NV];
+      euler_eigen_rows<D, T>(ub, n, gm1, v, Lw, Rv);
+      T aw[NK], adw[NF][KD];
+#pragma unroll
+      for (int k = 0; k < NK; ++k) {
+        T s = (T)0;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) s += Lw[j] * __shfl_sync(0xffffffffu, ao[k], base + j);
+        aw[k] = s;
+      }
+#pragma unroll
+      for (int g = 0; g < NF; ++g)
+#pragma unroll
+        for (int k = 0; k < KD; ++k) {
+          T s = (T)0;
+#pragma unroll
+          for (int j = 0; j < NV; ++j) s += Lw[j] * __shfl_sync(0xffffffffu, ad[g][k], base + j);
+          adw[g][k] = s;
+        }
+      T wbar = (T)0;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) wbar += Lw[j] * ub[j];
+      const uint32_t bits = lane_select<NF, NK, KD, T, SCHEME>(a, adm, aw, adw, oc, sid);
+      if (a.flags && active) a.flags[(f * NV + v) * N + i] = (uint8_t)bits;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        T W = wbar;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) W += phi(f, q, k) * aw[k];
+        T val = (T)0;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) val += Rv[j] * __shfl_sync(0xffffffffu, W, base + j);
+        fv[f][q] = val;
+        const bool pb = lane_point_bad<D, T>(a, val, base);  // every lane shuffles
+        bad = bad || pb;
       }
     }
   }
@@ -782,12 +934,44 @@ __device__ __forceinline__ void lane_finish(const KArgs &a, const int64_t i, con
   }
 }
 
+// The second half of the variable-per-lane schedule (degrees 2 and 3), from the central
+// coefficients ao and the directional coefficients ad of variable v: selection and face values
+// (lane_select, lane_faces). Every lane of the warp calls it (the guard and the characteristic
+// projection exchange values by shuffles).
+template <int D, int R, typename T, int SCHEME, bool CHR = false>
+__device__ __forceinline__ void lane_finish(const KArgs &a, const int64_t i, const bool active, const int v,
+                                            const int base, T (&ao)[Shape<D, R>::NK],
+                                            const T (&ad)[Lay<D>::NF][D], const uint32_t info, const T U0,
+                                            const float L0, const T *__restrict__ sPhi) {
+  using S = Shape<D, R>;
+  using L = Lay<D>;
+  constexpr int NK = S::NK, NP = S::NP, NQ = L::NQ;
+  constexpr T INV_FACT = (D == 2) ? (T)0.5 : (T)(1.0 / 6.0);
+  const uint32_t perm = info >> kInfoPermShift;
+  auto oc = [](int idx) { return cO<T, R>(idx); };
+  auto sid = [&](const T (&adf)[D]) {  // the linear block of O is |V0'| I
+    T s = (T)0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) s += adf[k] * adf[k];
+    return s * INV_FACT;
+  };
+  auto phi = [&](int f, int q, int k) -> T {
+    if constexpr (D == 2) {
+      return cPhi2<T, R>((f * 2 + q) * NK + k);
+    } else {
+      const int p = (perm >> (3 * f)) & 7u;
+      return sPhi[((f * NP + p) * NQ + q) * NK + k];
+    }
+  };
+  lane_faces<D, NK, D, NQ, T, SCHEME, CHR>(a, i, active, v, base, ao, ad, info, U0, L0, oc, sid, phi);
+}
+
 // One cell of the variable-per-lane schedule, seen from lane v of its group (first lane base);
 // every lane of the warp calls it (inactive lanes with a clamped valid cell i) because the
 // positivity guard exchanges values with shuffles. Operator pointers as for recon_cell. HALO:
 // sti holds the cell's uint16 local indices (members, then the cell itself) into `halo`, the
 // shared-memory FP32 (hi, lo) records of its tile's distinct stencil members.
-template <int D, int R, typename T, int SCHEME, bool SH, bool HALO = false>
+template <int D, int R, typename T, int SCHEME, bool SH, bool HALO = false, bool CHR = false>
 __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, const bool active, const int v,
                                            const int base, const T *__restrict__ Pci,
                                            const T *__restrict__ Pdi, const void *__restrict__ sti_,
@@ -892,10 +1076,10 @@ __device__ __forceinline__ void recon_lane(const KArgs &a, const int64_t i, cons
       off += nm;
     }
   }
-  lane_finish<D, R, T, SCHEME>(a, i, active, v, base, ao, ad, info, U0, L0, sPhi);
+  lane_finish<D, R, T, SCHEME, CHR>(a, i, active, v, base, ao, ad, info, U0, L0, sPhi);
 }
 
-template <int D, int R, typename T, int SCHEME>
+template <int D, int R, typename T, int SCHEME, bool CHR = false>
 __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
   using S = Shape<D, R>;
   using L = Lay<D>;
@@ -922,7 +1106,7 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
   const bool active = grp < CPW && cell < N;
   const int64_t i = active ? cell : N - 1;  // spare lanes shadow a valid cell
 
-  recon_lane<D, R, T, SCHEME, false>(a, i, active, v, base, (const T *)a.Pc + i * (int64_t)(M * NK),
+  recon_lane<D, R, T, SCHEME, false, false, CHR>(a, i, active, v, base, (const T *)a.Pc + i * (int64_t)(M * NK),
                                      (const T *)a.Pd + i * (int64_t)(NF * PDS), a.st + i * M, sPhi);
   if (a.dt_swap && blockIdx.x == 0)
     for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {

@@ -8,7 +8,9 @@ cudaError_t launch_recon_2d_high(int degree, int fp32, int scheme, const KArgs &
   const int threads = block - kLaneSchedule;
   const int64_t cells_per_block = (int64_t)(threads / 32) * 8;
   const unsigned grid = (unsigned)((a.N + cells_per_block - 1) / cells_per_block);
-#define CTENO_HIGH(R, T, SC) launch_stage_kernel(recon_high_kernel<R, T, SC>, grid, threads, 0, s, a)
+#define CTENO_HIGH(R, T, SC)                                                              \
+  (a.characteristic ? launch_stage_kernel(recon_high_kernel<R, T, SC, true>, grid, threads, 0, s, a) \
+                    : launch_stage_kernel(recon_high_kernel<R, T, SC, false>, grid, threads, 0, s, a))
   if (degree == 4 && fp32 && scheme == 0) CTENO_HIGH(4, float, 0);
   if (degree == 4 && fp32 && scheme == 1) CTENO_HIGH(4, float, 1);
   if (degree == 5 && fp32 && scheme == 0) CTENO_HIGH(5, float, 0);

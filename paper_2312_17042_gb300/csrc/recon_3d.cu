@@ -4,6 +4,8 @@
 namespace cteno {
 
 cudaError_t launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s) {
+  // the characteristic reconstruction runs in the variable-per-lane schedule only
+  if (a.characteristic && !(block >= kLaneSchedule && block < kStagedCells)) return cudaErrorInvalidValue;
   if (block == kHaloLanes || block == kHaloLanes + 1) {  // gather-staged lane schedule (mixed)
     if (!fp32) return cudaErrorInvalidValue;  // mixed path only
     const bool one = block == kHaloLanes + 1;  // one tile per block, single stage
@@ -58,7 +60,9 @@ cudaError_t launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, in
     const int threads = block - kLaneSchedule, cpw = 32 / (3 + 2);
     const int64_t cells_per_block = (int64_t)(threads / 32) * cpw;
     const unsigned grid = (unsigned)((a.N + cells_per_block - 1) / cells_per_block);
-#define CTENO_LANES(R, T, SC) launch_stage_kernel(recon_lanes_kernel<3, R, T, SC>, grid, threads, 0, s, a)
+#define CTENO_LANES(R, T, SC)                                                                   \
+  (a.characteristic ? launch_stage_kernel(recon_lanes_kernel<3, R, T, SC, true>, grid, threads, 0, s, a) \
+                    : launch_stage_kernel(recon_lanes_kernel<3, R, T, SC, false>, grid, threads, 0, s, a))
     if (degree == 2 && fp32 && scheme == 0) CTENO_LANES(2, float, 0);
     if (degree == 2 && fp32 && scheme == 1) CTENO_LANES(2, float, 1);
     if (degree == 3 && fp32 && scheme == 0) CTENO_LANES(3, float, 0);

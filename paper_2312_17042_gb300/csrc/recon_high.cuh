@@ -104,7 +104,7 @@ inline cudaError_t upload_high_tables(const Tables &t, cudaStream_t s) {
 
 // One block of 8-cell warps; lane v of group grp reconstructs variable v of cell 8 w + grp (the
 // last cell shadows the lanes past the end and stores nothing).
-template <int R, typename T, int SCHEME>
+template <int R, typename T, int SCHEME, bool CHR>
 __global__ void __launch_bounds__(256) recon_high_kernel(const KArgs a) {
   using H = HighShape<R>;
   using DR = Dir<2, R>;
@@ -192,133 +192,22 @@ __global__ void __launch_bounds__(256) recon_high_kernel(const KArgs a) {
     }
   }
 
-  // p_1 (eq. 17) in place of a_opt, the smoothness indicators (eq. 15) and the selection
-  const int stn = 1 + __popc(adm);
-  T lams;
-  double lamsd = 0.0;
-  float log2lams = 0.0f, inv_stm1 = 0.0f;
-  if constexpr (F32) {
-    lams = pick<NF>(a.lams_f, stn - 1);
-    log2lams = pick<NF>(a.log2_lams_f, stn - 1);
-    inv_stm1 = pick<NF>(a.inv_stm1_f, stn - 1);
-  } else {
-    lamsd = pick<NF>(a.lams_d, stn - 1);
-    lams = lamsd;
-  }
-  if (stn > 1 && a.central_split) {  // TENO keeps p_opt (Sec. 2.4)
-#pragma unroll
-    for (int k = 0; k < KD; ++k) {
-      T s = (T)0;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) s += ad[f][k];  // inadmissible stencils hold zeros
-      ao[k] -= lams * s;
-    }
-    T inv_lam1;
-    if constexpr (F32) inv_lam1 = a.inv_lam1_32; else inv_lam1 = a.inv_lam1;
-#pragma unroll
-    for (int k = 0; k < NK; ++k) ao[k] *= inv_lam1;
-  }
-  T SI0 = (T)0;
-#pragma unroll
-  for (int k = 0; k < NK; ++k) {
-    T rr = (T)0;
-#pragma unroll
-    for (int l = k; l < NK; ++l) rr += cOH<T, R>(k * NK + l) * ao[l];
-    SI0 += ao[k] * rr;
-  }
-  T SId[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
+  // p_1 (eq. 17) in place of a_opt, the smoothness indicators (eq. 15: a directional one with
+  // the top-left 5 x 5 block of O), the selection or the CWENO weights, the face values
+  auto oc = [](int idx) { return cOH<T, R>(idx); };
+  auto sid = [](const T (&adf)[KD]) {
     T s = (T)0;
 #pragma unroll
     for (int k = 0; k < KD; ++k) {
       T rr = (T)0;
 #pragma unroll
-      for (int l = k; l < KD; ++l) rr += cOH<T, R>(k * NK + l) * ad[f][l];
-      s += ad[f][k] * rr;
+      for (int l = k; l < KD; ++l) rr += cOH<T, R>(k * NK + l) * adf[l];
+      s += adf[k] * rr;
     }
-    SId[f] = s;
-  }
-  uint32_t bits;
-  if (a.cweno) {  // CWENO (Sec. 2.3): every stencil, with the weights of eq. 14
-    T w0, wd[NF];
-    if constexpr (F32) cweno_weights<NF>(SI0, SId, adm, a.log2_lam1, log2lams, a.eps32, w0, wd);
-    else cweno_weights<NF>(SI0, SId, adm, a.lam1, lamsd, a.eps, w0, wd);
-#pragma unroll
-    for (int k = 0; k < NK; ++k) ao[k] *= w0;
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-      for (int k = 0; k < KD; ++k) ao[k] += wd[f] * ad[f][k];  // zero weight where inadmissible
-    bits = 1u | (adm << 1);
-  } else {
-    if constexpr (F32) {
-      bits = select_fp32<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.log2_lam1, log2lams,
-                             inv_stm1, a.eps32, a.C_T32);
-    } else {
-      bits = select_fp64<NF>(SI0, SId, adm, stn, SCHEME, a.ctenoz_form, a.lam_gamma, a.lam1, lamsd, a.eps, a.C_T);
-    }
-    if (!(bits & 1u)) {  // the mean of the selected directional polynomials
-      const T w = (T)1 / (T)__popc(bits >> 1);
-#pragma unroll
-      for (int k = 0; k < NK; ++k) ao[k] = (T)0;
-#pragma unroll
-      for (int f = 0; f < NF; ++f)
-        if ((bits >> (1 + f)) & 1u) {
-#pragma unroll
-          for (int k = 0; k < KD; ++k) ao[k] += w * ad[f][k];
-        }
-    } else {
-      bits = 1u;
-    }
-  }
-  if (a.flags && active) a.flags[v * N + i] = (uint8_t)bits;
-
-  // face values of variable v; the positivity guard gathers rho, momentum and E of each point
-  // from the group's lanes
-  T *__restrict__ Ufi = (T *)a.Uf + i * (int64_t)(NF * NQ * NV);
-  const uint32_t perm = info >> kInfoPermShift;
-  T gm1;
-  if constexpr (F32) gm1 = a.gm1_32; else gm1 = a.gamma - 1.0;
-  bool bad = false;
-  T fv[NF][NQ];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      T val = (T)L0;
-#pragma unroll
-      for (int k = 0; k < NK; ++k) val += cPhiH<T, R>((f * NQ + q) * NK + k) * ao[k];
-      val += U0;
-      fv[f][q] = val;
-      const T rho = __shfl_sync(0xffffffffu, val, base);
-      const T mx = __shfl_sync(0xffffffffu, val, base + 1);
-      const T my = __shfl_sync(0xffffffffu, val, base + 2);
-      const T E = __shfl_sync(0xffffffffu, val, base + 3);
-      const T ke = mx * mx + my * my;
-      if constexpr (F32) {  // rho > 0 and p > 0, the latter as rho E - |m|^2 / 2 > 0 (no division)
-        bad = bad || !(rho > 0.0f) || !(rho * E - 0.5f * ke > 0.0f);
-      } else {
-        const T pr = gm1 * (E - (T)0.5 * ke / rho);
-        bad = bad || !(rho > (T)0) || !(pr > (T)0);
-      }
-    }
-  }
-  if (a.guard_on && bad) {
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) fv[f][q] = U0 + (T)L0;
-    if (active && v == 0) atomicAdd(a.guard, 1ull);
-  }
-  if (active) {
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const int p = (perm >> (3 * f)) & 7u;
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) Ufi[(f * NQ + (p ? NQ - 1 - q : q)) * NV + v] = fv[f][q];
-    }
-  }
+    return s;
+  };
+  auto phi = [](int f, int q, int k) { return cPhiH<T, R>((f * NQ + q) * NK + k); };
+  lane_faces<2, NK, KD, NQ, T, SCHEME, CHR>(a, i, active, v, base, ao, ad, info, U0, L0, oc, sid, phi);
   // CFL time step bookkeeping at the first stage of a step: dt[next] -> dt[cur]
   if (a.dt_swap && blockIdx.x == 0)
     for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {

@@ -11,6 +11,7 @@ import numpy as np
 CTENO_SCHEME_CTENO, CTENO_SCHEME_CTENOZ, CTENO_SCHEME_CWENO, CTENO_SCHEME_TENO = 0, 1, 2, 3
 CTENO_FP64, CTENO_MIXED = 0, 1
 CTENO_BOUNDARY_TRANSMISSIVE = 0
+CTENO_BOUNDARY_WALL = 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libcteno.so")
@@ -25,7 +26,8 @@ class CtenoError(RuntimeError):
 
 class cteno_params(C.Structure):
     _fields_ = [("dim", C.c_int), ("degree", C.c_int), ("scheme", C.c_int), ("precision", C.c_int),
-                ("lam_gamma", C.c_int), ("positivity_guard", C.c_int), ("ctenoz_form", C.c_int), ("C_T", C.c_double),
+                ("lam_gamma", C.c_int), ("positivity_guard", C.c_int), ("ctenoz_form", C.c_int),
+                ("characteristic", C.c_int), ("rk", C.c_int), ("C_T", C.c_double),
                 ("lambda1p", C.c_double), ("eps", C.c_double), ("cfl", C.c_double),
                 ("gamma", C.c_double)]
 
@@ -107,14 +109,14 @@ def cteno_create(params: cteno_params, stream: int = 0):
     return h
 
 
-def cteno_mesh_build(ctx, xyz: np.ndarray, cells: np.ndarray, period=None) -> int:
+def cteno_mesh_build(ctx, xyz: np.ndarray, cells: np.ndarray, period=None, boundary: int = 0) -> int:
     xyz = np.ascontiguousarray(xyz, np.float64)
     cells = np.ascontiguousarray(cells, np.int32)
     per = None if period is None else np.ascontiguousarray(period, np.float64)
     mid = C.c_int32(-1)
     rc = load_library().cteno_mesh_build(ctx, xyz.shape[0], _ptr(xyz), cells.shape[0], _ptr(cells),
                                          None if per is None else _ptr(per),
-                                         CTENO_BOUNDARY_TRANSMISSIVE, C.byref(mid))
+                                         int(boundary), C.byref(mid))
     _check(ctx, rc)
     return mid.value
 
@@ -204,8 +206,10 @@ def cteno_record_flags(ctx, enable: bool = True):
 
 
 def cteno_get_flags(ctx, mesh_id: int) -> np.ndarray:
+    """[ncells, nv] flags, or [ncells, (d+1) nv] (face-major) with the characteristic
+    reconstruction."""
     info = cteno_info(ctx, mesh_id)
-    out = np.empty((info[7], info[4]), np.uint8)
+    out = np.empty((info[7], info[9]), np.uint8)
     _check(ctx, load_library().cteno_get_flags(ctx, mesh_id, _ptr(out)))
     return out
 
@@ -230,7 +234,7 @@ def cteno_get_stencil(ctx, mesh_id: int, cell: int, with_admissibility: bool = T
 
 
 def cteno_info(ctx, mesh_id: int = -1) -> np.ndarray:
-    out = np.zeros(9, np.int64)
+    out = np.zeros(10, np.int64)
     _check(ctx, load_library().cteno_info(ctx, mesh_id, _ptr(out)))
     return out
 
@@ -303,14 +307,14 @@ class Solver:
     """
 
     def __init__(self, meshes, dim: int, degree: int = 2, scheme: int = 0, precision: int = 0,
-                 stream: int = 0, build: bool = True, **kw):
+                 stream: int = 0, build: bool = True, boundary: int = 0, **kw):
         p = cteno_default_params()
         p.dim, p.degree, p.scheme, p.precision = dim, degree, scheme, precision
         for k, v in kw.items():
             setattr(p, k, v)
         self.params = p
         self.ctx = cteno_create(p, stream)
-        self.mesh_ids = [cteno_mesh_build(self.ctx, m.xyz, m.cells, m.period) for m in meshes]
+        self.mesh_ids = [cteno_mesh_build(self.ctx, m.xyz, m.cells, m.period, boundary) for m in meshes]
         if build:
             cteno_stencil_build(self.ctx)
             cteno_lsq_build(self.ctx)
@@ -336,7 +340,7 @@ class Solver:
         cteno_rk_stage(self.ctx, s, dt)
 
     def step(self, dt=None):
-        for s in range(3):
+        for s in range(self.params.rk):
             cteno_rk_stage(self.ctx, s, dt)
 
     def run(self, nsteps: int):

@@ -90,3 +90,21 @@ def test_host_stencils_match_oracle_exactly(mesh, degree):
         assert np.array_equal(c_lib, c_orc), i
         assert np.array_equal(d_lib, d_orc), i
     native.cteno_destroy(ctx)
+
+
+def test_launch_values_of_the_lane_only_paths_without_gpu():
+    """Degrees 4-6 and the characteristic reconstruction run the variable-per-lane schedule only:
+    every other reconstruction launch value is refused before anything runs."""
+    native = _lib()
+    for kw in (dict(degree=5), dict(characteristic=1), dict(dim=3, degree=3, characteristic=1)):
+        p = native.cteno_default_params()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        p.precision = 1
+        ctx = native.cteno_create(p)
+        for bad in (128, -64, 2048 + 64, 3072 + 128, 4096, 5120 + 8, 6144 + 4):
+            with pytest.raises(native.CtenoError) as e:
+                native.cteno_set_launch(ctx, bad, 0)
+            assert e.value.code == -1
+        native.cteno_set_launch(ctx, 1024 + 256, 8192 + 128)   # lanes + face-based flux
+        native.cteno_destroy(ctx)

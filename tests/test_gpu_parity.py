@@ -316,7 +316,8 @@ def flag_band(o, rel=1e-4):
     mask = o.stencil_mask()
     adm = np.stack([np.ones_like(mask, bool)] + [(mask >> (1 + f)) & 1 == 1 for f in range(o.nf)], axis=1)
     near = np.abs(chi - o.p["C_T"]) <= rel * o.p["C_T"]
-    return (near & adm[:, None, :]).any(axis=2)
+    adm = adm.reshape((adm.shape[0],) + (1,) * (chi.ndim - 2) + (adm.shape[1],))  # per face and field too
+    return (near & adm).any(axis=-1)
 
 
 def assert_flags_within_contract(fl, o, min_compared=1):

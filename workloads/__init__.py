@@ -314,6 +314,24 @@ def shock_tube_2d(nx: int = 512, ny: int = 128, seed: int = 0, jitter: float = 0
                     dict(dim=2, cfl=0.4))
 
 
+def triple_point_2d(nx: int = 500, ny: int = 215, seed: int = 0, jitter: float = 0.1) -> Workload:
+    """The single-material triple point problem (Sec. 3.4) on [0,7]x[0,3] with walls all round:
+    (1,0,0,1) for x <= 1, (0.125,0,0,0.1) for x > 1 and y > 1.5, (1,0,0,0.1) for x > 1 and
+    y <= 1.5. 500 x 215 squares give 215000 triangles (the paper's mesh: 214770, h ~ 1/67).
+    The paper states no ratio of specific heats for it: gamma = 1.4."""
+    mesh = tri_mesh(nx, ny, 7.0, 3.0, periodic=False, jitter=jitter, seed=seed)
+
+    def f(x):
+        left = x[:, 0] <= 1.0
+        top = x[:, 1] > 1.5
+        prim = np.zeros((x.shape[0], 4))
+        prim[:, 0] = np.where(left, 1.0, np.where(top, 0.125, 1.0))
+        prim[:, 3] = np.where(left, 1.0, 0.1)
+        return prim
+    return Workload(f"triple_point_2d_{nx}x{ny}", mesh, cell_average(mesh, f, n_rule=6),
+                    dict(dim=2, cfl=0.4, boundary="wall"))
+
+
 def quadrant_states(seed: int, k: int) -> np.ndarray:
     """Per-quadrant primitive states of batch member k: rho, p ~ U[0.1,2], u, v ~ U[-1,1]."""
     rng = SplitMix64(seed * 1000003 + 7919 * (k + 1))
