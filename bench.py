@@ -447,22 +447,26 @@ def run_ours(args, rank, world, local):
                     m = variants[f"{oc.name}:{variant_name(sc, dg, 1)}"]
                     m["speedup_vs_fp64"] = round(m["value"] / variants[f"{oc.name}:{variant_name(sc, dg, 0)}"]["value"], 2)
                     m["config"] = oc.description
-                # the cost comparison of the paper's Tables 4-5 (time per step normalised to CWENO
-                # of the same order), here per degree and precision on the GPU
-                for dg in sorted({dg for sc, dg in oc.variants}):
-                    for pr in (1, 0):
-                        base = variants.get(f"{oc.name}:{variant_name(2, dg, pr)}")
-                        if base:
-                            for sc in (2, 3, 0, 1):
-                                v = variants.get(f"{oc.name}:{variant_name(sc, dg, pr)}")
-                                if v:
-                                    v["time_vs_cweno_same_order"] = round(v["ms_per_step"] / base["ms_per_step"], 3)
                 del oc
             else:
                 oc, sc, dg, pr = item
                 variants[f"{oc.name}:{variant_name(sc, dg, pr)}"] = measure(
                     native, oc, sc, dg, pr, stream, flush, torch, dist, world, 0, 3, peaks, peak_kind, alu,
                     seconds=args.variant_seconds)
+    # the cost comparison of the paper's Tables 4-5 (time per step normalised to CWENO of the same
+    # order), per workload, degree and precision on the GPU
+    timed = dict(variants)
+    timed[f"{case.name}:{variant_name(h['scheme'], h['degree'], h['precision'])}"] = head
+    for name in {k.split(":")[0] for k in timed}:
+        for dg in range(2, 7):
+            for pr in (0, 1):
+                base = timed.get(f"{name}:{variant_name(2, dg, pr)}")
+                if not base:
+                    continue
+                for sc in (2, 3, 0, 1):
+                    v = timed.get(f"{name}:{variant_name(sc, dg, pr)}")
+                    if v:
+                        v["time_vs_cweno_same_order"] = round(v["ms_per_step"] / base["ms_per_step"], 3)
     fp64_same = variants.get(f"{case.name}:{variant_name(h['scheme'], h['degree'], 0)}")
 
     # CPU baseline: the oracle on the host cores -------------------------------------------------
