@@ -246,6 +246,8 @@ def recon_kernel_name(dim, degree, scheme, precision, launch):
     args = f"{dim},{degree},{'float' if precision else 'double'},{SCHEMES[scheme]}"
     if degree >= 4:
         return f"recon_high_kernel<{degree},{'float' if precision else 'double'},{SCHEMES[scheme]}> x{launch - 1024}"
+    if 7168 < launch <= 7176 or 7200 < launch <= 7208:
+        return f"recon_pair_kernel<{args},{2 if launch < 7200 else 3} stages> x{32 * (launch % 32)}"
     if 6144 < launch <= 6152:
         return f"recon_stream_cells_kernel<{args}> x{32 * (launch - 6144)}"
     if 5120 < launch <= 5136:

@@ -253,7 +253,9 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
  * (mixed path, w warps per block, 1..8) selects the streamed thread-per-cell schedule: every warp
  * walks tiles of 32 cells, one thread per cell, and each lane streams its own cell's operator
  * record through the warp's ring of shared-memory stages four stencil members at a time; refused
- * likewise when it does not fit. Flux only:
+ * likewise when it does not fit. 7168 + w / 7200 + w (mixed path, w warps per block, 1..8) select
+ * the streamed schedule with two lanes per cell (each lane half of the conserved variables, 16
+ * cells per warp) and a two- / three-stage ring of 4-member chunks; refused likewise. Flux only:
  * 8192 + b (b a multiple of 32 in
  * [32, 256]) selects the face-based schedule: HLLC once per face, in its owner's orientation, into
  * a face-flux array, then a per-cell gather and update (results bit-identical to the per-cell

@@ -880,6 +880,12 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
       return b >= kLaneSchedule + 32 && b <= kLaneSchedule + 256 && b % 32 == 0;
     if (b >= kFaceFlux)  // face-based flux schedule
       return !recon && b - kFaceFlux >= 32 && b - kFaceFlux <= 256 && b % 32 == 0;
+    {
+      int w = 0, st = 0;
+      pair_launch(b, &w, &st);
+      if (w)  // two lanes per cell: reconstruction, mixed, fits
+        return recon && ctx->fp32 && recon_pair_smem(ctx->d, ctx->p.degree, w, st) <= kMaxStreamSmem;
+    }
     if (b > kStreamCells && b <= kStreamCells + 8)  // streamed cells: reconstruction, mixed, fits
       return recon && ctx->fp32 &&
              recon_stream_cells_smem(ctx->d, ctx->p.degree, b - kStreamCells) <= kMaxStreamSmem;
@@ -967,6 +973,10 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
     }
     for (int w : {2, 4, 6, 7, 8})
       if (recon_stream_cells_smem(ctx->d, ctx->p.degree, w) <= kMaxStreamSmem) rcand.push_back(kStreamCells + w);
+    for (int w : {4, 6, 8}) {
+      if (recon_pair_smem(ctx->d, ctx->p.degree, w, 2) <= kMaxStreamSmem) rcand.push_back(kPairLanes + w);
+      if (recon_pair_smem(ctx->d, ctx->p.degree, w, 3) <= kMaxStreamSmem) rcand.push_back(kPairLanes3 + w);
+    }
   }
   if (ctx->p.characteristic)  // the variable-per-lane schedule only
     rcand = {kLaneSchedule + 64, kLaneSchedule + 128, kLaneSchedule + 256};

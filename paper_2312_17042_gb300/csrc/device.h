@@ -216,6 +216,26 @@ inline void stream_launch(int b, int *warps, int *stages) {
   if (b > kStreamLanes && b <= kStreamLanes + 16) *warps = b - kStreamLanes, *stages = 3;
   if (b > kStreamLanes2 && b <= kStreamLanes2 + 16) *warps = b - kStreamLanes2, *stages = 2;
 }
+// kPairLanes + w / kPairLanes3 + w (w warps per block, 1..8): the streamed schedule with two lanes
+// per cell (mixed path), a two- / three-stage ring of 4-member chunks of 16 cells per warp.
+constexpr int kPairLanes = 7168;
+constexpr int kPairLanes3 = 7200;
+inline long long recon_pair_smem(int d, int degree, int warps, int stages) {
+  const int nk = (d == 2 ? (degree + 1) * (degree + 2) / 2 : (degree + 1) * (degree + 2) * (degree + 3) / 6) - 1;
+  const int M = 2 * (nk + 1);
+  const long long stage = 16LL * 4 * nk * 4;
+  const long long hdr = 16LL * (d + 1) * lay_pds(d) * 4 + 16LL * M * 4;
+  const long long nphi = d == 3 ? (long long)(d + 1) * 6 * 4 * nk : 1;
+  const long long phi = (nphi * 4 + 15) / 16 * 16;
+  return phi + (long long)warps * (2 * hdr + stages * stage) + (long long)warps * (2 + stages) * 8 + 8;
+}
+// Launch value -> (warps, stages) of the two-lanes-per-cell schedule, or warps = 0.
+inline void pair_launch(int b, int *warps, int *stages) {
+  *warps = 0;
+  *stages = 0;
+  if (b > kPairLanes && b <= kPairLanes + 8) *warps = b - kPairLanes, *stages = 2;
+  if (b > kPairLanes3 && b <= kPairLanes3 + 8) *warps = b - kPairLanes3, *stages = 3;
+}
 inline int halo_tile(int d) { return kHaloWarps * (32 / (d + 2)); }
 inline int halo_ms(int M) { return (M + 1 + 7) / 8 * 8; }
 // Dynamic shared memory of the gather-staged launch for a tile record of hrec words.

@@ -1,5 +1,6 @@
 // recon_3d.cu -- instantiations of the reconstruction kernel for d = 3.
 #include "recon.cuh"
+#include "recon_pair.cuh"
 
 namespace cteno {
 
@@ -17,6 +18,21 @@ cudaError_t launch_recon_3d(int degree, int fp32, int scheme, const KArgs &a, in
     if (degree == 3 && scheme == 1) CTENO_HALO(3, 1);
 #undef CTENO_HALO
     return cudaSuccess;
+  }
+  {
+    int warps = 0, stages = 0;
+    pair_launch(block, &warps, &stages);
+    if (warps) {  // streamed schedule, two lanes per cell (mixed)
+      if (!fp32) return cudaErrorInvalidValue;  // mixed path only
+#define CTENO_PAIR(R, SC) \
+  (stages == 3 ? launch_recon_pair<3, R, SC, 3>(a, warps, s) : launch_recon_pair<3, R, SC, 2>(a, warps, s))
+      if (degree == 2 && scheme == 0) CTENO_PAIR(2, 0);
+      if (degree == 2 && scheme == 1) CTENO_PAIR(2, 1);
+      if (degree == 3 && scheme == 0) CTENO_PAIR(3, 0);
+      if (degree == 3 && scheme == 1) CTENO_PAIR(3, 1);
+#undef CTENO_PAIR
+      return cudaSuccess;
+    }
   }
   if (block > kStreamCells && block <= kStreamCells + 8) {  // streamed thread-per-cell schedule (mixed)
     if (!fp32) return cudaErrorInvalidValue;  // mixed path only

@@ -64,7 +64,7 @@ def test_non_finite_state_is_reported(precision):
     _fresh_context_works(native)
 
 
-@pytest.mark.parametrize("launch", [2048 + 64, 3072 + 128, 4096, 4097, 5120 + 8, 6144 + 4])
+@pytest.mark.parametrize("launch", [2048 + 64, 3072 + 128, 4096, 4097, 5120 + 8, 6144 + 4, 7168 + 4])
 def test_bounded_wait_timeout_is_reported(launch):
     native = _native()
     wl = W.shock_tube_2d(64, 16)

@@ -208,6 +208,19 @@ def _stream_cells_smem(d, degree, warps):
     return phi + warps * 3 * 32 * 4 * nk * 4 + warps * 3 * 8 + 8
 
 
+def _pair_smem(d, degree, warps, stages):
+    """Shared memory of the two-lanes-per-cell streamed schedule: per warp two tile headers of 16
+    cells and `stages` chunks of 4 members of 16 cells, the 3D face basis values, the barriers."""
+    nk = (degree + 1) * (degree + 2) // 2 - 1 if d == 2 else (degree + 1) * (degree + 2) * (degree + 3) // 6 - 1
+    M = 2 * (nk + 1)
+    pds = 8 if d == 2 else 20
+    stage = 16 * 4 * nk * 4
+    hdr = 16 * (d + 1) * pds * 4 + 16 * M * 4
+    nphi = (d + 1) * 6 * 4 * nk if d == 3 else 1
+    phi = (nphi * 4 + 15) // 16 * 16
+    return phi + warps * (2 * hdr + stages * stage) + warps * (2 + stages) * 8 + 8
+
+
 def _stream_smem(d, degree, warps, stages=3):
     """Shared memory of the streamed lane schedule: per warp two tile headers (directional
     operators, stencil ids) and three (two) chunk stages of 8 (or 4) members' operator rows per cell."""
@@ -225,13 +238,14 @@ def _stream_smem(d, degree, warps, stages=3):
                                     (3072 + 128, 256), (3072 + 256, 128), (4096, 128), (4097, 8192 + 128),
                                     (5120 + 1, 128), (5120 + 4, 8192 + 128), (5120 + 10, 128), (5120 + 16, 128),
                                     (5152 + 3, 128), (5152 + 16, 8192 + 128),
-                                    (6144 + 1, 128), (6144 + 4, 8192 + 128), (6144 + 7, 128), (6144 + 8, 128)],
+                                    (6144 + 1, 128), (6144 + 4, 8192 + 128), (6144 + 7, 128), (6144 + 8, 128),
+                                    (7168 + 2, 128), (7168 + 8, 8192 + 128), (7200 + 4, 128), (7200 + 8, 128)],
                          ids=["cell-thread", "capped", "var-lanes-128", "var-lanes-256", "staged-cells-32",
                               "staged-cells-64", "staged-lanes-64", "staged-lanes-128", "staged-lanes-256",
                               "gather-staged", "gather-staged-one-tile", "streamed-1", "streamed-4",
                               "streamed-10", "streamed-16", "streamed2-3", "streamed2-16", "streamed-cells-1",
                               "streamed-cells-4",
-                              "streamed-cells-7", "streamed-cells-8"])
+                              "streamed-cells-7", "streamed-cells-8", "pair-2", "pair-8", "pair3-4", "pair3-8"])
 def test_mixed_schedules_agree(launch):
     """Every launch schedule of the mixed path gives the same face states and update on a 2D and a
     3D mesh (the arithmetic per variable is the same in each schedule). A staged schedule whose two
@@ -253,7 +267,12 @@ def test_mixed_schedules_agree(launch):
                 native.cteno_set_launch(s.ctx, *launch)
             s.close()
             continue
-        if launch[0] > 6144 and _stream_cells_smem(d, deg, launch[0] - 6144) > STREAM_SMEM_MAX:
+        if launch[0] > 7168 and _pair_smem(d, deg, launch[0] % 32, 2 if launch[0] < 7200 else 3) > STREAM_SMEM_MAX:
+            with pytest.raises(native.CtenoError):
+                native.cteno_set_launch(s.ctx, *launch)
+            s.close()
+            continue
+        if 6144 < launch[0] <= 6152 and _stream_cells_smem(d, deg, launch[0] - 6144) > STREAM_SMEM_MAX:
             with pytest.raises(native.CtenoError):
                 native.cteno_set_launch(s.ctx, *launch)
             s.close()
