@@ -15,12 +15,14 @@ with CTENO and CTENOZ at degree 2 and 3; the 3D density wave (64^3 x 6 tetrahedr
 2); the batch of 64 four-quadrant Riemann problems (1.74M triangles, CTENOZ degree 2, one launch
 per kernel for all meshes); the single-material triple point (Sec. 3.4: 215000 triangles, walls,
 lambda_1' = 1e4) with CWENO, TENO, CTENO and CTENOZ at fifth and seventh order, whose times per
-step relative to CWENO of the same order are the GPU counterpart of the paper's Table 5 -- each
-in both precisions. L2 (129 MB) is flushed between timed steps by a 256 MB write outside the
+step relative to CWENO of the same order are the GPU counterpart of the paper's Table 5; the shock
+tube again with the characteristic-variable reconstruction (its cost against the conserved one) --
+each in both precisions. L2 (129 MB) is flushed between timed steps by a 256 MB write outside the
 timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload blast_3d_96|shock_tube_2d|density_wave_3d_64|batch_2d|triple_point_2d]
+                  [--workload blast_3d_96|shock_tube_2d|density_wave_3d_64|batch_2d|triple_point_2d|
+                              shock_tube_2d_characteristic]
                   [--variants all|workload|none] [--profile]
 
 --profile runs only warm-up + steps of the headline (a short command for ncu).
@@ -49,7 +51,8 @@ METRIC = "Mcell-RK-stage/s (deg 2/3, 2D tri & 3D tet), FP32-mixed vs FP64 on one
 UNIT = "Mcell-RK-stage/s"
 SCHEMES = {0: "CTENO", 1: "CTENOZ", 2: "CWENO", 3: "TENO"}
 PRECISIONS = {0: "fp64", 1: "mixed"}
-WORKLOADS = ["blast_3d_96", "shock_tube_2d", "density_wave_3d_64", "batch_2d", "triple_point_2d"]
+WORKLOADS = ["blast_3d_96", "shock_tube_2d", "density_wave_3d_64", "batch_2d", "triple_point_2d",
+             "shock_tube_2d_characteristic"]
 
 
 class Case:
@@ -92,6 +95,11 @@ def make_case(name, n=0):
                     f"{sum(w.mesh.ncells for w in wls)} cells, four-quadrant Riemann states, CFL 0.4, "
                     "one launch per kernel for all meshes", [w.mesh for w in wls], [w.U0 for w in wls],
                     2, 1, 2, 0.4, [(1, 2)], (0.5, 0.5))
+    if name == "shock_tube_2d_characteristic":
+        wl = W.shock_tube_2d(512, 128)
+        return Case(name, "the 2D shock tube (131072 triangles, Sod, CFL 0.4) reconstructed in characteristic "
+                    "variables (per face, Sec. 2.2 / 3.2)", [wl.mesh], [wl.U0], 2, 0, 2, 0.4,
+                    [(0, 2), (0, 3), (1, 2), (1, 3)], (0.5, 0.125), extra=dict(characteristic=1))
     if name == "triple_point_2d":
         wl = W.triple_point_2d()
         return Case(name, f"single-material triple point (Sec. 3.4), [0,7]x[0,3], 500x215 squares -> "
