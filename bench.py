@@ -16,13 +16,15 @@ with CTENO and CTENOZ at degree 2 and 3; the 3D density wave (64^3 x 6 tetrahedr
 per kernel for all meshes); the single-material triple point (Sec. 3.4: 215000 triangles, walls,
 lambda_1' = 1e4) with CWENO, TENO, CTENO and CTENOZ at fifth and seventh order, whose times per
 step relative to CWENO of the same order are the GPU counterpart of the paper's Table 5; the shock
-tube again with the characteristic-variable reconstruction (its cost against the conserved one) --
-each in both precisions. L2 (129 MB) is flushed between timed steps by a 256 MB write outside the
+tube again with the characteristic-variable reconstruction (its cost against the conserved one); the
+double Mach reflection on the paper's timing mesh size (Sec. 3.3: 715208 triangles against 714138)
+with CWENO, TENO, CTENO and CTENOZ at fifth order (Table 4's comparison) and CTENO / CTENOZ at
+seventh -- each in both precisions. L2 (129 MB) is flushed between timed steps by a 256 MB write outside the
 timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload blast_3d_96|shock_tube_2d|density_wave_3d_64|batch_2d|triple_point_2d|
-                              shock_tube_2d_characteristic]
+                              shock_tube_2d_characteristic|dmr_2d]
                   [--variants all|workload|none] [--profile]
 
 --profile runs only warm-up + steps of the headline (a short command for ncu).
@@ -52,7 +54,7 @@ UNIT = "Mcell-RK-stage/s"
 SCHEMES = {0: "CTENO", 1: "CTENOZ", 2: "CWENO", 3: "TENO"}
 PRECISIONS = {0: "fp64", 1: "mixed"}
 WORKLOADS = ["blast_3d_96", "shock_tube_2d", "density_wave_3d_64", "batch_2d", "triple_point_2d",
-             "shock_tube_2d_characteristic"]
+             "shock_tube_2d_characteristic", "dmr_2d"]
 
 
 class Case:
@@ -100,6 +102,14 @@ def make_case(name, n=0):
         return Case(name, "the 2D shock tube (131072 triangles, Sod, CFL 0.4) reconstructed in characteristic "
                     "variables (per face, Sec. 2.2 / 3.2)", [wl.mesh], [wl.U0], 2, 0, 2, 0.4,
                     [(0, 2), (0, 3), (1, 2), (1, 3)], (0.5, 0.125), extra=dict(characteristic=1))
+    if name == "dmr_2d":
+        wl = W.dmr_2d(n or 299)
+        regions, states = W.dmr_boundary()
+        return Case(name, f"double Mach reflection (Sec. 3.3), [0,4]x[0,1], {4 * (n or 299)}x{n or 299} squares -> "
+                    f"{wl.mesh.ncells} triangles (the paper's timing mesh: 714138), inflow / wall / moving-shock / "
+                    "transmissive boundaries, lambda_1' = 1e15, CFL 0.4", [wl.mesh], [wl.U0], 2, 0, 4, 0.4,
+                    [(2, 4), (3, 4), (0, 4), (1, 4), (0, 6), (1, 6)], (0.5, 0.25),
+                    extra=dict(lambda1p=1e15, regions=regions, states=states))
     if name == "triple_point_2d":
         wl = W.triple_point_2d()
         return Case(name, f"single-material triple point (Sec. 3.4), [0,7]x[0,3], 500x215 squares -> "
@@ -373,7 +383,9 @@ def measure(native, case, scheme, degree, precision, stream, flush, torch, dist,
     out["roofline"] = roofline_of(case, scheme, degree, precision, launch[0], stats, recon_ms, peaks, peak_kind, alu)
     out["flux"] = {"launch_ms": round(flux_ms, 5), "algorithmic_bytes_per_launch": stats[1],
                    "achieved_gbs": round(stats[1] / (flux_ms * 1e-3) / 1e9, 1)}
-    out["gpu_launches"] = 3 * (1 + (2 if launch[1] >= 8192 else 1)) * steps
+    # per stage one reconstruction and one (or, face-based, two) flux/update launches; a
+    # moving-shock boundary adds the time advance at the end of each step
+    out["gpu_launches"] = (3 * (1 + (2 if launch[1] >= 8192 else 1)) + (1 if "regions" in case.extra else 0)) * steps
     if clk is not None:
         out["clocks"] = clk
     if e2e:
@@ -525,6 +537,18 @@ def _subbox_sample(case, target):
     return np.sort(np.argsort(d, kind="stable")[:target]).astype(np.int32)
 
 
+def _oracle_for(case, mesh, degree, scheme):
+    """The oracle of a workload (set-up deferred to the sampled cells), with its boundary regions."""
+    from oracle import Oracle
+    params = {k: v for k, v in case.extra.items() if k not in ("regions", "states")}
+    o = Oracle(mesh, setup=False, degree=degree, scheme=scheme, cfl=case.cfl, **params)
+    for lo, hi, kind in case.extra.get("regions", ()):
+        o.boundary_region(lo, hi, kind)
+    if "states" in case.extra:
+        o.boundary_states(*case.extra["states"])
+    return o
+
+
 # cells of one oracle stage of the sample, by (dim, degree): about 1-2 s of one stage on 16 cores
 SAMPLE_CELLS = {(2, 2): 131072, (2, 3): 131072, (3, 2): 300000, (3, 3): 60000, (2, 4): 60000, (2, 5): 40000,
                 (2, 6): 30000}
@@ -539,7 +563,7 @@ def oracle_sample_timing(case, h, budget_s=20.0):
     mesh, U0 = case.meshes[0], case.states[0]
     ids = _subbox_sample(case, SAMPLE_CELLS[(case.dim, h["degree"])])
     t0 = time.perf_counter()
-    o = Oracle(mesh, setup=False, degree=h["degree"], scheme=h["scheme"], cfl=case.cfl, **case.extra)
+    o = _oracle_for(case, mesh, h["degree"], h["scheme"])
     o.set_state(U0)
     nbr = o.geometry()["nbr"][ids]
     o.setup_cells(np.unique(np.concatenate([ids, nbr[nbr >= 0]])))
@@ -568,7 +592,7 @@ def run_reference(args, rank, world):
     h = dict(scheme=case.scheme, degree=case.degree)
     mesh, U0 = case.meshes[0], case.states[0]
     ids = _subbox_sample(case, SAMPLE_CELLS[(case.dim, case.degree)])
-    o = Oracle(mesh, setup=False, degree=case.degree, scheme=case.scheme, cfl=case.cfl, **case.extra)
+    o = _oracle_for(case, mesh, case.degree, case.scheme)
     o.set_state(U0)
     nbr = o.geometry()["nbr"][ids]
     o.setup_cells(np.unique(np.concatenate([ids, nbr[nbr >= 0]])))

@@ -54,7 +54,14 @@ enum { CTENO_FP64 = 0, CTENO_MIXED = 1 };
  * (the outside state at each Gauss point is the mirror image of the reconstructed inside state,
  * (rho, m - 2 (m.n) n, E); the paper's Sec. 3.3 and 3.4 run walls without printing their
  * treatment). Periodic directions have no boundary faces. */
-enum { CTENO_BOUNDARY_TRANSMISSIVE = 0, CTENO_BOUNDARY_WALL = 1 };
+enum {
+  CTENO_BOUNDARY_TRANSMISSIVE = 0,
+  CTENO_BOUNDARY_WALL = 1,
+  CTENO_BOUNDARY_STATE_A = 2,  /* the outside state is the fixed state A (inflow, post-shock) */
+  CTENO_BOUNDARY_SHOCK_AB = 3  /* 2D: state A where the moving shock line x = xs0 + sy y + vs t has
+                                  passed the face midpoint (xs0 + sy y_mid + vs t > x_mid), else B;
+                                  t is the stage's time (cteno_set_time / cteno_get_time) */
+};
 
 /* Scheme parameters (paper notation). */
 typedef struct {
@@ -122,8 +129,9 @@ int cteno_create(cteno_ctx **out, const cteno_params *p, void *cuda_stream);
  *   period             : host, period[dim]; period[j] > 0 makes direction j periodic with that
  *                        length (vertices are stored once and cells unwrap across the box);
  *                        NULL or 0 = bounded.
- *   boundary_kind      : CTENO_BOUNDARY_TRANSMISSIVE or CTENO_BOUNDARY_WALL, for every bounded
- *                        boundary face of this mesh (meshes of a batch may differ).
+ *   boundary_kind      : CTENO_BOUNDARY_TRANSMISSIVE, CTENO_BOUNDARY_WALL or
+ *                        CTENO_BOUNDARY_STATE_A for every bounded boundary face of this mesh
+ *                        (meshes of a batch may differ; cteno_boundary_region refines it).
  *   mesh_id_out        : receives the index of the mesh in the batch.
  * Errors: CTENO_ERR_MESH for degenerate cells or faces shared by more than two cells. Meshes can
  * only be added before cteno_stencil_build. */
@@ -219,6 +227,25 @@ int cteno_get_face_states(cteno_ctx *ctx, int32_t mesh_id, double *out);
  * cteno_lsq_build; dok may be NULL before it. */
 int cteno_get_stencil(cteno_ctx *ctx, int32_t mesh_id, int64_t cell, int32_t *central,
                       int32_t *dir, int32_t *dok);
+
+/* Boundary kinds by region (before cteno_lsq_build): every boundary face of mesh `mesh_id` whose
+ * midpoint lies in the axis-aligned box [lo, hi] (host arrays of dim values, inclusive) gets `kind`
+ * (CTENO_BOUNDARY_*); later calls override earlier ones, and faces outside every box keep the kind
+ * given to cteno_mesh_build. CTENO_ERR_ARG for an unknown kind (or a moving shock in 3D). */
+int cteno_boundary_region(cteno_ctx *ctx, int32_t mesh_id, const double *lo, const double *hi, int kind);
+
+/* States A and B (host, nv conserved values each) of the fixed-state and moving-shock kinds, and
+ * the moving shock line x = xs0 + sy y + vs t. xs0 and sy enter the face geometry built by
+ * cteno_lsq_build, so they must be set before it (CTENO_ERR_STATE after it if they change); A, B
+ * and vs may change at any time. */
+int cteno_boundary_states(cteno_ctx *ctx, const double *A, const double *B, double xs0, double sy, double vs);
+
+/* Physical time of every mesh (a moving-shock boundary needs it; it starts at 0 and advances by
+ * each step's dt, the stages of a step seeing t + c_s dt with c = (0, 1, 1/2) for SSP-RK3 and
+ * (0, 1/2, 1/2, 1) for RK4). cteno_set_time sets every mesh's time (a no-op without a moving-shock
+ * boundary); cteno_get_time (host t_out[nmeshes]) returns CTENO_ERR_STATE without one. */
+int cteno_set_time(cteno_ctx *ctx, double t);
+int cteno_get_time(cteno_ctx *ctx, double *t_out);
 
 /* Sizes, out[10]: out[0] = nmeshes, out[1] = total cells, out[2] = M, out[3] = K-1, out[4] = nv,
  * out[5] = faces per cell, out[6] = Gauss points per face, out[7] = cells of mesh `mesh_id`

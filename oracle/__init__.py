@@ -72,6 +72,11 @@ def _load():
     lib.orc_simplex_monomial.argtypes = [V, _dp, C.c_int]
     lib.orc_num_threads.restype = C.c_int
     lib.orc_eigen.argtypes = [V, _dp, _dp, _dp, _dp]
+    lib.orc_boundary_region.argtypes = [V, _dp, _dp, C.c_int]
+    lib.orc_boundary_states.argtypes = [V, _dp, _dp, C.c_double, C.c_double, C.c_double]
+    lib.orc_set_time.argtypes = [V, C.c_double]
+    lib.orc_get_time.restype = C.c_double
+    lib.orc_get_time.argtypes = [V]
     _lib = lib
     return lib
 
@@ -257,6 +262,23 @@ class Oracle:
         out = np.empty((self.ncells,) + self.sel_shape + (self.nk,))
         self.lib.orc_get_coeffs(self.h, out)
         return out
+
+    # boundary kinds (oracle readings): 0 transmissive, 1 wall, 2 fixed state A, 3 moving shock
+    # (state A where xs0 + sy y + vs t exceeds the face midpoint's x, else B)
+    def boundary_region(self, lo, hi, kind: int):
+        """Every boundary face whose midpoint lies in the box [lo, hi] gets `kind`."""
+        self.lib.orc_boundary_region(self.h, np.ascontiguousarray(lo, np.float64),
+                                     np.ascontiguousarray(hi, np.float64), int(kind))
+
+    def boundary_states(self, A, B, xs0=0.0, sy=0.0, vs=0.0):
+        self.lib.orc_boundary_states(self.h, np.ascontiguousarray(A, np.float64),
+                                     np.ascontiguousarray(B, np.float64), xs0, sy, vs)
+
+    def set_time(self, t: float):
+        self.lib.orc_set_time(self.h, float(t))
+
+    def time(self) -> float:
+        return float(self.lib.orc_get_time(self.h))
 
     def eigen(self, u, n):
         """(R, L): right and left eigenvectors of the Euler flux Jacobian in unit direction n at

@@ -87,6 +87,10 @@ typedef struct {
   double *Jinv;        /* [ncells][dim][dim] inverse of the reference map Jacobian */
   double *detJ;
   int *nbr, *nbrf;     /* [ncells][nf] neighbour cell / its local face; -1 = boundary */
+  signed char *bkind;  /* [ncells][nf] kind of a boundary face (BND_*) */
+  double bstate[2][MAXNV]; /* conserved states A and B of the fixed-state and moving-shock kinds */
+  double shock[3];     /* moving shock: A where xs0 + sy y + vs t > x at the face midpoint, else B */
+  double time, stage_time; /* physical time at the start of the step / of the current stage */
   double *area, *nrm;  /* [ncells][nf], [ncells][nf][dim] outward unit normal */
   double *fq;          /* [ncells][nf][nq][dim] physical face Gauss points (canonical order) */
   double fw[MAXNQ];    /* face weights (sum 1) */
@@ -382,6 +386,13 @@ static void face_rule(int d, int nq, double t[MAXNQ][3], double *w) {
       }
   }
 }
+
+/* Boundary face kinds. Reading (the paper runs walls, inflow and a moving-shock top boundary in
+ * Sec. 3.3 / 3.4 without printing their treatment): transmissive, the outside state is the cell
+ * mean; wall, the mirror image of the reconstructed inside state; fixed state A; moving shock,
+ * state A on the side of the shock line x = xs0 + sy y + vs t where x is smaller, else B, decided
+ * at the face midpoint. */
+enum { BND_TRANSMISSIVE = 0, BND_WALL = 1, BND_STATE_A = 2, BND_SHOCK_AB = 3 };
 
 static int build_faces(orc *o) {
   const int d = o->p.dim, nvc = d + 1, n = o->ncells, nf = o->nf;
@@ -1169,12 +1180,24 @@ static void residual_cell(orc *o, int i, double *Rout) {
     for (int q = 0; q < nq; ++q) {
       const double *uL = o->face + (((size_t)i * nf + f) * nq + q) * nv;
       double ub[MAXNV];
-      if (o->p.boundary == 1) {
+      const int kind = (j >= 0) ? -1 : o->bkind[i * nf + f];
+      if (kind == BND_WALL) {
         double mn = 0.0;
         for (int k = 0; k < d; ++k) mn += uL[1 + k] * n[k];
         ub[0] = uL[0];
         for (int k = 0; k < d; ++k) ub[1 + k] = uL[1 + k] - 2.0 * mn * n[k];
         ub[d + 1] = uL[d + 1];
+      } else if (kind == BND_STATE_A || kind == BND_SHOCK_AB) {
+        int use_a = 1;
+        if (kind == BND_SHOCK_AB) {
+          double mid[3] = {0, 0, 0};
+          const double *X = o->X + (size_t)i * (d + 1) * d;
+          for (int a = 0; a <= d; ++a)
+            if (a != f)
+              for (int k = 0; k < d; ++k) mid[k] += X[a * d + k] / d;
+          use_a = o->shock[0] + o->shock[1] * mid[1] + o->shock[2] * o->stage_time > mid[0];
+        }
+        for (int v = 0; v < nv; ++v) ub[v] = o->bstate[use_a ? 0 : 1][v];
       } else {
         for (int v = 0; v < nv; ++v) ub[v] = o->U[v * o->ncells + i];
       }
@@ -1226,6 +1249,10 @@ double orc_dt(orc *o) {
  * U^{n+1} = U^n + dt/6 (k_1 + 2 k_2 + 2 k_3 + k_4) (accumulated stage by stage in Acc). */
 void orc_stage(orc *o, int stage, double dt) {
   const int n = o->ncells, nv = o->nv;
+  /* the stage's time, for the time-dependent boundary: t^n + c_s dt with c = (0, 1, 1/2) for
+   * SSP-RK3 and (0, 1/2, 1/2, 1) for RK4 */
+  static const double c3[3] = {0.0, 1.0, 0.5}, c4[4] = {0.0, 0.5, 0.5, 1.0};
+  o->stage_time = o->time + (o->p.rk == 4 ? c4[stage] : c3[stage]) * dt;
   if (stage == 0) memcpy(o->Un, o->U, sizeof(double) * nv * n);
   residual_all(o, o->U);
   if (o->p.rk == 4) {
@@ -1254,7 +1281,42 @@ void orc_stage(orc *o, int stage, double dt) {
 double orc_step(orc *o, double dt) {
   if (!(dt > 0.0)) dt = orc_dt(o);
   for (int s = 0; s < (o->p.rk == 4 ? 4 : 3); ++s) orc_stage(o, s, dt);
+  o->time += dt;
   return dt;
+}
+
+/* Sets the time of the next step (and of a residual evaluated outside a step). */
+void orc_set_time(orc *o, double t) { o->time = o->stage_time = t; }
+double orc_get_time(const orc *o) { return o->time; }
+
+/* Every boundary face whose midpoint lies in the box [lo, hi] (inclusive) becomes of the given
+ * kind (later calls override earlier ones). */
+void orc_boundary_region(orc *o, const double *lo, const double *hi, int kind) {
+  const int d = o->p.dim, nf = o->nf;
+  for (int i = 0; i < o->ncells; ++i)
+    for (int f = 0; f < nf; ++f) {
+      if (o->nbr[i * nf + f] >= 0) continue;
+      const double *X = o->X + (size_t)i * (d + 1) * d;
+      int in = 1;
+      for (int k = 0; k < d; ++k) {
+        double m = 0.0;
+        for (int a = 0; a <= d; ++a)
+          if (a != f) m += X[a * d + k] / d;
+        in = in && m >= lo[k] && m <= hi[k];
+      }
+      if (in) o->bkind[i * nf + f] = (signed char)kind;
+    }
+}
+
+/* States A and B (conserved) and the moving shock x = xs0 + sy y + vs t of the fixed-state kinds. */
+void orc_boundary_states(orc *o, const double *A, const double *B, double xs0, double sy, double vs) {
+  for (int v = 0; v < o->nv; ++v) {
+    o->bstate[0][v] = A[v];
+    o->bstate[1][v] = B[v];
+  }
+  o->shock[0] = xs0;
+  o->shock[1] = sy;
+  o->shock[2] = vs;
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -1325,6 +1387,8 @@ orc *orc_create(int dim, int degree, int scheme, int lam_gamma, int ctenoz_form,
   o->U = (double *)calloc(n * o->nv, sizeof(double));
   o->Un = (double *)calloc(n * o->nv, sizeof(double));
   o->Acc = (double *)calloc(n * o->nv, sizeof(double));
+  o->bkind = (signed char *)malloc(n * o->nf);
+  for (size_t k = 0; k < n * (size_t)o->nf; ++k) o->bkind[k] = (signed char)(boundary == 1 ? BND_WALL : BND_TRANSMISSIVE);
   o->Rres = (double *)calloc(n * o->nv, sizeof(double));
   o->face = (double *)calloc(n * o->nf * o->nq * o->nv, sizeof(double));
   o->flags = (uint8_t *)calloc(n * o->nsel, 1);
@@ -1384,7 +1448,7 @@ void orc_destroy(orc *o) {
   free(o->cv); free(o->X); free(o->vol); free(o->cen); free(o->Jinv); free(o->detJ);
   free(o->nbr); free(o->nbrf); free(o->area); free(o->nrm); free(o->fq);
   free(o->v2c_off); free(o->v2c); free(o->qlam); free(o->qw);
-  free(o->U); free(o->Un); free(o->Acc); free(o->Rres); free(o->face); free(o->flags); free(o->SI); free(o->chi);
+  free(o->U); free(o->Un); free(o->Acc); free(o->bkind); free(o->Rres); free(o->face); free(o->flags); free(o->SI); free(o->chi);
   free(o->stmask);
   free(o->guarded);
   free(o->coef);

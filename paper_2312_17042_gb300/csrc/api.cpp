@@ -33,6 +33,9 @@ struct cteno_ctx {
   int64_t *d_mesh_off = nullptr;
   double *U = nullptr, *Un = nullptr;
   double *Acc = nullptr;             // RK4 running sum
+  double bA[6] = {}, bB[6] = {};     // boundary states A and B (conserved)
+  double shock[3] = {};              // moving shock: xs0, sy, vs
+  double *time = nullptr;            // [nmesh] physical time (allocated when a moving shock exists)
   float *U32 = nullptr;
   int32_t *st = nullptr, *nbr = nullptr;
   int32_t *hl = nullptr;             // gather staging: per-tile distinct member lists (mixed path)
@@ -142,6 +145,18 @@ KArgs make_args(cteno_ctx *ctx, int stage, int dt_swap) {
   a.ctenoz_form = ctx->p.ctenoz_form;
   a.characteristic = ctx->p.characteristic;
   a.Acc = ctx->Acc;
+  for (int v = 0; v < 6; ++v) {
+    a.bA[v] = ctx->bA[v];
+    a.bB[v] = ctx->bB[v];
+    a.bA32[v] = (float)ctx->bA[v];
+    a.bB32[v] = (float)ctx->bB[v];
+  }
+  a.shock_vs = ctx->shock[2];
+  a.time = ctx->time;
+  {  // stage time offsets: SSP-RK3 (0, 1, 1/2), RK4 (0, 1/2, 1/2, 1)
+    static const double c3[3] = {0.0, 1.0, 0.5}, c4[4] = {0.0, 0.5, 0.5, 1.0};
+    a.stage_c = (ctx->nst == 4) ? c4[stage] : c3[stage];
+  }
   a.rk4 = ctx->nst == 4;
   a.last_stage = ctx->nst - 1;
   a.cweno = ctx->p.scheme == CTENO_SCHEME_CWENO;
@@ -308,7 +323,8 @@ int cteno_mesh_build(cteno_ctx *ctx, int64_t nverts, const double *xyz, int64_t 
   if (!ctx) return CTENO_ERR_ARG;
   if (ctx->stencils) return fail(ctx, CTENO_ERR_STATE, "meshes must be added before cteno_stencil_build");
   if (!xyz || !cell_verts || nverts <= 0 || ncells <= 0 || ncells > INT32_MAX / 2 ||
-      (boundary_kind != CTENO_BOUNDARY_TRANSMISSIVE && boundary_kind != CTENO_BOUNDARY_WALL))
+      (boundary_kind != CTENO_BOUNDARY_TRANSMISSIVE && boundary_kind != CTENO_BOUNDARY_WALL &&
+       boundary_kind != CTENO_BOUNDARY_STATE_A))
     return fail(ctx, CTENO_ERR_ARG, "invalid mesh arguments");
   Mesh m;
   int rc = ingest_mesh(ctx->d, nverts, xyz, ncells, cell_verts, period, &m, &ctx->err);
@@ -317,7 +333,7 @@ int cteno_mesh_build(cteno_ctx *ctx, int64_t nverts, const double *xyz, int64_t 
     for (int j = 0; j < 3; ++j)
       if (ctx->meshes[0].period[j] != m.period[j])
         return fail(ctx, CTENO_ERR_ARG, "all meshes of one context must have the same period");
-  m.wall = boundary_kind == CTENO_BOUNDARY_WALL;
+  m.bkind.assign((size_t)m.ncells * (ctx->d + 1), (int8_t)boundary_kind);
   ctx->meshes.push_back(std::move(m));
   if (mesh_id_out) *mesh_id_out = (int32_t)ctx->meshes.size() - 1;
   return CTENO_OK;
@@ -452,7 +468,8 @@ int cteno_lsq_build(cteno_ctx *ctx) {
         if (nb < 0) {
           hnbr[(size_t)g * 4 + f] = -1;
           meta |= 1u << (kMetaOwnerShift + f);
-          if (m.wall) meta |= 1u << (kMetaWallShift + f);
+          const int kind = m.bkind[(size_t)c * nf + f];
+          meta |= (uint32_t)kind << (kMetaKindShift + 2 * f);
         } else {
           const int64_t gn = m.offset + m.rank[nb];
           hnbr[(size_t)g * 4 + f] = (int32_t)gn;
@@ -463,6 +480,12 @@ int cteno_lsq_build(cteno_ctx *ctx) {
       hmeta[g] = meta;
     }
   }
+  // a moving-shock boundary needs the physical time on the device
+  bool shock_faces = false;
+  for (int64_t g = 0; g < N && !shock_faces; ++g)
+    for (int f = 0; f < nf; ++f)
+      if (hnbr[(size_t)g * 4 + f] < 0 && ((hmeta[g] >> (kMetaKindShift + 2 * f)) & 3u) == CTENO_BOUNDARY_SHOCK_AB)
+        shock_faces = true;
   // face list of the face-based flux schedule: owner cell-faces in (cell, face) order; every
   // cell-face refers to its face, flagged where the cell is not the owner
   std::vector<int32_t> hface, hcellface((size_t)N * 4, 0);
@@ -524,6 +547,10 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   if (ctx->fp32) CK(dalloc(ctx, &ctx->geo32, sizeof(float) * nf * 4 * N));
   CK(dalloc(ctx, &ctx->vol, sizeof(double) * N));
   CK(dalloc(ctx, &ctx->dt, sizeof(double) * 2 * nmesh));
+  if (shock_faces) {
+    CK(dalloc(ctx, &ctx->time, sizeof(double) * nmesh));
+    CK(cudaMemsetAsync(ctx->time, 0, sizeof(double) * nmesh, ctx->stream));
+  }
   CK(dalloc(ctx, &ctx->derr, sizeof(int)));
   CK(dalloc(ctx, &ctx->guard, sizeof(unsigned long long)));
   ctx->d_rank.resize(nmesh);
@@ -582,6 +609,8 @@ int cteno_lsq_build(cteno_ctx *ctx) {
   s.vol = ctx->vol;
   s.geo32 = ctx->geo32;
   s.tab = ctx->d_tab;
+  s.shock_xs0 = ctx->shock[0];
+  s.shock_sy = ctx->shock[1];
   s.err = ctx->derr;
   for (int j = 0; j < 3; ++j) s.period[j] = ctx->meshes[0].period[j];  // shared by all meshes
   launch_setup(d, ctx->p.degree, s, ctx->stream);
@@ -705,6 +734,8 @@ int cteno_rk_stage(cteno_ctx *ctx, int stage, const double *dt) {
     swap = 1;  // the CFL step of the current state (computed by set_state or the last stage)
   }
   CK(enqueue_stage(ctx, stage, swap, ctx->stream));
+  if (ctx->time && stage == ctx->nst - 1)  // the end of the step
+    launch_time_advance(ctx->time, ctx->dt, (int)ctx->meshes.size(), ctx->stream);
   CK(cudaGetLastError());
   return CTENO_OK;
 }
@@ -730,6 +761,7 @@ int cteno_run(cteno_ctx *ctx, int nsteps) {
       launch_flux(ctx->d, ctx->nq, ctx->fp32 ? 1 : 0, a, ctx->flux_block, ctx->capture);
       if (ctx->timing) CK(cudaEventRecordWithFlags(ctx->tev[2 * s + 2], ctx->capture, cudaEventRecordExternal));
     }
+    if (ctx->time) launch_time_advance(ctx->time, ctx->dt, (int)ctx->meshes.size(), ctx->capture);
     cudaError_t e = cudaStreamEndCapture(ctx->capture, &ctx->graph);
     if (e != cudaSuccess) return fail(ctx, CTENO_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     CK(cudaGraphInstantiate(&ctx->graph_exec, ctx->graph, 0));
@@ -836,6 +868,66 @@ int cteno_get_stencil(cteno_ctx *ctx, int32_t mesh_id, int64_t cell, int32_t *ce
     const uint32_t info = ctx->h_cinfo[m.offset + m.rank[cell]];
     for (int f = 0; f < nf; ++f) dok[f] = (info >> (kInfoAdmShift + f)) & 1u;
   }
+  return CTENO_OK;
+}
+
+int cteno_boundary_region(cteno_ctx *ctx, int32_t mesh_id, const double *lo, const double *hi, int kind) {
+  if (!ctx) return CTENO_ERR_ARG;
+  int rc = check_mesh(ctx, mesh_id);
+  if (rc) return rc;
+  if (ctx->built) return fail(ctx, CTENO_ERR_STATE, "boundary regions must be set before cteno_lsq_build");
+  if (!lo || !hi || kind < CTENO_BOUNDARY_TRANSMISSIVE || kind > CTENO_BOUNDARY_SHOCK_AB ||
+      (kind == CTENO_BOUNDARY_SHOCK_AB && ctx->d != 2))
+    return fail(ctx, CTENO_ERR_ARG, "bad boundary region (the moving-shock kind is 2D only)");
+  Mesh &m = ctx->meshes[mesh_id];
+  const int d = ctx->d, nvc = d + 1, nf = d + 1;
+  for (int64_t c = 0; c < m.ncells; ++c)
+    for (int f = 0; f < nf; ++f) {
+      if (m.nbr[c * nf + f] >= 0) continue;
+      bool in = true;
+      for (int k = 0; k < d; ++k) {
+        double mid = 0.0;
+        for (int v = 0; v < nvc; ++v)
+          if (v != f) mid += m.X[(c * nvc + v) * d + k] / d;
+        in = in && mid >= lo[k] && mid <= hi[k];
+      }
+      if (in) m.bkind[(size_t)c * nf + f] = (int8_t)kind;
+    }
+  return CTENO_OK;
+}
+
+int cteno_boundary_states(cteno_ctx *ctx, const double *A, const double *B, double xs0, double sy, double vs) {
+  if (!ctx || !A || !B) return CTENO_ERR_ARG;
+  if (ctx->built && (xs0 != ctx->shock[0] || sy != ctx->shock[1]))
+    return fail(ctx, CTENO_ERR_STATE, "the shock line's position (xs0, sy) must be set before cteno_lsq_build");
+  for (int v = 0; v < ctx->nv; ++v) {
+    ctx->bA[v] = A[v];
+    ctx->bB[v] = B[v];
+  }
+  ctx->shock[0] = xs0;
+  ctx->shock[1] = sy;
+  ctx->shock[2] = vs;
+  drop_graph(ctx);
+  return CTENO_OK;
+}
+
+int cteno_set_time(cteno_ctx *ctx, double t) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (!ctx->time) return CTENO_OK;  // no moving-shock boundary: the time is not tracked
+  std::vector<double> h(ctx->meshes.size(), t);
+  CK(cudaMemcpyAsync(ctx->time, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CTENO_OK;
+}
+
+int cteno_get_time(cteno_ctx *ctx, double *t_out) {
+  int rc = check_built(ctx);
+  if (rc) return rc;
+  if (!t_out) return fail(ctx, CTENO_ERR_ARG, "null output");
+  if (!ctx->time) return fail(ctx, CTENO_ERR_STATE, "the time is tracked only with a moving-shock boundary");
+  CK(cudaMemcpyAsync(t_out, ctx->time, sizeof(double) * ctx->meshes.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return CTENO_OK;
 }
 

@@ -51,9 +51,10 @@ constexpr int kInfoAdmShift = 16;
 constexpr int kInfoPermShift = 20;
 // Bits of `fmeta`: [2f, 2f+2) neighbour's local face; 8 + f: this cell owns face f (computes the
 // flux in its own orientation; the other cell uses the exact negative normal and negates);
-// 12 + f: face f is a reflective wall (a boundary face of a mesh built with CTENO_BOUNDARY_WALL).
+// [12 + 2f, 14 + 2f): kind of boundary face f (CTENO_BOUNDARY_*: transmissive, wall, fixed state
+// A, moving shock between states A and B).
 constexpr int kMetaOwnerShift = 8;
-constexpr int kMetaWallShift = 12;
+constexpr int kMetaKindShift = 12;
 
 // Error word bits.
 constexpr int kErrNonFinite = 1;
@@ -141,6 +142,13 @@ struct KArgs {
   // test hook of the bounded waits (0 = off): the staged schedules first wait at most this many
   // nanoseconds on a barrier that nothing completes, then take their timeout path
   unsigned long long test_wait_ns;
+  // boundary states A and B (conserved, padded) and the moving shock's speed term: a face of the
+  // moving-shock kind takes A where c_f + vs t > 0, c_f = xs0 + sy y_mid - x_mid stored in the
+  // face's unused third geometry slot (2D), t = time[mesh] + stage_c dt[mesh]
+  double bA[6], bB[6];
+  float bA32[6], bB32[6];
+  double shock_vs, stage_c;
+  const double *time;       // [nmesh] physical time at the start of the step (moving shock only)
   int stage;                // 0 .. last_stage
   int rk4;                  // classical four-stage Runge-Kutta (else SSP-RK3)
   int last_stage;           // 2 (SSP-RK3) or 3 (RK4): the stage that computes the next CFL step
@@ -162,6 +170,7 @@ struct SetupArgs {
   float *geo32;
   const DevTables *tab;
   int *err;
+  double shock_xs0, shock_sy;  // moving-shock line x = xs0 + sy y + vs t (2D boundary faces)
 };
 
 // Launch-value convention of the reconstruction kernel: b in [32, 256] one thread per cell;
@@ -280,6 +289,8 @@ inline cudaError_t launch_recon(int dim, int degree, int fp32, int scheme, const
 void launch_flux(int dim, int nq, int fp32, const KArgs &a, int block, cudaStream_t s);
 void launch_dt(int dim, const KArgs &a, cudaStream_t s);
 void launch_dt_reset(const KArgs &a, cudaStream_t s);
+// time[m] += dt[m] for every mesh: the end of a step (kept only when a moving-shock boundary exists)
+void launch_time_advance(double *time, const double *dt, int nmesh, cudaStream_t s);
 // CFL step of one mesh only (device cells [first, first + count)).
 void launch_dt_mesh(int dim, const KArgs &a, int mesh, int64_t first, int64_t count, cudaStream_t s);
 // All meshes in one launch: host-side order is mesh after mesh, [v][cell] per mesh in the mesh's

@@ -170,6 +170,38 @@ __device__ __forceinline__ int mesh_of(const KArgs &a, int64_t i) {
   return lo;
 }
 
+// Outside state of boundary face f of cell i at NQ Gauss points (reading: the paper runs walls,
+// inflow and a moving-shock boundary in Sec. 3.3 / 3.4 without printing their treatment): kind 1
+// the mirror image of the inside state uI (wall_mirror); kind 2 the fixed state A; kind 3 state A
+// where the moving shock line has passed the face midpoint (c_f + vs t > 0, c_f in the face's
+// geometry slot 2), else B; kind 0 (transmissive) the cell mean um.
+template <int D, typename T, int NQ>
+__device__ __forceinline__ void boundary_state(const KArgs &a, const int64_t i, const int kind, const T *gf,
+                                               const T *uI, const double *um, T *uO) {
+  constexpr int NV = D + 2;
+  constexpr bool F32 = sizeof(T) == 4;
+  if (kind == 1) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) wall_mirror<D, T>(uI + q * NV, gf, uO + q * NV);
+    return;
+  }
+  bool use_a = kind == 2;
+  if (kind == 3) {
+    const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
+    const double t = a.time[mesh] + a.stage_c * a.dt[mesh];
+    use_a = (double)gf[2] + a.shock_vs * t > 0.0;
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T x;
+    if (kind == 0) x = (T)um[v];
+    else if constexpr (F32) x = use_a ? a.bA32[v] : a.bB32[v];
+    else x = use_a ? a.bA[v] : a.bB[v];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) uO[q * NV + v] = x;
+  }
+}
+
 // Order-preserving map of a non-negative double onto unsigned 64-bit (for an atomic minimum).
 __device__ __forceinline__ void atomic_min_pos(double *addr, double v) {
   atomicMin((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
@@ -379,14 +411,8 @@ __global__ void __launch_bounds__(MINB ? 128 : 256, MINB ? MINB : 1) flux_kernel
       load16<T, FB>(Uf + (i * NF + f) * FB, uI[ff]);
       if (j >= 0) {
         load16<T, FB>(Uf + (j * NF + fj) * FB, uO[ff]);
-      } else if ((meta >> (kMetaWallShift + f)) & 1u) {  // reflective wall: the mirror image
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) wall_mirror<D, T>(uI[ff] + q * NV, gf[ff], uO[ff] + q * NV);
-      } else {  // transmissive boundary: the cell mean outside
-#pragma unroll
-        for (int q = 0; q < NQ; ++q)
-#pragma unroll
-          for (int v = 0; v < NV; ++v) uO[ff][q * NV + v] = (T)u64[v];
+      } else {  // boundary face: its kind's outside state
+        boundary_state<D, T, NQ>(a, i, (meta >> (kMetaKindShift + 2 * f)) & 3u, gf[ff], uI[ff], u64, uO[ff]);
       }
     }
 #pragma unroll
@@ -459,16 +485,11 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const KArgs a) {
     const int64_t j = codes.y >> 2;
     const int fj = codes.y & 3;
     load16<T, FB>(Uf + (j * NF + fj) * FB, uO);
-  } else if ((__ldg(a.fmeta + i) >> (kMetaWallShift + f)) & 1u) {  // reflective wall: the mirror image
+  } else {  // boundary face: its kind's outside state
+    double um[NVP];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) wall_mirror<D, T>(uI + q * NV, gf, uO + q * NV);
-  } else {  // transmissive boundary: the cell mean outside
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T m = (T)a.U[i * NVP + v];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) uO[q * NV + v] = m;
-    }
+    for (int v = 0; v < NVP; ++v) um[v] = a.U[i * NVP + v];
+    boundary_state<D, T, NQ>(a, i, (__ldg(a.fmeta + i) >> (kMetaKindShift + 2 * f)) & 3u, gf, uI, um, uO);
   }
   T n[D];
 #pragma unroll
@@ -576,6 +597,11 @@ __global__ void dt_kernel(const KArgs a, int64_t first, int64_t count) {
   }
   const int mesh = (a.nmesh > 1) ? mesh_of(a, i) : 0;
   warp_min_to(a.dt, a.nmesh + mesh, active ? a.cfl * local_dt<D, T>(a, i, uu) : 1e300);
+}
+
+__global__ void time_advance_kernel(double *time, const double *dt, int nmesh) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < nmesh) time[m] += dt[m];
 }
 
 __global__ void dt_reset_kernel(double *dt, int nmesh) {
@@ -744,6 +770,10 @@ void launch_set_state_all(int dim, const KArgs &a, const int32_t *grank, const d
 void launch_permute_out_all(int nv, int nvp, int64_t N, int nmesh, const int64_t *mesh_off,
                             const int32_t *grank, const double *U, double *dst, cudaStream_t s) {
   permute_out_all_kernel<<<grid_for(N, 256), 256, 0, s>>>(nv, nvp, N, nmesh, mesh_off, grank, U, dst);
+}
+
+void launch_time_advance(double *time, const double *dt, int nmesh, cudaStream_t s) {
+  time_advance_kernel<<<grid_for(nmesh, 64), 64, 0, s>>>(time, dt, nmesh);
 }
 
 void launch_dt_reset(const KArgs &a, cudaStream_t s) {

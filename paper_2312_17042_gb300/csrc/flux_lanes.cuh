@@ -38,16 +38,11 @@ __global__ void __launch_bounds__(256) flux_lanes_kernel(const KArgs a) {
   load16<T, FB>(Uf + (i * NF + f) * FB, uI);
   if (j >= 0) {
     load16<T, FB>(Uf + (j * NF + fj) * FB, uO);
-  } else if ((meta >> (kMetaWallShift + f)) & 1u) {  // reflective wall: the mirror image
+  } else {  // boundary face: its kind's outside state
+    double um[NVP];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) wall_mirror<D, T>(uI + q * NV, gf, uO + q * NV);
-  } else {  // transmissive boundary: the cell mean outside
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T m = (T)a.U[i * NVP + v];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) uO[q * NV + v] = m;
-    }
+    for (int v = 0; v < NVP; ++v) um[v] = a.U[i * NVP + v];
+    boundary_state<D, T, NQ>(a, i, (meta >> (kMetaKindShift + 2 * f)) & 3u, gf, uI, um, uO);
   }
   T n[D];
 #pragma unroll

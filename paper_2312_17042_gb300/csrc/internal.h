@@ -66,7 +66,7 @@ struct Mesh {
   int dim = 0;
   int64_t nverts = 0, ncells = 0, offset = 0;  // offset: first global (device) cell index
   double period[3] = {0, 0, 0};
-  bool wall = false;             // boundary faces are reflective walls (else transmissive)
+  std::vector<int8_t> bkind;     // [ncells][nf] kind of each boundary face (CTENO_BOUNDARY_*)
   std::vector<double> xyz;       // [nverts][dim]
   std::vector<int32_t> cv;       // [ncells][dim+1], positively oriented
   std::vector<double> X;         // [ncells][dim+1][dim] unwrapped oriented vertex coordinates

@@ -166,6 +166,12 @@ __global__ void __launch_bounds__(128) setup_kernel(const SetupArgs a) {
     const int32_t nb = a.nbr[i * 4 + f];
     double gv[4] = {0.0, 0.0, 0.0, area};
     for (int j = 0; j < D; ++j) gv[j] = n[j];
+    if constexpr (D == 2) {  // moving-shock boundary face: c_f = xs0 + sy y_mid - x_mid in slot 2
+      if (nb < 0 && ((meta >> (kMetaKindShift + 2 * f)) & 3u) == 3u) {
+        const double xm = 0.5 * (Xi[loc[0]][0] + Xi[loc[1]][0]), ym = 0.5 * (Xi[loc[0]][1] + Xi[loc[1]][1]);
+        gv[2] = a.shock_xs0 + a.shock_sy * ym - xm;
+      }
+    }
     for (int c = 0; c < 4; ++c) {
       a.geo[(i * NF + f) * 4 + c] = gv[c];
       if (a.geo32) a.geo32[(i * NF + f) * 4 + c] = (float)gv[c];

@@ -12,6 +12,8 @@ CTENO_SCHEME_CTENO, CTENO_SCHEME_CTENOZ, CTENO_SCHEME_CWENO, CTENO_SCHEME_TENO =
 CTENO_FP64, CTENO_MIXED = 0, 1
 CTENO_BOUNDARY_TRANSMISSIVE = 0
 CTENO_BOUNDARY_WALL = 1
+CTENO_BOUNDARY_STATE_A = 2
+CTENO_BOUNDARY_SHOCK_AB = 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libcteno.so")
@@ -65,6 +67,10 @@ def load_library():
         "cteno_get_face_states": (I, [V, C.c_int32, V]),
         "cteno_get_stencil": (I, [V, C.c_int32, I64, V, V, V]),
         "cteno_info": (I, [V, C.c_int32, V]),
+        "cteno_boundary_region": (I, [V, C.c_int32, V, V, I]),
+        "cteno_boundary_states": (I, [V, V, V, D, D, D]),
+        "cteno_set_time": (I, [V, D]),
+        "cteno_get_time": (I, [V, V]),
         "cteno_sync": (I, [V, P(I64)]),
         "cteno_set_launch": (I, [V, I, I]),
         "cteno_autotune": (I, [V, V]),
@@ -233,6 +239,28 @@ def cteno_get_stencil(ctx, mesh_id: int, cell: int, with_admissibility: bool = T
     return central, dirm, dok
 
 
+def cteno_boundary_region(ctx, mesh_id: int, lo, hi, kind: int):
+    lo = np.ascontiguousarray(lo, np.float64)
+    hi = np.ascontiguousarray(hi, np.float64)
+    _check(ctx, load_library().cteno_boundary_region(ctx, mesh_id, _ptr(lo), _ptr(hi), int(kind)))
+
+
+def cteno_boundary_states(ctx, A, B, xs0: float = 0.0, sy: float = 0.0, vs: float = 0.0):
+    A = np.ascontiguousarray(A, np.float64)
+    B = np.ascontiguousarray(B, np.float64)
+    _check(ctx, load_library().cteno_boundary_states(ctx, _ptr(A), _ptr(B), float(xs0), float(sy), float(vs)))
+
+
+def cteno_set_time(ctx, t: float):
+    _check(ctx, load_library().cteno_set_time(ctx, float(t)))
+
+
+def cteno_get_time(ctx) -> np.ndarray:
+    out = np.empty(cteno_info(ctx, -1)[0])
+    _check(ctx, load_library().cteno_get_time(ctx, _ptr(out)))
+    return out
+
+
 def cteno_info(ctx, mesh_id: int = -1) -> np.ndarray:
     out = np.zeros(10, np.int64)
     _check(ctx, load_library().cteno_info(ctx, mesh_id, _ptr(out)))
@@ -307,7 +335,7 @@ class Solver:
     """
 
     def __init__(self, meshes, dim: int, degree: int = 2, scheme: int = 0, precision: int = 0,
-                 stream: int = 0, build: bool = True, boundary: int = 0, **kw):
+                 stream: int = 0, build: bool = True, boundary: int = 0, regions=None, states=None, **kw):
         p = cteno_default_params()
         p.dim, p.degree, p.scheme, p.precision = dim, degree, scheme, precision
         for k, v in kw.items():
@@ -315,6 +343,12 @@ class Solver:
         self.params = p
         self.ctx = cteno_create(p, stream)
         self.mesh_ids = [cteno_mesh_build(self.ctx, m.xyz, m.cells, m.period, boundary) for m in meshes]
+        # boundary regions and states (e.g. workloads.dmr_boundary()): applied to every mesh
+        for lo, hi, kind in (regions or ()):
+            for mid in self.mesh_ids:
+                cteno_boundary_region(self.ctx, mid, lo, hi, kind)
+        if states is not None:
+            cteno_boundary_states(self.ctx, *states)
         if build:
             cteno_stencil_build(self.ctx)
             cteno_lsq_build(self.ctx)

@@ -108,3 +108,19 @@ def test_launch_values_of_the_lane_only_paths_without_gpu():
             assert e.value.code == -1
         native.cteno_set_launch(ctx, 1024 + 256, 8192 + 128)   # lanes + face-based flux
         native.cteno_destroy(ctx)
+
+
+def test_boundary_region_validation_without_gpu():
+    native = _lib()
+    p = native.cteno_default_params()
+    p.dim = 3
+    ctx = native.cteno_create(p)
+    m = W.tet_mesh(3, periodic=False)
+    mid = native.cteno_mesh_build(ctx, m.xyz, m.cells, m.period)
+    native.cteno_boundary_region(ctx, mid, (-1, -1, -1), (2, 2, 0.0), native.CTENO_BOUNDARY_WALL)
+    for kind in (native.CTENO_BOUNDARY_SHOCK_AB, 7, -1):   # the moving shock is 2D only
+        with pytest.raises(native.CtenoError):
+            native.cteno_boundary_region(ctx, mid, (-1, -1, -1), (2, 2, 2), kind)
+    with pytest.raises(native.CtenoError):
+        native.cteno_boundary_region(ctx, 5, (-1, -1, -1), (2, 2, 2), 0)
+    native.cteno_destroy(ctx)

@@ -143,3 +143,33 @@ def test_triple_point_reduced_matches_oracle(degree, scheme):
     print(f"triple point 70x30, degree {degree}, scheme {scheme}: max rel {err:.2e} (tol {tol:.1e})")
     assert err < 10 * tol
     s.close()
+
+
+@pytest.mark.parametrize("degree,lam", [(2, 1e15), (4, 1e15)], ids=["CTENO3", "CTENO5"])
+def test_double_mach_reflection_reduced_matches_oracle(degree, lam):
+    """The double Mach reflection's construction (Sec. 3.3) at 48 x 12 squares (1152 triangles):
+    inflow, wall, moving-shock and transmissive boundary faces, 10 FP64 steps against the oracle;
+    the library's physical time equals the sum of the steps."""
+    native = _native()
+    from oracle import Oracle
+    wl = W.dmr_2d(12)
+    regions, states = W.dmr_boundary()
+    o = Oracle(wl.mesh, degree=degree, scheme=0, lambda1p=lam, cfl=0.4)
+    for lo, hi, kind in regions:
+        o.boundary_region(lo, hi, kind)
+    o.boundary_states(*states)
+    tol = 1e-12
+    if degree >= 4:
+        tol = max(tol, 50 * max(np.linalg.cond(o.lsq(i)[0]) for i in range(wl.mesh.ncells)) * U_EPS)
+    o.set_state(wl.U0)
+    dts = o.run(10)
+    s = _solver(native, [wl.mesh], 2, degree=degree, scheme=0, lambda1p=lam, cfl=0.4, regions=regions,
+                states=states)
+    s.set_state(wl.U0)
+    s.run(10)
+    err = _relerr(s.get_state(), o.get_state())
+    t = native.cteno_get_time(s.ctx)[0]
+    print(f"DMR 48x12, degree {degree}: max rel {err:.2e} (tol {tol:.1e}), t = {t:.6f}")
+    assert err < 10 * tol
+    assert abs(t - dts.sum()) < 1e-14 and abs(o.time() - dts.sum()) < 1e-14
+    s.close()

@@ -114,3 +114,55 @@ def test_rk4_step_of_a_uniform_flow_is_exact():
     o.set_state(U)
     o.run(3, 0.01)
     assert np.abs(o.get_state() - U).max() < 1e-14
+
+
+def test_fixed_state_boundary_keeps_a_matching_uniform_flow():
+    """Every boundary face of the fixed-state kind: with A equal to the interior uniform state the
+    residual vanishes to rounding; with another A exactly the cells that own a boundary face move."""
+    mesh = W.tri_mesh(12, 6, ly=0.5, periodic=False)
+    U = _uniform(mesh, 1.3, [0.7, -0.4], 2.0)
+    o = Oracle(mesh, degree=2)
+    o.boundary_region((-1, -1), (2, 2), 2)
+    o.boundary_states(U[:, 0], U[:, 0])
+    o.set_state(U)
+    assert np.abs(o.residual()).max() < 1e-12
+    o.boundary_states(_uniform(mesh, 1.0, [0.0, 0.0], 1.0)[:, 0], U[:, 0])
+    R = o.residual()
+    touched = (o.geometry()["nbr"] < 0).any(axis=1)
+    assert np.array_equal(np.abs(R).max(axis=0) > 1e-12, touched)
+
+
+def test_moving_shock_boundary_switches_at_the_line():
+    """Kind 3 on every boundary face, line x = 0.2 + 0.5 t (xs0 = 0.2, sy = 0, vs = 0.5), A equal to
+    the interior state, B another: only cells with a boundary face whose midpoint lies right of the
+    line at the stage's time see B, so their residual is the only nonzero one; one step later the
+    line has moved by 0.5 dt and fewer faces see B."""
+    mesh = W.tri_mesh(16, 4, ly=0.25, periodic=False, jitter=0.0)
+    U = _uniform(mesh, 1.0, [0.0, 0.0], 1.0)
+    B = _uniform(mesh, 0.5, [0.0, 0.0], 0.4)[:, 0]
+    o = Oracle(mesh, degree=2)
+    o.boundary_region((-1, -1), (2, 2), 3)
+    o.boundary_states(U[:, 0], B, 0.2, 0.0, 0.5)
+    g = o.geometry()
+    cells = g["cells"]
+    xyz = mesh.xyz
+    nb = g["nbr"]
+
+    def expected(t):
+        hit = np.zeros(mesh.ncells, bool)
+        for i in range(mesh.ncells):
+            for f in range(3):
+                if nb[i, f] < 0:
+                    mid = np.delete(xyz[cells[i]], f, axis=0).mean(0)
+                    hit[i] |= not (0.2 + 0.5 * t > mid[0])
+        return hit
+    for t in (0.0, 0.3):
+        o.set_time(t)
+        o.set_state(U)
+        R = o.residual()
+        got = np.abs(R).max(axis=0) > 1e-12
+        assert np.array_equal(got, expected(t)), t
+    assert expected(0.0).sum() > expected(0.3).sum() > 0
+    o.set_time(0.0)
+    o.step(0.01)
+    assert abs(o.time() - 0.01) < 1e-16

@@ -332,6 +332,42 @@ def triple_point_2d(nx: int = 500, ny: int = 215, seed: int = 0, jitter: float =
                     dict(dim=2, cfl=0.4, boundary="wall"))
 
 
+# Double Mach reflection (Sec. 3.3): a Mach-10 shock at 60 degrees from x = 1/6 on the bottom wall.
+DMR_PRE = (1.4, 0.0, 0.0, 1.0)
+# post-shock state: rho and velocity as printed (8.25 (cos 30, -sin 30)); the pressure from the
+# Rankine-Hugoniot condition of the Mach-10 shock into DMR_PRE, (2 gamma M^2 - (gamma - 1)) / (gamma + 1)
+# = 116.5 (the paper prints 116.8333, which that shock does not produce)
+DMR_POST = (8.0, 8.25 * np.cos(np.pi / 6), -8.25 * np.sin(np.pi / 6), 116.5)
+
+
+def dmr_2d(ny: int = 20, seed: int = 0, jitter: float = 0.1) -> Workload:
+    """[0,4]x[0,1], 4 ny x ny squares -> 8 ny^2 triangles (ny = 215: 369800, ny = 299: 715208, the
+    paper's 369604 and 714138), post-shock state where y >= sqrt(3) (x - 1/6), pre-shock elsewhere;
+    boundaries from dmr_boundary()."""
+    mesh = tri_mesh(4 * ny, ny, 4.0, 1.0, periodic=False, jitter=jitter, seed=seed)
+
+    def f(x):
+        post = x[:, 1] >= np.sqrt(3.0) * (x[:, 0] - 1.0 / 6.0)
+        return np.where(post[:, None], np.array(DMR_POST), np.array(DMR_PRE))
+    return Workload(f"dmr_2d_{4 * ny}x{ny}", mesh, cell_average(mesh, f, n_rule=6), dict(dim=2, cfl=0.4))
+
+
+def dmr_boundary():
+    """(regions, states) of the double Mach reflection: boundary faces by the box their midpoint
+    lies in -- left x = 0 and bottom x < 1/6 the post-shock state (kind 2), bottom x >= 1/6 a
+    reflective wall (kind 1), top y = 1 the moving shock (kind 3: post-shock left of the line
+    x = 1/6 + (y + 20 t) / sqrt(3), pre-shock right of it), right x = 4 transmissive (kind 0, the
+    default) -- and the states (A = post-shock, B = pre-shock, conserved) with the line's xs0, sy, vs."""
+    eps = 1e-9
+    regions = [((-1.0, -1.0), (eps, 2.0), 2),
+               ((-1.0, -1.0), (1.0 / 6.0, eps), 2),
+               ((1.0 / 6.0, -1.0), (5.0, eps), 1),
+               ((-1.0, 1.0 - eps), (5.0, 2.0), 3)]
+    A = primitive_to_conserved(np.array([DMR_POST]))[0]
+    B = primitive_to_conserved(np.array([DMR_PRE]))[0]
+    return regions, (A, B, 1.0 / 6.0, 1.0 / np.sqrt(3.0), 20.0 / np.sqrt(3.0))
+
+
 def quadrant_states(seed: int, k: int) -> np.ndarray:
     """Per-quadrant primitive states of batch member k: rho, p ~ U[0.1,2], u, v ~ U[-1,1]."""
     rng = SplitMix64(seed * 1000003 + 7919 * (k + 1))
