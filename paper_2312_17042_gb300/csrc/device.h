@@ -214,8 +214,7 @@ inline long long recon_stream_smem(int d, int degree, int warps, int stages) {
   const int M = 2 * (nk + 1), nv = d + 2, cpw = 32 / nv, mc = (M % 8 == 0) ? 8 : 4;
   const long long stage = (long long)cpw * mc * nk * 4;
   const long long hdr = (long long)cpw * (d + 1) * lay_pds(d) * 4 + (long long)cpw * M * 4;
-  const long long nphi = d == 3 ? (long long)(d + 1) * 6 * 4 * nk : 1;
-  const long long phi = (nphi * 4 + 15) / 16 * 16;
+  const long long phi = 16;  // no face-value table (see StreamShape)
   return phi + (long long)warps * (2 * hdr + stages * stage) + (long long)warps * (2 + stages) * 8 + 8;
 }
 // Launch value -> (warps, stages) of the streamed lane schedule, or warps = 0.

@@ -52,6 +52,7 @@ struct Tables {
   // permutation p of its local vertices
   double Phi[kMaxNF][kMaxPerm][kMaxNQ][kMaxNK] = {};
   double fw[kMaxNQ] = {};               // face weights, sum 1
+  double fbary[kMaxNQ][3] = {};         // face points, barycentric in the sorted face vertices
   // collapsed Gauss-Jacobi rule on the unit reference simplex, exact to degree max(3, r)
   int nvq = 0;
   double vq[kMaxVQ][3] = {};            // reference coordinates

@@ -42,6 +42,11 @@ __constant__ float c_O_r2f[kLowNK * kLowNK], c_O_r3f[kLowNK * kLowNK];
 __constant__ double c_Phi2_r2d[3 * 2 * kLowNK], c_Phi2_r3d[3 * 2 * kLowNK];
 __constant__ float c_Phi2_r2f[3 * 2 * kLowNK], c_Phi2_r3f[3 * 2 * kLowNK];
 
+// 3D, FP32: the face rule's points in barycentric coordinates of the face's sorted vertices and
+// the basis means psibar_k, for the face values of the polynomial evaluated at the point.
+__constant__ float c_fbary3f[4 * 3];
+__constant__ float c_psibar3_r2f[kLowNK], c_psibar3_r3f[kLowNK];
+
 template <typename T, int R>
 __device__ __forceinline__ T cO(int idx) {
   if constexpr (R == 2) {
@@ -78,7 +83,17 @@ inline cudaError_t upload_recon_tables(int dim, int degree, const Tables &t, cud
           Pd2[(f * 2 + q) * t.nk + k] = t.Phi[f][0][q][k];
           Pf2[(f * 2 + q) * t.nk + k] = (float)t.Phi[f][0][q][k];
         }
+  float fb[4 * 3] = {}, pb[kLowNK] = {};
+  if (dim == 3) {
+    for (int q = 0; q < 4; ++q)
+      for (int j = 0; j < 3; ++j) fb[q * 3 + j] = (float)t.fbary[q][j];
+    for (int k = 0; k < t.nk; ++k) pb[k] = (float)t.psibar[k];
+  }
   cudaError_t e;
+  if ((e = cudaMemcpyToSymbolAsync(c_fbary3f, fb, sizeof(fb), 0, cudaMemcpyHostToDevice, s))) return e;
+  if ((e = cudaMemcpyToSymbolAsync(degree == 2 ? c_psibar3_r2f : c_psibar3_r3f, pb, sizeof(pb), 0,
+                                   cudaMemcpyHostToDevice, s)))
+    return e;
   if (degree == 2) {
     if ((e = cudaMemcpyToSymbolAsync(c_O_r2d, Od, sizeof(Od), 0, cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaMemcpyToSymbolAsync(c_O_r2f, Of, sizeof(Of), 0, cudaMemcpyHostToDevice, s))) return e;
@@ -830,6 +845,108 @@ __device__ __forceinline__ void euler_eigen_rows(const T (&ub)[D + 2], const T (
 // for each face, lane v takes field w = v of W = L U (L from the cell's mean and the face's outward
 // normal), projects the conserved coefficients by shuffles (the least squares are linear in the
 // data), selects, evaluates W at the face's points and transforms back, U = R W.
+// Face values for lane_faces: value(f, q, a, init) = init + sum_k phi_k(x_fq) a_k at point q of
+// local face f, with offset(a) subtracted from init first. PhiTab reads phi_k = psi_k - psibar_k
+// from a table (offset 0; the sum in k order, from init).
+template <typename F>
+struct PhiTab {
+  F tab;
+  template <int NK, typename T>
+  __device__ __forceinline__ T value(int f, int q, const T (&a)[NK], T init) const {
+#pragma unroll
+    for (int k = 0; k < NK; ++k) init += tab(f, q, k) * a[k];
+    return init;
+  }
+  template <int NK, typename T>
+  __device__ __forceinline__ T offset(const T (&)[NK]) const { return (T)0; }
+};
+template <typename F>
+__device__ __forceinline__ PhiTab<F> phi_tab(F f) { return PhiTab<F>{f}; }
+
+// Sorted position (0..2) of local vertex c + 1 (c = 0..2) on local face f of a tetrahedron, or 3
+// when the face does not hold it, for each of the six orders p of the face's vertex slots (the
+// lexicographic permutations, as the host tables number them): 2 bits per c, 6 bits per p.
+__host__ __device__ constexpr uint64_t tet_face_positions(int f) {
+  int slots[3] = {0, 0, 0}, ns = 0;
+  for (int a = 0; a < 4; ++a)
+    if (a != f) slots[ns++] = a;
+  const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  uint64_t bits = 0;
+  for (int p = 0; p < 6; ++p)
+    for (int c = 0; c < 3; ++c) {
+      uint64_t pos = 3;
+      for (int j = 0; j < 3; ++j)
+        if (slots[P[p][j]] == c + 1) pos = (uint64_t)j;
+      bits |= pos << (6 * p + 2 * c);
+    }
+  return bits;
+}
+template <int F>
+struct TetFacePos {
+  static constexpr uint64_t bits = tet_face_positions(F);
+};
+// Index of the monomial x^i y^j z^l (1 <= i + j + l) in the basis order: graded, within a degree
+// by the z then the y power.
+__host__ __device__ constexpr int mono_index3(int i, int j, int l) {
+  const int t = i + j + l;
+  int k = (t + 2) * (t + 1) * t / 6 - 1;  // the monomials of degrees 1 .. t - 1
+  for (int c = 0; c < l; ++c) k += t - c + 1;
+  return k + j;
+}
+
+// 3D, FP32: the polynomial at the face point from the point's reference coordinates (xi_c = the
+// barycentric weight of the sorted face vertex that is local vertex c + 1; local vertex 0 is the
+// origin), offset sum_k psibar_k a_k. Nested Horner in x, y, z: one FMA per monomial. On face
+// f >= 1 the coordinate f - 1 is zero and its monomials are skipped (exactly the value at zero).
+// The same polynomial as the table, without its per-cell permutation index: no shared memory.
+template <int R>
+struct PhiMono3 {
+  uint32_t perm;  // the cell's face orders, 3 bits per face
+  template <int NK>
+  __device__ __forceinline__ float value(int f, int q, const float (&a)[NK], float init) const {
+    const uint64_t fb = f == 0 ? TetFacePos<0>::bits
+                      : f == 1 ? TetFacePos<1>::bits
+                      : f == 2 ? TetFacePos<2>::bits : TetFacePos<3>::bits;
+    const int p = (int)((perm >> (3 * f)) & 7u);
+    const uint32_t jp = (uint32_t)(fb >> (6 * p)) & 63u;
+    const float b0 = c_fbary3f[q * 3], b1 = c_fbary3f[q * 3 + 1], b2 = c_fbary3f[q * 3 + 2];
+    // a coordinate whose vertex is on the face takes one of the three weights
+    auto coord = [&](uint32_t j) { return j == 0u ? b0 : j == 1u ? b1 : b2; };
+    const int zc = f - 1;  // the coordinate that vanishes on this face (none for f = 0)
+    const float x = zc == 0 ? 0.0f : coord(jp & 3u);
+    const float y = zc == 1 ? 0.0f : coord((jp >> 2) & 3u);
+    const float z = zc == 2 ? 0.0f : coord((jp >> 4) & 3u);
+    const int imax = zc == 0 ? 0 : R;
+    float px = 0.0f;
+#pragma unroll
+    for (int i = R; i >= 0; --i) {
+      if (i > imax) continue;
+      const int jmax = zc == 1 ? 0 : R - i;
+      float qy = 0.0f;
+#pragma unroll
+      for (int j = R; j >= 0; --j) {
+        if (j > jmax) continue;
+        const int lmax = zc == 2 ? 0 : R - i - j;
+        // sum_l a_ijl z^l, the constant term (i = j = l = 0) being init
+        float sz = (i + j + lmax == 0) ? init : a[mono_index3(i, j, lmax)];
+#pragma unroll
+        for (int l = R - 1; l >= 0; --l)
+          if (l < lmax) sz = fmaf(sz, z, (i + j + l == 0) ? init : a[mono_index3(i, j, l)]);
+        qy = (j == jmax) ? sz : fmaf(qy, y, sz);
+      }
+      px = (i == imax) ? qy : fmaf(px, x, qy);
+    }
+    return px;
+  }
+  template <int NK>
+  __device__ __forceinline__ float offset(const float (&a)[NK]) const {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) s += (R == 2 ? c_psibar3_r2f[k] : c_psibar3_r3f[k]) * a[k];
+    return s;
+  }
+};
+
 template <int D, int NK, int KD, int NQ, typename T, int SCHEME, bool CHR, typename OC, typename SID,
           typename PHI>
 __device__ __forceinline__ void lane_faces(const KArgs &a, const int64_t i, const bool active, const int v,
@@ -847,13 +964,12 @@ __device__ __forceinline__ void lane_faces(const KArgs &a, const int64_t i, cons
   if constexpr (!CHR) {
     const uint32_t bits = lane_select<NF, NK, KD, T, SCHEME>(a, adm, ao, ad, oc, sid);
     if (a.flags && active) a.flags[v * N + i] = (uint8_t)bits;
+    const T off = phi.offset(ao);
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
-        T val = (T)L0;
-#pragma unroll
-        for (int k = 0; k < NK; ++k) val += phi(f, q, k) * ao[k];
+        T val = phi.value(f, q, ao, (T)L0 - off);
         val += U0;
         fv[f][q] = val;
         // every lane takes part in the test's shuffles (no short-circuit before it)
@@ -900,10 +1016,10 @@ __device__ __forceinline__ void lane_faces(const KArgs &a, const int64_t i, cons
       const uint32_t bits = lane_select<NF, NK, KD, T, SCHEME>(a, adm, aw, adw, oc, sid);
       if (a.flags && active) a.flags[(f * NV + v) * N + i] = (uint8_t)bits;
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        T W = wbar;
+      const T off = phi.offset(aw);
 #pragma unroll
-        for (int k = 0; k < NK; ++k) W += phi(f, q, k) * aw[k];
+      for (int q = 0; q < NQ; ++q) {
+        const T W = phi.value(f, q, aw, wbar - off);
         T val = (T)0;
 #pragma unroll
         for (int j = 0; j < NV; ++j) val += Rv[j] * __shfl_sync(0xffffffffu, W, base + j);
@@ -955,15 +1071,21 @@ __device__ __forceinline__ void lane_finish(const KArgs &a, const int64_t i, con
     for (int k = 0; k < D; ++k) s += adf[k] * adf[k];
     return s * INV_FACT;
   };
-  auto phi = [&](int f, int q, int k) -> T {
-    if constexpr (D == 2) {
-      return cPhi2<T, R>((f * 2 + q) * NK + k);
-    } else {
-      const int p = (perm >> (3 * f)) & 7u;
-      return sPhi[((f * NP + p) * NQ + q) * NK + k];
-    }
-  };
-  lane_faces<D, NK, D, NQ, T, SCHEME, CHR>(a, i, active, v, base, ao, ad, info, U0, L0, oc, sid, phi);
+  if constexpr (D == 3 && sizeof(T) == 4) {
+    lane_faces<D, NK, D, NQ, T, SCHEME, CHR>(a, i, active, v, base, ao, ad, info, U0, L0, oc, sid,
+                                             PhiMono3<R>{perm});
+  } else {
+    auto phi = [&](int f, int q, int k) -> T {
+      if constexpr (D == 2) {
+        return cPhi2<T, R>((f * 2 + q) * NK + k);
+      } else {
+        const int p = (perm >> (3 * f)) & 7u;
+        return sPhi[((f * NP + p) * NQ + q) * NK + k];
+      }
+    };
+    lane_faces<D, NK, D, NQ, T, SCHEME, CHR>(a, i, active, v, base, ao, ad, info, U0, L0, oc, sid,
+                                             phi_tab(phi));
+  }
 }
 
 // One cell of the variable-per-lane schedule, seen from lane v of its group (first lane base);
@@ -1085,10 +1207,11 @@ __global__ void __launch_bounds__(256) recon_lanes_kernel(const KArgs a) {
   using L = Lay<D>;
   constexpr int NV = L::NV, NF = L::NF, NQ = L::NQ, PDS = L::PDS;
   constexpr int NK = S::NK, M = S::M, NP = S::NP;
-  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
+  constexpr bool TAB = D == 3 && sizeof(T) == 8;  // FP32 lanes: no face-value table
+  constexpr int NPHI = TAB ? NF * NP * NQ * NK : 1;
   constexpr int CPW = 32 / NV;  // cells per warp
   __shared__ T sPhi[NPHI];
-  if constexpr (D == 3) {
+  if constexpr (TAB) {
     const DevTables &tb = *a.tab;
     for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
       const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
@@ -1141,7 +1264,8 @@ __global__ void __launch_bounds__(256) recon_staged_kernel(const KArgs a) {
   using B = StagedRecord<D, R, T>;
   constexpr int NV = L::NV, NF = L::NF, NQ = L::NQ, PDS = L::PDS;
   constexpr int NK = S::NK, M = S::M, NP = S::NP;
-  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
+  constexpr bool TAB = D == 3 && !LANES;  // FP32 lanes: no face-value table
+  constexpr int NPHI = TAB ? NF * NP * NQ * NK : 1;
   constexpr int CPW = 32 / NV;
   __shared__ T sPhi[NPHI];
   __shared__ __align__(8) uint64_t bar[3];  // two stages; bar[2] only for the test hook
@@ -1172,7 +1296,7 @@ __global__ void __launch_bounds__(256) recon_staged_kernel(const KArgs a) {
     mbar_init(&bar[2], 1);
     fence_barrier_init();
   }
-  if constexpr (D == 3) {
+  if constexpr (TAB) {
     const DevTables &tb = *a.tab;
     for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
       const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
@@ -1261,7 +1385,8 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
   using B = StagedRecord<D, R, T>;
   constexpr int NV = L::NV, NVP = L::NVP, NF = L::NF, NQ = L::NQ, PDS = L::PDS;
   constexpr int NK = S::NK, M = S::M, NP = S::NP;
-  constexpr int NPHI = (D == 3) ? NF * NP * NQ * NK : 1;
+  constexpr bool TAB = false;  // FP32 lanes: no face-value table
+  constexpr int NPHI = TAB ? NF * NP * NQ * NK : 1;
   constexpr int CPW = 32 / NV, C = kHaloWarps * CPW;
   constexpr int MS = (M + 1 + 7) / 8 * 8;   // local ids per cell
   constexpr int HS = NVP * 2 * 4;           // bytes of one member state (FP32 pairs)
@@ -1327,7 +1452,7 @@ __global__ void __launch_bounds__(kHaloWarps * 32) recon_halo_kernel(const KArgs
     mbar_init(&bar[2], 1);
     fence_barrier_init();
   }
-  if constexpr (D == 3) {
+  if constexpr (TAB) {
     const DevTables &tb = *a.tab;
     for (int t = threadIdx.x; t < NPHI; t += blockDim.x) {
       const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
@@ -1431,8 +1556,7 @@ struct StreamShape {
   static constexpr int HST = CPW * S::M * 4;                  //   stencil ids
   static constexpr int HDR = HPD + HST;
   static constexpr int WARP_BYTES = 2 * HDR + NST * STAGE;
-  static constexpr int NPHI = (D == 3) ? L::NF * S::NP * L::NQ * S::NK : 1;
-  static constexpr int PHI_BYTES = (NPHI * 4 + 15) / 16 * 16;
+  static constexpr int PHI_BYTES = 16;  // FP32 face values: the polynomial at the point, no table
   static_assert(S::M % MC == 0 && CHUNK_CELL % 16 == 0 && HPD % 16 == 0 && HST % 16 == 0,
                 "bulk copies need 16-byte spans");
 };
@@ -1505,13 +1629,6 @@ __global__ void __launch_bounds__(512, 1) recon_stream_kernel(const KArgs a) {
     for (int b = 0; b < 2 + NST; ++b) mbar_init(&hbar[b], 1);
     if (threadIdx.x == 0) mbar_init(tbar, 1);
     fence_barrier_init();
-  }
-  if constexpr (D == 3) {
-    const DevTables &tb = *a.tab;
-    for (int t = threadIdx.x; t < Q::NPHI; t += blockDim.x) {
-      const int k = t % NK, q = (t / NK) % NQ, p = (t / (NK * NQ)) % NP, f = t / (NK * NQ * NP);
-      sPhi[t] = (T)tb.Phi[f][p][q][k];
-    }
   }
   __syncthreads();
   // the operator records do not depend on the previous kernel: their copies start now

@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(256) recon_high_kernel(const KArgs a) {
     return s;
   };
   auto phi = [](int f, int q, int k) { return cPhiH<T, R>((f * NQ + q) * NK + k); };
-  lane_faces<2, NK, KD, NQ, T, SCHEME, CHR>(a, i, active, v, base, ao, ad, info, U0, L0, oc, sid, phi);
+  lane_faces<2, NK, KD, NQ, T, SCHEME, CHR>(a, i, active, v, base, ao, ad, info, U0, L0, oc, sid,
+                                           phi_tab(phi));
   // CFL time step bookkeeping at the first stage of a step: dt[next] -> dt[cur]
   if (a.dt_swap && blockIdx.x == 0)
     for (int t = threadIdx.x; t < a.nmesh; t += blockDim.x) {

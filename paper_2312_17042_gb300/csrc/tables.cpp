@@ -213,7 +213,7 @@ void build_tables(int dim, int degree, Tables *t) {
   // face rule in barycentric coordinates of the face's vertices, sorted by global id:
   // 2D: n-point Gauss-Legendre along the edge (symmetric: the reversed edge visits the same
   // points in the opposite order); 3D: collapsed 2x2 (Gauss-Jacobi (1-u) x Legendre)
-  double bary[kMaxNQ][3] = {};
+  double (&bary)[kMaxNQ][3] = t->fbary;
   if (d == 2 && t->nq > 2) {
     double xl[8], wl[8];
     gauss_jacobi(t->nq, 0, xl, wl);

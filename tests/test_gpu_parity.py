@@ -229,7 +229,7 @@ def _stream_smem(d, degree, warps, stages=3):
     cpw = 32 // (d + 2)
     mc = 8 if M % 8 == 0 else 4
     hdr = cpw * (d + 1) * (8 if d == 2 else 20) * 4 + cpw * M * 4
-    phi = (((d + 1) * 6 * 4 * nk if d == 3 else 1) * 4 + 15) // 16 * 16
+    phi = 16   # no face-value table: the FP32 face values come from the polynomial at the point
     return phi + warps * (2 * hdr + stages * cpw * mc * nk * 4) + warps * (2 + stages) * 8 + 8
 
 
