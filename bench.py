@@ -108,7 +108,7 @@ def make_case(name, n=0):
         return Case(name, f"double Mach reflection (Sec. 3.3), [0,4]x[0,1], {4 * (n or 299)}x{n or 299} squares -> "
                     f"{wl.mesh.ncells} triangles (the paper's timing mesh: 714138), inflow / wall / moving-shock / "
                     "transmissive boundaries, lambda_1' = 1e15, CFL 0.4", [wl.mesh], [wl.U0], 2, 0, 4, 0.4,
-                    [(2, 4), (3, 4), (0, 4), (1, 4), (0, 6), (1, 6)], (0.5, 0.25),
+                    [(2, 4), (3, 4), (0, 4), (1, 4), (2, 6), (3, 6), (0, 6), (1, 6)], (0.5, 0.25),
                     extra=dict(lambda1p=1e15, regions=regions, states=states))
     if name == "triple_point_2d":
         wl = W.triple_point_2d()
