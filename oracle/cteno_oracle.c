@@ -16,7 +16,10 @@
  * integral; least squares against numpy.linalg.lstsq; polynomial reproduction; mean
  * preservation; free-stream preservation; HLLC consistency, symmetry and exact contact
  * resolution; selection invariants and hand cases; conservation; convergence order on the
- * smooth density wave (Table 3 of the paper); Sod exact-solution envelope.
+ * smooth density wave (Table 3 of the paper); Sod exact-solution envelope; the Euler flux
+ * Jacobian's eigenvectors (they diagonalise it; smooth fields and contacts; Sod exact solution);
+ * reflective walls (closed-box conservation, the exact reflected-shock state); the orders of
+ * the RK3 and RK4 steps in time; which faces see the fixed and the moving-shock states.
  * Parity unpinned: the exact stencil membership (readings of the SBC and directional-stencil
  * rules, which the paper defers to its reference [30]) is fixed only by this file.
  *
