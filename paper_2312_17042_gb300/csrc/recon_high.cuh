@@ -105,7 +105,7 @@ inline cudaError_t upload_high_tables(const Tables &t, cudaStream_t s) {
 // One block of 8-cell warps; lane v of group grp reconstructs variable v of cell 8 w + grp (the
 // last cell shadows the lanes past the end and stores nothing).
 template <int R, typename T, int SCHEME, bool CHR>
-__global__ void __launch_bounds__(256) recon_high_kernel(const KArgs a) {
+__device__ __forceinline__ void recon_high_body(const KArgs &a) {
   using H = HighShape<R>;
   using DR = Dir<2, R>;
   constexpr int NV = 4, NVP = 4, NF = 3, CPW = 8;
@@ -215,6 +215,19 @@ __global__ void __launch_bounds__(256) recon_high_kernel(const KArgs a) {
       a.dt[t] = a.dt[a.nmesh + t];
       a.dt[a.nmesh + t] = 1e300;
     }
+}
+
+template <int R, typename T, int SCHEME, bool CHR>
+__global__ void __launch_bounds__(256) recon_high_kernel(const KArgs a) {
+  recon_high_body<R, T, SCHEME, CHR>(a);
+}
+
+// The FP32 degree-4 body compiled for at most 64 registers per thread (launch value kHighOcc + b):
+// 32 resident warps per SM instead of 24, for a kernel that waits on its record loads and
+// neighbour gathers.
+template <int SCHEME>
+__global__ void __launch_bounds__(256, 4) recon_high_kernel_r4occ(const KArgs a) {
+  recon_high_body<4, float, SCHEME, false>(a);
 }
 
 }  // namespace cteno

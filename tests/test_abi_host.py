@@ -102,7 +102,7 @@ def test_launch_values_of_the_lane_only_paths_without_gpu():
             setattr(p, k, v)
         p.precision = 1
         ctx = native.cteno_create(p)
-        for bad in (128, -64, 2048 + 64, 3072 + 128, 4096, 5120 + 8, 6144 + 4):
+        for bad in (128, -64, 2048 + 64, 3072 + 128, 4096, 5120 + 8, 6144 + 4, 1536 + 64):
             with pytest.raises(native.CtenoError) as e:
                 native.cteno_set_launch(ctx, bad, 0)
             assert e.value.code == -1
