@@ -263,7 +263,7 @@ def recon_kernel_name(dim, degree, scheme, precision, launch):
     """Name of the reconstruction kernel a launch value selects."""
     args = f"{dim},{degree},{'float' if precision else 'double'},{SCHEMES[scheme]}"
     if degree >= 4 and launch >= 1536:
-        return f"recon_high_kernel_r4occ<{SCHEMES[scheme]}> (64 registers) x{launch - 1536}"
+        return f"recon_high_kernel_occ<{degree},{SCHEMES[scheme]}> (64 registers) x{launch - 1536}"
     if degree >= 4:
         return f"recon_high_kernel<{degree},{'float' if precision else 'double'},{SCHEMES[scheme]}> x{launch - 1024}"
     if 7168 < launch <= 7176 or 7200 < launch <= 7208:

@@ -287,9 +287,9 @@ int cteno_sync(cteno_ctx *ctx, int64_t *guard_count);
  * [32, 256]) selects the face-based schedule: HLLC once per face, in its owner's orientation, into
  * a face-flux array, then a per-cell gather and update (results bit-identical to the per-cell
  * schedules). At central degrees 4 to 6 and with the characteristic reconstruction the reconstruction
- * takes 1024 + b only (default 1024 + 128), and at degree 4 on the mixed path without the
- * characteristic reconstruction also 1536 + b (the same schedule compiled for at most 64 registers
- * per thread, so that more warps share an SM); every other reconstruction value is refused with
+ * takes 1024 + b only (default 1024 + 128), and on the mixed path without the characteristic
+ * reconstruction also 1536 + b (the same schedule compiled for at most 64 registers per thread, so
+ * that more warps share an SM); every other reconstruction value is refused with
  * CTENO_ERR_ARG. */
 int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block);
 

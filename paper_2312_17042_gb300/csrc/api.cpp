@@ -967,7 +967,7 @@ int cteno_set_launch(cteno_ctx *ctx, int recon_block, int flux_block) {
     if (b == 0) return true;
     if (recon && ctx->p.degree >= 4) {  // degrees 4 to 6: the variable-per-lane schedule only
       if (b >= kHighOcc + 32 && b <= kHighOcc + 256 && b % 32 == 0)  // its 64-register build
-        return ctx->p.degree == 4 && ctx->fp32 && !ctx->p.characteristic;
+        return ctx->fp32 && !ctx->p.characteristic;
       return b >= kLaneSchedule + 32 && b <= kLaneSchedule + 256 && b % 32 == 0;
     }
     // the characteristic reconstruction: the variable-per-lane schedule only
@@ -1050,7 +1050,7 @@ int cteno_autotune(cteno_ctx *ctx, int32_t *best_out) {
   for (int b : {128, 256}) cand.push_back(kLaneSchedule + b);
   std::vector<int> rcand = cand;
   if (ctx->p.degree >= 4) rcand = {kLaneSchedule + 64, kLaneSchedule + 128, kLaneSchedule + 256};
-  if (ctx->p.degree == 4 && ctx->fp32 && !ctx->p.characteristic)
+  if (ctx->p.degree >= 4 && ctx->fp32 && !ctx->p.characteristic)
     for (int b : {64, 128, 256}) rcand.push_back(kHighOcc + b);
   // the staged schedules (mixed path) whose two stages fit
   if (ctx->fp32 && ctx->p.degree <= 3)

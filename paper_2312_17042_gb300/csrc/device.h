@@ -267,9 +267,9 @@ inline long long recon_staged_smem(int d, int degree, int fp32, int block) {
 
 void launch_setup(int dim, int degree, const SetupArgs &a, cudaStream_t s);
 // Central degrees 4 to 6 (2D): constant banks and the variable-per-lane reconstruction
-// (recon_2d_high.cu); launch values other than kLaneSchedule + b (and, at degree 4 on the mixed
-// path without the characteristic projection, kHighOcc + b: the same schedule compiled for at
-// most 64 registers per thread) give cudaErrorInvalidValue.
+// (recon_2d_high.cu); launch values other than kLaneSchedule + b (and, on the mixed path without
+// the characteristic projection, kHighOcc + b: the same schedule compiled for at most 64
+// registers per thread) give cudaErrorInvalidValue.
 constexpr int kHighOcc = 1536;
 cudaError_t upload_recon_tables_2d_high(int degree, const Tables &t, cudaStream_t s);
 cudaError_t launch_recon_2d_high(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s);

@@ -4,12 +4,18 @@
 namespace cteno {
 
 cudaError_t launch_recon_2d_high(int degree, int fp32, int scheme, const KArgs &a, int block, cudaStream_t s) {
-  if (block >= kHighOcc + 32 && block <= kHighOcc + 256 && block % 32 == 0) {  // 64-register degree 4
-    if (degree != 4 || !fp32 || a.characteristic) return cudaErrorInvalidValue;
+  if (block >= kHighOcc + 32 && block <= kHighOcc + 256 && block % 32 == 0) {  // the 64-register build
+    if (!fp32 || a.characteristic) return cudaErrorInvalidValue;
     const int threads = block - kHighOcc;
     const unsigned grid = (unsigned)((a.N + (threads / 32) * 8 - 1) / ((threads / 32) * 8));
-    if (scheme == 0) launch_stage_kernel(recon_high_kernel_r4occ<0>, grid, threads, 0, s, a);
-    else launch_stage_kernel(recon_high_kernel_r4occ<1>, grid, threads, 0, s, a);
+#define CTENO_OCC(R, SC) launch_stage_kernel(recon_high_kernel_occ<R, SC>, grid, threads, 0, s, a)
+    if (degree == 4 && scheme == 0) CTENO_OCC(4, 0);
+    if (degree == 4 && scheme == 1) CTENO_OCC(4, 1);
+    if (degree == 5 && scheme == 0) CTENO_OCC(5, 0);
+    if (degree == 5 && scheme == 1) CTENO_OCC(5, 1);
+    if (degree == 6 && scheme == 0) CTENO_OCC(6, 0);
+    if (degree == 6 && scheme == 1) CTENO_OCC(6, 1);
+#undef CTENO_OCC
     return cudaSuccess;
   }
   if (block < kLaneSchedule + 32 || block > kLaneSchedule + 256 || block % 32) return cudaErrorInvalidValue;

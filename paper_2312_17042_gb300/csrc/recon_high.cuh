@@ -222,12 +222,12 @@ __global__ void __launch_bounds__(256) recon_high_kernel(const KArgs a) {
   recon_high_body<R, T, SCHEME, CHR>(a);
 }
 
-// The FP32 degree-4 body compiled for at most 64 registers per thread (launch value kHighOcc + b):
-// 32 resident warps per SM instead of 24, for a kernel that waits on its record loads and
-// neighbour gathers.
-template <int SCHEME>
-__global__ void __launch_bounds__(256, 4) recon_high_kernel_r4occ(const KArgs a) {
-  recon_high_body<4, float, SCHEME, false>(a);
+// The FP32 body compiled for at most 64 registers per thread (launch value kHighOcc + b): 32
+// resident warps per SM instead of 24-28, for a kernel that waits on its record loads and
+// neighbour gathers (a few dozen bytes of spill).
+template <int R, int SCHEME>
+__global__ void __launch_bounds__(256, 4) recon_high_kernel_occ(const KArgs a) {
+  recon_high_body<R, float, SCHEME, false>(a);
 }
 
 }  // namespace cteno

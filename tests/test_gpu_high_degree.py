@@ -202,11 +202,12 @@ def test_orders_and_lambda1p_study():
 
 
 @pytest.mark.parametrize("scheme", [0, 1], ids=["CTENO", "CTENOZ"])
-def test_degree4_64_register_build_matches_default(scheme):
-    """The degree-4 mixed reconstruction compiled for at most 64 registers per thread (launch
+@pytest.mark.parametrize("degree", [4, 5, 6])
+def test_64_register_build_matches_default(degree, scheme):
+    """The mixed reconstruction of degrees 4-6 compiled for at most 64 registers per thread (launch
     values 1536 + b) is the same arithmetic as the default build (1024 + b): face states and the
     update agree on the smeared Sod state and the flags equal the oracle's outside the 1e-4 band;
-    degree 5, the FP64 path and the characteristic reconstruction refuse the launch value."""
+    the FP64 path, the characteristic reconstruction and degree 3 refuse the launch value."""
     native = _native()
     from oracle import Oracle
     wl = W.shock_tube_2d(40, 10)
@@ -214,13 +215,13 @@ def test_degree4_64_register_build_matches_default(scheme):
     o.set_state(wl.U0)
     o.run(8)
     U = o.get_state()
-    o = Oracle(wl.mesh, degree=4, scheme=scheme)
+    o = Oracle(wl.mesh, degree=degree, scheme=scheme)
     o.set_state(U)
     dt = 0.5 * o.dt()
     o.stage(0, dt)
     out = []
     for launch in (1024 + 128, 1536 + 64, 1536 + 256):
-        s = _solver(native, [wl.mesh], 2, degree=4, scheme=scheme, precision=1)
+        s = _solver(native, [wl.mesh], 2, degree=degree, scheme=scheme, precision=1)
         native.cteno_set_launch(s.ctx, launch, 0)
         native.cteno_record_flags(s.ctx, True)
         s.set_state(U)
@@ -232,7 +233,8 @@ def test_degree4_64_register_build_matches_default(scheme):
         assert np.abs(fs - out[0][0]).max() <= 1e-6 * np.abs(out[0][0]).max()
         assert _relerr(Un, out[0][1]) < 1e-6
         assert not ((fl != o.flags()) & ~band).any()
-    for kw in (dict(degree=5, precision=1), dict(degree=4, precision=0), dict(degree=4, precision=1, characteristic=1)):
+    for kw in (dict(degree=3, precision=1), dict(degree=degree, precision=0),
+               dict(degree=degree, precision=1, characteristic=1)):
         s = _solver(native, [wl.mesh], 2, **kw)
         with pytest.raises(native.CtenoError):
             native.cteno_set_launch(s.ctx, 1536 + 64, 0)
