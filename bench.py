@@ -392,28 +392,58 @@ def measure(native, case, scheme, degree, precision, stream, flush, torch, dist,
         out["clocks"] = clk
     if e2e:
         nv = case.dim + 2
-        pinned = torch.empty(nv * case.ncells, dtype=torch.float64, pin_memory=True).numpy()
-        outs = torch.empty(nv * case.ncells, dtype=torch.float64, pin_memory=True).numpy()
+        hin = torch.empty(nv * case.ncells, dtype=torch.float64, pin_memory=True)
+        hout = torch.empty(nv * case.ncells, dtype=torch.float64, pin_memory=True)
+        pinned, outs = hin.numpy(), hout.numpy()
         native.cteno_get_state_all(s.ctx, pinned)
         n_e2e = max(5, min(steps, 50))
         torch.cuda.synchronize()
         t_total = 0.0
+        parts = np.zeros(3)  # state in (host -> device), the step, state out (device -> host), ms
         for it in range(n_e2e + 2):
             flush.zero_()
-            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record()
             native.cteno_set_state_all(s.ctx, pinned)
+            ev[1].record()
             s.run(1)
+            ev[2].record()
             native.cteno_get_state_all(s.ctx, outs)
-            b_.record()
-            b_.synchronize()
+            ev[3].record()
+            ev[3].synchronize()
             if it >= 2:
-                t_total += a.elapsed_time(b_)
+                t_total += ev[0].elapsed_time(ev[3])
+                parts += [ev[j].elapsed_time(ev[j + 1]) for j in range(3)]
         t_total = dist.max(t_total, device="cuda")
+        parts /= n_e2e
+        # the same bytes as one plain copy-engine transfer each way, for comparison
+        dev = torch.empty(pinned.size, dtype=torch.float64, device="cuda")
+        copy_ms = np.zeros(2)
+        for it in range(7):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record()
+            dev.copy_(hin, non_blocking=True)
+            ev[1].record()
+            hout.copy_(dev, non_blocking=True)
+            ev[2].record()
+            ev[2].synchronize()
+            if it >= 2:
+                copy_ms += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])]
+        copy_ms /= 5
+        del dev
         out["e2e"] = {"value": round(whole_job_value(world, case.ncells, n_e2e, t_total), 2), "unit": UNIT,
                       "h2d_bytes_per_step": int(pinned.nbytes), "d2h_bytes_per_step": int(outs.nbytes),
                       "steps": n_e2e,
-                      "api": "cteno_set_state_all(host) + cteno_run(1) + cteno_get_state_all(host), pinned buffers"}
+                      "api": "cteno_set_state_all(host) + cteno_run(1) + cteno_get_state_all(host), pinned buffers",
+                      # where the end-to-end step goes: each call timed with events on the same stream;
+                      # the state calls' rates are host-link rates (the kernels access the page-locked
+                      # buffers directly, permuting to and from the library's cell order on the way)
+                      "ms_state_in": round(float(parts[0]), 4), "ms_step": round(float(parts[1]), 4),
+                      "ms_state_out": round(float(parts[2]), 4),
+                      "h2d_gbs": round(pinned.nbytes / (parts[0] * 1e-3) / 1e9, 1),
+                      "d2h_gbs": round(outs.nbytes / (parts[2] * 1e-3) / 1e9, 1),
+                      "copy_engine_h2d_gbs": round(pinned.nbytes / (copy_ms[0] * 1e-3) / 1e9, 1),
+                      "copy_engine_d2h_gbs": round(outs.nbytes / (copy_ms[1] * 1e-3) / 1e9, 1)}
     s.close()
     return out
 
