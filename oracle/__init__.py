@@ -23,8 +23,14 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    build()
-    lib = C.CDLL(LIB)
+    # CTENO_ORACLE_LIB names another build of the oracle to load instead (the mutation tests point
+    # it at deliberately altered copies to show that the pins catch them)
+    alt = os.environ.get("CTENO_ORACLE_LIB")
+    if alt:
+        lib = C.CDLL(alt)
+    else:
+        build()
+        lib = C.CDLL(LIB)
     V = C.c_void_p
     lib.orc_create.restype = V
     lib.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,

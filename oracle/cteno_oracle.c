@@ -14,12 +14,15 @@
  *
  * Parity pins (tests/test_oracle_*.py): quadrature exactness against the Dirichlet monomial
  * integral; least squares against numpy.linalg.lstsq; polynomial reproduction; mean
- * preservation; free-stream preservation; HLLC consistency, symmetry and exact contact
- * resolution; selection invariants and hand cases; conservation; convergence order on the
+ * preservation; free-stream preservation; HLLC consistency, symmetry, exact contact
+ * resolution and the exact flux of an isolated shock (Roe averages); selection invariants and
+ * closed-form flip points; conservation; convergence order on the
  * smooth density wave (Table 3 of the paper); Sod exact-solution envelope; the Euler flux
  * Jacobian's eigenvectors (they diagonalise it; smooth fields and contacts; Sod exact solution);
  * reflective walls (closed-box conservation, the exact reflected-shock state); the orders of
- * the RK3 and RK4 steps in time; which faces see the fixed and the moving-shock states.
+ * the RK3 and RK4 steps in time; which faces see the fixed and the moving-shock states. Altered
+ * copies of this file (misread exponents, averages, cut-off, Roe averages, RK weights) must fail
+ * those pins (tests/test_oracle_mutations.py).
  * Parity unpinned: the exact stencil membership (readings of the SBC and directional-stencil
  * rules, which the paper defers to its reference [30]) is fixed only by this file.
  *

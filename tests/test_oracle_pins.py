@@ -350,6 +350,43 @@ def test_hllc_resolves_isolated_contact_and_supersonic_upwinding(mk):
     assert np.allclose(o.hllc(uL, uR, n), X.euler_flux(uL, n), rtol=1e-14)
 
 
+@pytest.mark.parametrize("mk", [_oracle2d, _oracle3d], ids=["2d", "3d"])
+@pytest.mark.parametrize("mach", [1.5, 2.0, 4.0])
+def test_hllc_exact_for_an_isolated_shock(mk, mach):
+    """An isolated shock between states that satisfy the Rankine-Hugoniot conditions: Roe's
+    averages (eq. 26) make U_R - U_L an eigenvector of the Roe matrix with the shock speed S as
+    its eigenvalue, so the wave-speed estimate S_R of eq. 25 equals S, the middle speed S_M of
+    eq. 28 equals the post-shock normal velocity and the right star state of eq. 29 equals U_L.
+    In a frame where the interface lies between the post-shock flow and the shock (u_L < 0 < S)
+    the HLLC flux is then exactly the interface flux F(U_L) (= F(U_R) + S (U_L - U_R))."""
+    o = mk()
+    d = o.dim
+    g = 1.4
+    rng = _rng(23)
+    for _ in range(5):
+        n = rng.normal(size=d)
+        n /= np.linalg.norm(n)
+        t = rng.normal(size=d)
+        t -= (t @ n) * n                      # a tangential velocity, equal on both sides
+        rR, pR = rng.uniform(0.5, 2.0), rng.uniform(0.5, 2.0)
+        cR = np.sqrt(g * pR / rR)
+        # normal-shock relations for a shock moving into the resting state R at Mach `mach`
+        S0 = mach * cR
+        rL = rR * (g + 1) * mach ** 2 / ((g - 1) * mach ** 2 + 2)
+        pL = pR * (1 + 2 * g / (g + 1) * (mach ** 2 - 1))
+        uL0 = S0 * (1 - rR / rL)
+        w = 0.5 * (uL0 + S0)                  # frame velocity: u_L < 0 < S
+        uLn, uRn, S = uL0 - w, -w, S0 - w
+        assert uLn < 0 < S
+        UL = X.prim_to_cons(np.concatenate([[rL], uLn * n + t, [pL]]))
+        UR = X.prim_to_cons(np.concatenate([[rR], uRn * n + t, [pR]]))
+        FL, FR = X.euler_flux(UL, n), X.euler_flux(UR, n)
+        assert np.allclose(FR - FL, S * (UR - UL), rtol=1e-12, atol=1e-12)  # Rankine-Hugoniot
+        F = o.hllc(UL, UR, n)
+        scale = np.abs(FL).max()
+        assert np.abs(F - FL).max() < 1e-12 * scale, (mach, F, FL)
+
+
 # --------------------------------------------------------------------------------------------
 # Selection (eqs. 19-23, Alg. 1, Alg. 2)
 # --------------------------------------------------------------------------------------------
