@@ -4,8 +4,9 @@ Each case below alters one constant or operation of the oracle's source the way 
 the paper would -- an exponent of eq. 19 / Alg. 1 or of the CTENOZ measure of Alg. 2, the average
 over s_t - 1 directional stencils, the "1 +" of the CTENOZ weight, the cut-off C_T of eq. 23, the
 linear coefficients of eq. 18, the CWENO exponent of eq. 14, the division by lambda_1 in eq. 17,
-the smoothness integral of eq. 15, the Roe averages and wave speeds of eqs. 25-26, the SSP-RK3
-weights, the sum over faces of the CFL step -- compiles the altered copy, and runs the pins that
+the smoothness integral of eq. 15, the Roe averages, wave speeds and star states of eqs. 25-29,
+the SSP-RK3 and RK4 weights, the reflected wall state, the characteristic eigenvectors, the sum
+over faces of the CFL step -- compiles the altered copy, and runs the pins that
 should notice against it: at least one of them must fail. An unaltered copy compiled the same way
 must pass all of them, which shows that the altered build is the one under test.
 """
@@ -24,6 +25,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "cteno_oracle.c")
 SELECTION = (os.path.join(ROOT, "tests", "test_oracle_selection_pins.py"), None)
 HLLC = (os.path.join(ROOT, "tests", "test_oracle_pins.py"), "hllc")
+WALLS = (os.path.join(ROOT, "tests", "test_oracle_walls_rk4.py"), "walls_conserve or flow_into_a_wall")
+RK4 = (os.path.join(ROOT, "tests", "test_oracle_walls_rk4.py"), "runge_kutta_order or rk4_step")
+CHAR = (os.path.join(ROOT, "tests", "test_oracle_characteristic.py"), "eigenvectors or smooth_field or contact")
 
 # (name, text in the oracle, misread replacement[, pins: (file, -k expression)]); the text occurs
 # once, except where noted; the pins default to the selection and time-step pins
@@ -65,6 +69,23 @@ MUTATIONS = [
     ("SSP-RK3 second stage with weights 1/2, 1/2",
      "a[3] = {0.0, 0.75, 1.0 / 3.0}, b[3] = {1.0, 0.25, 2.0 / 3.0}",
      "a[3] = {0.0, 0.5, 1.0 / 3.0}, b[3] = {1.0, 0.5, 2.0 / 3.0}", (HLLC[0], "ssp_rk3")),
+    ("HLLC star momentum with p* + p_L (eq. 29)",
+     "us[1 + j] = ((SL - unL) * uL[1 + j] + (ps - pL) * n[j]) * f;",
+     "us[1 + j] = ((SL - unL) * uL[1 + j] + (ps + pL) * n[j]) * f;", HLLC),
+    ("HLLC star energy without the p_L u_L term (eq. 29)",
+     "us[d + 1] = ((SL - unL) * uL[d + 1] - pL * unL + ps * SM) * f;",
+     "us[d + 1] = ((SL - unL) * uL[d + 1] + ps * SM) * f;", HLLC),
+    ("wall state with the normal momentum subtracted once instead of reflected",
+     "ub[1 + k] = uL[1 + k] - 2.0 * mn * n[k];", "ub[1 + k] = uL[1 + k] - mn * n[k];", WALLS),
+    ("RK4 last stage with dt/3",
+     "o->U[k] = o->Acc[k] + dk / 6.0;", "o->U[k] = o->Acc[k] + dk / 3.0;", RK4),
+    ("RK4 second stage accumulated with dt/6",
+     "o->Acc[k] += dk / 3.0;\n        o->U[k] = o->Un[k] + 0.5 * dk;",
+     "o->Acc[k] += dk / 6.0;\n        o->U[k] = o->Un[k] + 0.5 * dk;", RK4),
+    ("left eigenvector of u_n - c with the sign of u_n / c flipped",
+     "L[0][0] = 0.5 * (b2 + un / c);", "L[0][0] = 0.5 * (b2 - un / c);", CHAR),
+    ("left eigenvector of u_n - c with the sign of n / c flipped",
+     "L[0][1 + j] = 0.5 * (-b1 * vel[j] - n[j] / c);", "L[0][1 + j] = 0.5 * (-b1 * vel[j] + n[j] / c);", CHAR),
 ]
 
 
