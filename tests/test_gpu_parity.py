@@ -42,12 +42,24 @@ def _relerr(a, b):
     return float((np.abs(a - b) / scale).max())
 
 
+def _ragged(wl, drop):
+    """The workload without its last `drop` cells (the vertices stay; the cells left around the
+    gap get boundary faces): a 3D cell count that, unlike 6 n^3, is no multiple of the tiles of
+    any schedule (6, 16, 24 or 32 cells)."""
+    keep = wl.mesh.ncells - drop
+    mesh = W.Mesh(wl.mesh.dim, wl.mesh.xyz, np.ascontiguousarray(wl.mesh.cells[:keep]), wl.mesh.period,
+                  name=f"{wl.mesh.name}-minus{drop}")
+    return W.Workload(f"{wl.name}-minus{drop}", mesh, np.ascontiguousarray(wl.U0[:, :keep]), wl.params)
+
+
 CASES = [
     ("tri-per-r2", lambda: W.density_wave_2d(16), 2),
     ("tri-r3", lambda: W.shock_tube_2d(24, 8), 3),
     ("tri-r2-sod", lambda: W.shock_tube_2d(32, 8), 2),
+    ("tri-r2-ragged", lambda: W.shock_tube_2d(23, 7), 2),      # 322 cells: 8-cell tiles end ragged
     ("tet-per-r2", lambda: W.density_wave_3d(6), 2),
     ("tet-r3", lambda: W.blast_3d(5), 3),
+    ("tet-r3-ragged", lambda: _ragged(W.blast_3d(6), 5), 3),   # 1291 cells: 6-cell tiles end ragged
 ]
 
 
@@ -247,12 +259,14 @@ def _stream_smem(d, degree, warps, stages=3):
                               "streamed-cells-4",
                               "streamed-cells-7", "streamed-cells-8", "pair-2", "pair-8", "pair3-4", "pair3-8"])
 def test_mixed_schedules_agree(launch):
-    """Every launch schedule of the mixed path gives the same face states and update on a 2D and a
-    3D mesh (the arithmetic per variable is the same in each schedule). A staged schedule whose two
+    """Every launch schedule of the mixed path gives the same face states and update on 2D and 3D
+    meshes (the arithmetic per variable is the same in each schedule), including 3D meshes whose
+    cell count leaves the last tile of every schedule partly empty. A staged schedule whose two
     stages do not fit in shared memory is refused."""
     native = _native()
     for wl, d, deg in ((W.shock_tube_2d(40, 12), 2, 3), (W.blast_3d(6), 3, 3), (W.blast_3d(5), 3, 2),
-                       (W.shock_tube_2d(37, 11), 2, 2)):
+                       (W.shock_tube_2d(37, 11), 2, 2), (_ragged(W.blast_3d(6), 5), 3, 3),
+                       (_ragged(W.blast_3d(5), 1), 3, 2)):
         s = _solver(native, [wl.mesh], d, degree=deg, precision=1)
         if launch[0] == 4096 and d == 3 and deg == 3:
             # the gather-staged stages of a 3D degree-3 tile may exceed the shared-memory budget:
