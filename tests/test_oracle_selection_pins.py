@@ -115,6 +115,18 @@ def test_equal_indicators_give_linear_coefficients(scheme, form, st):
     assert np.allclose(chi, 1.0 / st, rtol=1e-14) and bits == (1 << st) - 1
 
 
+@pytest.mark.parametrize("scheme,form", [(0, 0), (1, 0), (1, 1), (2, 0), (3, 0)],
+                         ids=["CTENO", "CTENOZ", "CTENOZ-wenoz", "CWENO", "TENO"])
+def test_only_the_central_stencil_admissible(scheme, form):
+    """The degenerate case s_t = 1 (no admissible directional stencil): eq. 22 normalises a single
+    weight, so chi_1 = 1 whatever the indicator, and the central stencil is kept by every scheme
+    (eq. 23 with C_T < 1); nothing divides by s_t - 1."""
+    for si in (0.0, 1e-30, 0.3, 7.0e5):
+        for lambda1p in (1e15, 1e4, 2.0):
+            bits, chi = select([si], scheme=scheme, ctenoz_form=form, lambda1p=lambda1p)
+            assert bits == 1 and np.array_equal(chi, [1.0]), (si, lambda1p, bits, chi)
+
+
 # --------------------------------------------------------------------------------------------
 # CTENOZ (Alg. 2)
 # --------------------------------------------------------------------------------------------
