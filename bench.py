@@ -294,8 +294,15 @@ def ncu_traffic(key):
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    src = open(os.path.join(ROOT, "paper_2312_17042_gb300", "csrc", "recon.cuh"), "rb").read()
-    if d.get("recon_cuh_sha256") != hashlib.sha256(src).hexdigest():
+
+    def same(name, field):
+        src = open(os.path.join(ROOT, "paper_2312_17042_gb300", "csrc", name), "rb").read()
+        return d.get(field) == hashlib.sha256(src).hexdigest()
+
+    if not same("recon.cuh", "recon_cuh_sha256"):
+        return None
+    degree = int(key.split(":")[1].split("_r")[1].split("_")[0])
+    if degree >= 4 and not same("recon_high.cuh", "recon_high_cuh_sha256"):  # the degree 4-6 kernels
         return None
     return d.get("bytes_per_launch", {}).get(key)
 
