@@ -129,3 +129,60 @@ def test_boundary_region_validation_without_gpu():
     with pytest.raises(native.CtenoError):
         native.cteno_boundary_region(ctx, 5, (-1, -1, -1), (2, 2, 2), 0)
     native.cteno_destroy(ctx)
+
+
+def test_corrupt_meshes_are_refused_without_gpu():
+    """Host-side fault injection: corrupt connectivity, a degenerate (non-finite) vertex, a face
+    shared by three cells, an empty mesh and a periodic box too small for the stencils each return
+    an error code from the call that sees them, before any device work."""
+    native = _lib()
+    m = W.tri_mesh(8, 8, periodic=False)
+    out_of_range = m.cells.copy()
+    out_of_range[3, 1] = m.nverts + 5
+    negative = m.cells.copy()
+    negative[3, 1] = -1
+    nan_xyz = m.xyz.copy()
+    nan_xyz[2] = np.nan
+    cases = [(m.xyz, out_of_range, -3), (m.xyz, negative, -3),
+             (m.xyz, np.vstack([m.cells, m.cells[:1]]), -3),   # a repeated cell: faces shared three times
+             (nan_xyz, m.cells, -3), (m.xyz, m.cells[:0], -1)]
+    for xyz, cells, code in cases:
+        ctx = native.cteno_create(native.cteno_default_params())
+        with pytest.raises(native.CtenoError) as e:
+            native.cteno_mesh_build(ctx, xyz, cells, m.period)
+        assert e.value.code == code, (e.value.code, str(e.value))
+        native.cteno_destroy(ctx)
+    small = W.tri_mesh(3, 3, periodic=True)
+    ctx = native.cteno_create(native.cteno_default_params())
+    native.cteno_mesh_build(ctx, small.xyz, small.cells, small.period)
+    with pytest.raises(native.CtenoError) as e:   # a stencil would span more than 0.4 of the box
+        native.cteno_stencil_build(ctx)
+    assert e.value.code == -4
+    native.cteno_destroy(ctx)
+
+
+@pytest.mark.parametrize("mesh", [W.tri_mesh(10, 9, periodic=False, seed=8), W.tet_mesh(4, periodic=False, seed=9)],
+                         ids=["tri", "tet"])
+def test_cell_orientation_does_not_change_the_stencils(mesh):
+    """Reference map (reading R5): every cell is brought to the positive vertex order, so a mesh
+    given with every cell negatively oriented (two vertices swapped) gets the same central and
+    directional stencils, face for face, as the same mesh given positively."""
+    native = _lib()
+    d = mesh.dim
+    p = native.cteno_default_params()
+    p.dim = d
+    flipped = mesh.cells.copy()
+    flipped[:, [1, 2]] = flipped[:, [2, 1]]
+    got = []
+    for cells in (mesh.cells, flipped):
+        ctx = native.cteno_create(p)
+        native.cteno_mesh_build(ctx, mesh.xyz, cells, mesh.period)
+        native.cteno_stencil_build(ctx)
+        got.append([native.cteno_get_stencil(ctx, 0, i, with_admissibility=False)[:2]
+                    for i in range(0, mesh.ncells, 7)])
+        native.cteno_destroy(ctx)
+    for (c0, s0), (c1, s1) in zip(*got):
+        assert np.array_equal(c0, c1)
+        # directional stencils per face: the same member sets, whichever local numbering
+        assert sorted(tuple(sorted(c0[j] for j in row if j >= 0)) for row in s0) == \
+               sorted(tuple(sorted(c1[j] for j in row if j >= 0)) for row in s1)
