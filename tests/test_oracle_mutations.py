@@ -5,8 +5,9 @@ the paper would -- an exponent of eq. 19 / Alg. 1 or of the CTENOZ measure of Al
 over s_t - 1 directional stencils, the "1 +" of the CTENOZ weight, the cut-off C_T of eq. 23, the
 linear coefficients of eq. 18, the CWENO exponent of eq. 14, the division by lambda_1 in eq. 17,
 the smoothness integral of eq. 15, the Roe averages, wave speeds and star states of eqs. 25-29,
-the SSP-RK3 and RK4 weights, the reflected wall state, the characteristic eigenvectors, the sum
-over faces of the CFL step -- compiles the altered copy, and runs the pins that
+the SSP-RK3 and RK4 weights, the reflected wall state, the transmissive and moving-shock boundary
+states, the face quadrature and area weights, the characteristic eigenvectors, the sum over faces
+of the CFL step -- compiles the altered copy, and runs the pins that
 should notice against it: at least one of them must fail. An unaltered copy compiled the same way
 must pass all of them, which shows that the altered build is the one under test.
 """
@@ -28,6 +29,7 @@ HLLC = (os.path.join(ROOT, "tests", "test_oracle_pins.py"), "hllc")
 WALLS = (os.path.join(ROOT, "tests", "test_oracle_walls_rk4.py"), "walls_conserve or flow_into_a_wall")
 RK4 = (os.path.join(ROOT, "tests", "test_oracle_walls_rk4.py"), "runge_kutta_order or rk4_step")
 CHAR = (os.path.join(ROOT, "tests", "test_oracle_characteristic.py"), "eigenvectors or smooth_field or contact")
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
 
 # (name, text in the oracle, misread replacement[, pins: (file, -k expression)]); the text occurs
 # once, except where noted; the pins default to the selection and time-step pins
@@ -86,6 +88,21 @@ MUTATIONS = [
      "L[0][0] = 0.5 * (b2 + un / c);", "L[0][0] = 0.5 * (b2 - un / c);", CHAR),
     ("left eigenvector of u_n - c with the sign of n / c flipped",
      "L[0][1 + j] = 0.5 * (-b1 * vel[j] - n[j] / c);", "L[0][1 + j] = 0.5 * (-b1 * vel[j] + n[j] / c);", CHAR),
+    ("transmissive outside state the reconstructed inside value instead of the cell mean",
+     "for (int v = 0; v < nv; ++v) ub[v] = o->U[v * o->ncells + i];",
+     "for (int v = 0; v < nv; ++v) ub[v] = uL[v];", (PINS, "transmissive_inflow")),
+    ("moving-shock boundary without the shock's motion",
+     "use_a = o->shock[0] + o->shock[1] * mid[1] + o->shock[2] * o->stage_time > mid[0];",
+     "use_a = o->shock[0] + o->shock[1] * mid[1] > mid[0];",
+     (os.path.join(ROOT, "tests", "test_oracle_walls_rk4.py"), "moving_shock")),
+    ("face flux not weighted by the face area (eq. 2)",
+     "acc[v] += o->fw[q] * o->area[i * nf + f] * F[v];", "acc[v] += o->fw[q] * F[v];",
+     (PINS, "free_stream or conservation")),
+    ("edge Gauss points moved (2D face rule)",
+     "t[0][0] = 0.5 * (1.0 - g); /* fraction", "t[0][0] = 0.5 * (1.0 - 0.9 * g); /* fraction", (PINS, "face_rule")),
+    ("Gauss-Jacobi weight of the 3D face rule",
+     "double wu2 = (1.0 / 6.0 - 0.5 * u[0]) / (u[1] - u[0]);",
+     "double wu2 = (1.0 / 6.0 - 0.4 * u[0]) / (u[1] - u[0]);", (PINS, "face_rule")),
 ]
 
 

@@ -265,6 +265,40 @@ def test_free_stream_preserved(mesh):
     assert (o.flags() & 1).all()
 
 
+@pytest.mark.parametrize("degree", [2, 3])
+def test_transmissive_inflow_takes_the_cell_mean(degree):
+    """Reading R23 (the outside state of a transmissive face is the cell mean). Supersonic flow
+    u = 3 to the right over a linear density 1 + 0.1 x (uniform p) on [0,1] x [0,0.5]: every
+    polynomial reproduces the field, so the inside state at a boundary face is exact. Interior
+    fluxes cancel, the top and bottom faces carry no mass (u.n = 0), the outflow face x = 1 is
+    upwinded from inside (density 1.1) and the inflow face x = 0 from outside, i.e. from the cell
+    mean 1 + 0.1 x_c of the cell it bounds. Hence the mass rate in closed form:
+      sum_i |V_i| dRho_i/dt = 3 (sum_{inflow faces} |A_f| rho_bar_i - 1.1 * 0.5)."""
+    mesh = W.tri_mesh(12, 6, periodic=False, seed=4)
+    mesh.xyz[:, 1] *= 0.5
+    xyz, cells = mesh.xyz, mesh.cells
+    cen = xyz[cells].mean(axis=1)
+    rho = 1.0 + 0.1 * cen[:, 0]                   # exact cell means of a linear field
+    u, p, g = 3.0, 1.0, 1.4
+    U = np.stack([rho, rho * u, np.zeros_like(rho), p / (g - 1) + 0.5 * rho * u * u])
+    o = Oracle(mesh, degree=degree)
+    o.set_state(U)
+    R = o.residual()
+    vol = 0.5 * np.abs((xyz[cells[:, 1], 0] - xyz[cells[:, 0], 0]) * (xyz[cells[:, 2], 1] - xyz[cells[:, 0], 1])
+                       - (xyz[cells[:, 2], 0] - xyz[cells[:, 0], 0]) * (xyz[cells[:, 1], 1] - xyz[cells[:, 0], 1]))
+    inflow = 0.0
+    for i, c in enumerate(cells):
+        for a in range(3):
+            e = [c[b] for b in range(3) if b != a]
+            if xyz[e[0], 0] == 0.0 and xyz[e[1], 0] == 0.0:
+                inflow += abs(xyz[e[0], 1] - xyz[e[1], 1]) * rho[i]
+    expect = 3.0 * (inflow - 1.1 * 0.5)
+    got = float((vol * R[0]).sum())
+    assert abs(got - expect) < 1e-12 * abs(expect), (got, expect)
+    # the same with the face value 1.0 instead of the mean would differ by 3 * 0.1 * sum |A| x_c
+    assert abs(expect - 3.0 * (1.0 * 0.5 - 1.1 * 0.5)) > 1e-3
+
+
 # --------------------------------------------------------------------------------------------
 # Smoothness indicator (eq. 15)
 # --------------------------------------------------------------------------------------------
