@@ -332,7 +332,13 @@ int cteno_measure_alu_peak(double *fp64_tflops, double *fp32_tflops);
  * is at most 1e9. The error word of the context stays set: use a new context afterwards. */
 int cteno_test_wait_timeout(cteno_ctx *ctx, int64_t limit_ns);
 
+/* Message of the last error on this context ("" if none; "null context" for NULL). The string is
+ * owned by the context and valid until its next failing call or cteno_destroy. */
 const char *cteno_last_error(cteno_ctx *ctx);
+
+/* Wait for the context's work on its stream, then free everything it allocated (device arrays,
+ * staging buffers, the step graph, its events and capture stream). The borrowed stream is not
+ * destroyed. NULL is a no-op. */
 void cteno_destroy(cteno_ctx *ctx);
 
 #ifdef __cplusplus
