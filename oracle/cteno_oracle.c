@@ -24,7 +24,8 @@
  * copies of this file (misread exponents, averages, cut-off, Roe averages, RK weights) must fail
  * those pins (tests/test_oracle_mutations.py).
  * Parity unpinned: the exact stencil membership (readings of the SBC and directional-stencil
- * rules, which the paper defers to its reference [30]) is fixed only by this file.
+ * rules, which the paper defers to its reference [30]) is fixed only by this file, and so is the
+ * direction of the characteristic decomposition (each face's normal; the paper names none).
  *
  * Build: gcc -O2 -ffp-contract=off [-fopenmp] -shared -fPIC (oracle/build_oracle.py).
  */

@@ -88,6 +88,11 @@ MUTATIONS = [
      "L[0][0] = 0.5 * (b2 + un / c);", "L[0][0] = 0.5 * (b2 - un / c);", CHAR),
     ("left eigenvector of u_n - c with the sign of n / c flipped",
      "L[0][1 + j] = 0.5 * (-b1 * vel[j] - n[j] / c);", "L[0][1 + j] = 0.5 * (-b1 * vel[j] + n[j] / c);", CHAR),
+    ("characteristic face values transformed back with L^T instead of R",
+     "for (int w = 0; w < nv; ++w) s += R[v][w] * W[q][w];",
+     "for (int w = 0; w < nv; ++w) s += L[w][v] * W[q][w];", CHAR),
+    ("characteristic mean of field w taken as the conserved mean of variable w",
+     "for (int v = 0; v < nv; ++v) Wbar += L[w][v] * U0[v];", "Wbar = U0[w];", CHAR),
     ("transmissive outside state the reconstructed inside value instead of the cell mean",
      "for (int v = 0; v < nv; ++v) ub[v] = o->U[v * o->ncells + i];",
      "for (int v = 0; v < nv; ++v) ub[v] = uL[v];", (PINS, "transmissive_inflow")),
