@@ -88,6 +88,10 @@ MUTATIONS = [
      "L[0][0] = 0.5 * (b2 + un / c);", "L[0][0] = 0.5 * (b2 - un / c);", CHAR),
     ("left eigenvector of u_n - c with the sign of n / c flipped",
      "L[0][1 + j] = 0.5 * (-b1 * vel[j] - n[j] / c);", "L[0][1 + j] = 0.5 * (-b1 * vel[j] + n[j] / c);", CHAR),
+    ("least-squares rows without the member volumes |V'_m| (eq. 10, reading R6)",
+     "for (int k = 0; k < c->nst; ++k) b[k] = c->Vp[k] * (U[v * n + c->ids[k]] - U0[v]); /* eq. 10 */",
+     "for (int k = 0; k < c->nst; ++k) b[k] = (U[v * n + c->ids[k]] - U0[v]); /* eq. 10 */",
+     (PINS, "linear_fields_reproduced")),
     ("characteristic face values transformed back with L^T instead of R",
      "for (int w = 0; w < nv; ++w) s += R[v][w] * W[q][w];",
      "for (int w = 0; w < nv; ++w) s += L[w][v] * W[q][w];", CHAR),
